@@ -1,0 +1,305 @@
+"""Benchmark of the Binary Stereo Matching hot path on GB300.
+
+One step = the whole path on one stereo pair with inputs already resident in HBM: describe (left and
+right view), the fused cost + aggregation + WTA kernel (both reference views) and the left/right
+check + refinement. Metric: Gpix*disp/s = width * height * dmax per pair / step time.
+
+Default workload: the full-size synthetic 1390 x 1110 RGB8 pair with dmax 256 and a radiometric
+change on the right view (n = 256 bits, S = 31, aggregation window 5, k = n/4, R = 15).
+
+  python bench.py [--gpus N --steps K --warmup W] [--config c1|c2|c4] [--impl ours|reference]
+
+Multi-GPU (torchrun, one process per GPU) runs independent replicas: every rank processes its own
+pair, nothing is exchanged, value = all ranks' pixels*disparities / max-over-ranks time.
+"""
+import argparse
+import hashlib
+import json
+import os
+import re
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+CONFIGS = {
+    "c1": dict(w=450, h=375, dmax=60, radiometric=False, seed=1,
+               name="450x375 RGB8 pair (Teddy-shaped), dmax 60"),
+    "c2": dict(w=1390, h=1110, dmax=256, radiometric=True, seed=2,
+               name="1390x1110 RGB8 pair, dmax 256, radiometric right view"),
+    "c4": dict(w=3840, h=2160, dmax=256, radiometric=False, seed=4,
+               name="3840x2160 RGB8 pair, dmax 256"),
+}
+N_BITS, WINDOW_S, AGG, VOTE_R = 256, 31, 5, 15
+PAIR_SEED = 11
+METRIC = "Gpix*disp/s"
+L2_FLUSH_BYTES = 256 << 20
+POPC_PER_CLK_SM = 16  # measured integer-pipe rate of POPC on sm_103a
+SMS, MAX_SM_MHZ = 152, 2070
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--config", default="c2", choices=sorted(CONFIGS))
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region (SM clock, max clock, throttle reasons)."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:7]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def profile_traffic(kernel_file, workload_key):
+    """ncu DRAM traffic per launch recorded in profiles/, valid only for the unchanged kernel source."""
+    src = os.path.join(ROOT, "paper_1402_2020_gb300", "csrc", kernel_file)
+    digest = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    pdir = os.path.join(ROOT, "profiles")
+    if not os.path.isdir(pdir):
+        return None
+    for fn in sorted(os.listdir(pdir)):
+        if not fn.endswith(".md"):
+            continue
+        for line in open(os.path.join(pdir, fn)):
+            m = re.match(r"traffic_per_launch:\s*(\w+)\s+(\S+)\s+bytes=(\d+)\s+source_sha256=(\w+)", line.strip())
+            if m and m.group(1) == workload_key and m.group(2) == kernel_file and m.group(4) == digest:
+                return int(m.group(3))
+    return None
+
+
+def oracle_sample(cfg, rows):
+    """The oracle as it stands on a band of `rows` rows of the workload: returns (seconds, pix*disp)."""
+    from oracle import oracle
+    from paper_1402_2020_gb300 import synth
+
+    left, right, _ = synth.stereo_pair(cfg["w"], cfg["h"], cfg["dmax"], cfg["seed"], cfg["radiometric"])
+    pairs = synth.pair_table(N_BITS, WINDOW_S, seed=PAIR_SEED)
+    y0 = cfg["h"] // 2 - rows // 2
+    l = np.ascontiguousarray(left[y0:y0 + rows])
+    r = np.ascontiguousarray(right[y0:y0 + rows])
+    t = time.perf_counter()
+    oracle.pipeline(l, r, pairs, cfg["dmax"], win=AGG, R=VOTE_R)
+    dt = time.perf_counter() - t
+    return dt, cfg["w"] * rows * cfg["dmax"]
+
+
+def dist_init(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl" if args.impl == "ours" else "gloo")
+    return world, rank, local
+
+
+def run_reference(args, cfg, world, rank):
+    if rank != 0:
+        return
+    rows = 16
+    times = []
+    for i in range(args.warmup + args.steps):
+        dt, units = oracle_sample(cfg, rows)
+        if i >= args.warmup:
+            times.append(dt)
+    t = float(np.mean(times))
+    v = units / t / 1e9
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": METRIC, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": cfg["name"], "n_bits": N_BITS, "agg_window": AGG,
+                       "sample": f"{cfg['w']}x{rows} row band of the workload per step"},
+            "cpu_baseline": {"value": v, "unit": METRIC, "cores": 1, "kind": "oracle",
+                             "sample": f"{cfg['w']}x{rows} row band, whole oracle pipeline, single thread"},
+            "e2e": {"value": v, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    cfg = CONFIGS[args.config]
+    world, rank, local = dist_init(args)
+    if args.impl == "reference":
+        run_reference(args, cfg, world, rank)
+        return
+    import torch
+
+    from paper_1402_2020_gb300 import bsm, synth
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    w, h, dmax = cfg["w"], cfg["h"], cfg["dmax"]
+    left, right, _ = synth.stereo_pair(w, h, dmax, cfg["seed"] + rank * 1000, cfg["radiometric"])
+    pairs = synth.pair_table(N_BITS, WINDOW_S, seed=PAIR_SEED)
+    params = bsm.make_params(pairs, window_S=WINDOW_S, agg_window=AGG, dmax=dmax, vote_radius=VOTE_R)
+    ctx = bsm.bsm_create(params)
+    stream = torch.cuda.Stream(device=dev)
+    s = stream.cuda_stream
+    nw = N_BITS // 32
+    dl = torch.from_numpy(left).to(dev)
+    dr = torch.from_numpy(right).to(dev)
+    pitch = 3 * w
+    BL = torch.empty((h, w, nw), dtype=torch.int32, device=dev)
+    PL = torch.empty_like(BL)
+    BR = torch.empty_like(BL)
+    PR = torch.empty_like(BL)
+    dL = torch.empty((h, w), dtype=torch.int32, device=dev)
+    dR = torch.empty_like(dL)
+    out = torch.empty_like(dL)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(args.steps)]
+
+    def step(e=None):
+        if e: e[0].record(stream)
+        bsm.bsm_describe(ctx, dl, w, h, pitch, BL, PL, s)
+        if e: e[1].record(stream)
+        bsm.bsm_describe(ctx, dr, w, h, pitch, BR, PR, s)
+        if e: e[2].record(stream)
+        bsm.bsm_cost_aggregate_wta(ctx, BL, PL, BR, PR, w, h, dmax, dL, dR, None, s)
+        if e: e[3].record(stream)
+        bsm.bsm_refine(ctx, dl, pitch, dL, dR, w, h, dmax, out, s)
+        if e: e[4].record(stream)
+
+    with torch.cuda.stream(stream):
+        for _ in range(max(3, args.warmup)):
+            step()
+            flush.zero_()
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        clk = Clocks(local)
+        clk.start()
+        time.sleep(0.3)
+        for i in range(args.steps):
+            step(ev[i])
+            flush.zero_()  # L2 flush between timed steps, outside the step's events
+        torch.cuda.synchronize()
+        clocks = clk.stop()
+    assert bsm.bsm_last_error(ctx) == bsm.BSM_OK
+    per = np.array([[ev[i][j].elapsed_time(ev[i][j + 1]) for j in range(4)] for i in range(args.steps)])
+    step_ms = per.sum(axis=1)
+    t_step = float(step_ms.mean())
+    if world > 1:
+        tt = torch.tensor([t_step], device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        t_step = float(tt.item())
+    units = w * h * dmax
+    value = world * units / (t_step * 1e-3) / 1e9
+
+    # end to end through the host-buffer C-ABI call (H2D of both views and D2H of the map inside)
+    hl = torch.from_numpy(left).pin_memory()
+    hr = torch.from_numpy(right).pin_memory()
+    ho = torch.empty((h, w), dtype=torch.int32).pin_memory()
+    for _ in range(2):
+        bsm.bsm_match_host(ctx, hl.data_ptr(), hr.data_ptr(), w, h, pitch, dmax, ho.data_ptr(), s)
+    e2e_t = []
+    for _ in range(max(3, args.steps // 2)):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        bsm.bsm_match_host(ctx, hl.data_ptr(), hr.data_ptr(), w, h, pitch, dmax, ho.data_ptr(), s)
+        e2e_t.append(time.perf_counter() - t0)
+    e2e_s = float(np.mean(e2e_t))
+    if world > 1:
+        tt = torch.tensor([e2e_s], device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        e2e_s = float(tt.item())
+    e2e_value = world * units / e2e_s / 1e9
+
+    # roofline of the dominant kernel: fused cost/aggregation/WTA, both reference views per launch
+    t_k2 = float(per[:, 2].mean()) * 1e-3
+    word_ops = 2 * units * (N_BITS // 32)
+    achieved = word_ops / t_k2 / 1e9
+    peak = SMS * POPC_PER_CLK_SM * MAX_SM_MHZ * 1e6 / 1e9
+    traffic = profile_traffic("bsm_cost.cu", args.config)
+    line = {
+        "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": cfg["name"], "n_bits": N_BITS, "window_S": WINDOW_S, "agg_window": AGG,
+                   "mask_rank": N_BITS // 4, "vote_radius": VOTE_R, "parallelism": f"replicas x{world}",
+                   "l2": f"flushed between timed steps ({L2_FLUSH_BYTES >> 20} MiB write)"},
+        "stage_ms": {"describe_left": float(per[:, 0].mean()), "describe_right": float(per[:, 1].mean()),
+                     "cost_aggregate_wta": float(per[:, 2].mean()), "refine": float(per[:, 3].mean())},
+        "pairs_per_s": world / (t_step * 1e-3),
+        "e2e": {"value": e2e_value, "unit": METRIC, "h2d_bytes_per_step": 2 * h * pitch,
+                "d2h_bytes_per_step": 4 * w * h, "ms_per_step": e2e_s * 1e3},
+        "gpu_launches": 4 * args.steps,
+        "roofline": {"bound": "alu", "kernel": "cost_wta_kernel", "achieved": achieved, "peak": peak,
+                     "unit": "Gpopc/s", "frac": achieved / peak, "traffic": traffic,
+                     "work_per_launch": word_ops,
+                     "peak_basis": f"{SMS} SMs x {POPC_PER_CLK_SM} POPC/clk x {MAX_SM_MHZ} MHz"},
+        "clocks": clocks,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        dt, u = oracle_sample(cfg, 32)
+        line["cpu_baseline"] = {"value": u / dt / 1e9, "unit": METRIC, "cores": 1, "kind": "oracle",
+                                "sample": f"{w}x32 row band of the workload, whole oracle pipeline, single thread"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    bsm.bsm_destroy(ctx)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,165 @@
+/*
+ * bsm.h - C ABI of the GB300-native Binary Stereo Matching library (libbsm.so).
+ *
+ * Method: K. Zhang, J. Li, Y. Li, W. Hu, L. Sun, S. Yang, "Binary Stereo Matching", Sec. 3.
+ *   describe              Eq. 2-3 (BRIEF descriptor B(x)) and Eq. 5-7 (binary mask Phi(x))
+ *   cost_aggregate_wta    Eq. 8 (masked Hamming cost), a square-window box sum of that cost,
+ *                         and Eq. 1 (winner-take-all), for the left and for the right view
+ *   refine                the left/right check and the voting refinement of Eq. 9-10
+ *
+ * Conventions for every entry point:
+ *   - Image, descriptor, disparity and cost buffers are DEVICE pointers owned by the caller; the
+ *     library never frees them and keeps no reference after the call returns.
+ *   - RGB images are 8-bit, 3 bytes per pixel (R, G, B), rows of pitch_bytes >= 3 * width.
+ *   - Descriptor planes B and Phi are uint32 [height][width][n_bits / 32]; pair i (0-based) of the
+ *     sampling table is bit (i % 32) of word (i / 32), i.e. the weight 2^(i-1) of the paper's
+ *     1-based sum in Eq. 2 and Eq. 7.
+ *   - Disparity maps are int32 [height][width]; the cost volume is uint16 [height][width][dmax]
+ *     (d fastest).
+ *   - `stream` is a cudaStream_t (NULL selects the legacy default stream). Work is enqueued
+ *     asynchronously on it; argument errors are returned synchronously before anything is
+ *     enqueued. Errors detected inside a kernel (a bounded wait that gave up) are latched in a
+ *     device status word read by bsm_last_error().
+ *   - A context is not thread-safe: use one context per host thread (it may serve many streams
+ *     only if calls on it are serialised by the caller).
+ *   - No C++ exception crosses this ABI.
+ */
+#ifndef BSM_H
+#define BSM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct bsm_ctx bsm_ctx;
+
+typedef enum {
+  BSM_OK = 0,
+  BSM_ERR_INVALID_ARG = 1,   /* a size, pointer or parameter is out of its documented range */
+  BSM_ERR_OUT_OF_MEMORY = 2, /* a device or host allocation of the context failed */
+  BSM_ERR_CUDA = 3,          /* a CUDA runtime call or a kernel launch failed */
+  BSM_ERR_TIMEOUT = 4,       /* a bounded device-side wait gave up (see bsm_last_error) */
+  BSM_ERR_UNSUPPORTED = 5    /* valid per the paper, not built in this library version */
+} bsm_status;
+
+/* Parameters of the method, fixed at bsm_create. */
+typedef struct {
+  int32_t n_bits;        /* descriptor length n (Eq. 2): multiple of 32, 32..256 in this version
+                            (the paper uses 4096, Sec. 4.1) */
+  int32_t window_S;      /* sampling window S (Sec. 3): every offset satisfies |off| <= S / 2;
+                            3..63 */
+  const int8_t *pairs;   /* HOST pointer to n_bits entries of 4 int8 (px, py, qx, qy): the offsets of
+                            p_i and q_i from the centre pixel (Eq. 2). Copied at create; the caller
+                            keeps ownership. */
+  int32_t agg_window;    /* odd side of the square box window that sums Eq. 8's cost before Eq. 1;
+                            1 is the paper's method exactly. n_bits * agg_window^2 <= 65535. */
+  int32_t mask_rank;     /* k: T of Eq. 6 is the k-th smallest weight (1-based), 1..n_bits;
+                            0 selects n_bits / 4 (the paper's "quarter smallest value") */
+  int32_t dmax;          /* largest disparity range any call will use: d in [0, dmax-1]
+                            (Eq. 1); 1..256 */
+  int32_t lr_tol;        /* left/right check tolerance in pixels (>= 0; default 1) */
+  int32_t vote_radius;   /* R: the refinement votes over a (2R+1)^2 window (0..31; default 15) */
+  int32_t lambda_c;      /* lambda_c of Eq. 10 (paper: 9), > 0 */
+  int32_t lambda_e;      /* lambda_e of Eq. 10 (paper: 16), > 0 */
+} bsm_params;
+
+/*
+ * Create a context on the current CUDA device: validates the parameters, uploads the sampling
+ * pairs, builds the 2^24-entry colour table (packed CIELAB + intensity, see bsm_copy_color_table)
+ * and the integer vote tables of Eq. 10 on that device. Synchronous.
+ * Returns BSM_ERR_INVALID_ARG / BSM_ERR_UNSUPPORTED for bad parameters (before touching the GPU),
+ * BSM_ERR_OUT_OF_MEMORY or BSM_ERR_CUDA on device failure. *out is set only on BSM_OK.
+ */
+bsm_status bsm_create(const bsm_params *params, bsm_ctx **out);
+
+/* Release the context and everything it owns. Synchronises the device first. NULL is allowed. */
+void bsm_destroy(bsm_ctx *ctx);
+
+/*
+ * Eq. 2-3 and Eq. 5-7 for every pixel of one view.
+ *   rgb_dev      device RGB image, h rows of pitch_bytes
+ *   B_dev        device uint32 [h][w][n_bits/32] output: B(x), bit i = [I(p_i) > I(q_i)]
+ *   Phi_dev      device uint32 [h][w][n_bits/32] output: Phi(x), bit i = [w_i <= T] with
+ *                w_i = max(SAD(x, p_i), SAD(x, q_i)) in integer CIELAB and T the mask_rank-th
+ *                smallest w_i
+ * Intensity is I = (77 R + 150 G + 29 B + 128) >> 8. Sampling positions outside the image are
+ * clamped to the border. Sizes: 1 <= w, h <= 16384, pitch_bytes >= 3 w. B and Phi must be
+ * 16-byte aligned.
+ */
+bsm_status bsm_describe(bsm_ctx *ctx, const uint8_t *rgb_dev, int32_t w, int32_t h, int32_t pitch_bytes,
+                        uint32_t *B_dev, uint32_t *Phi_dev, void *stream);
+
+/*
+ * Eq. 8 + box aggregation + Eq. 1, once with the left view as reference (match x - d) and once with
+ * the right view as reference (match x + d).
+ *   C(x, d) = popcount((B_ref(x) XOR B_other(x_d)) AND Phi_ref(x)); a match outside the image
+ *   costs n_bits. A(x, d) = sum of C over the in-image pixels of the agg_window^2 box around x.
+ *   disp(x) = the smallest d in [0, dmax-1] with the minimum A(x, d).
+ *   dispL, dispR  device int32 [h][w] outputs (left and right reference)
+ *   costL_or_null optional device uint16 [h][w][dmax] output: A(x, d) for the left reference
+ * dmax <= the context's dmax. Descriptor planes must be 16-byte aligned.
+ */
+bsm_status bsm_cost_aggregate_wta(bsm_ctx *ctx, const uint32_t *BL, const uint32_t *PhiL, const uint32_t *BR,
+                                  const uint32_t *PhiR, int32_t w, int32_t h, int32_t dmax, int32_t *dispL,
+                                  int32_t *dispR, uint16_t *costL_or_null, void *stream);
+
+/*
+ * Left/right check and the voting refinement of Eq. 9-10 on the left map.
+ *   valid(x) = x - dL(x) >= 0 and |dL(x) - dR(x - dL(x))| <= lr_tol. Valid pixels keep dL(x).
+ *   An invalid pixel x takes the smallest d maximising W(x, d) = sum over valid p with dL(p) = d in
+ *   the (2R+1)^2 window of floor(Ec[c] * Es[e2] / 2^15), c = CIELAB SAD(x, p), e2 = |x - p|^2,
+ *   Ec[c] = round(32768 exp(-c / lambda_c)), Es[e2] = round(32768 exp(-sqrt(e2) / lambda_e)).
+ *   If no vote is positive: the smaller of the nearest valid dL to the left and to the right on
+ *   the row, the one that exists, else 0.
+ *   rgbL_dev  device left RGB image (h rows of pitch_bytes); out  device int32 [h][w]
+ * Every dL value must lie in [0, dmax-1].
+ */
+bsm_status bsm_refine(bsm_ctx *ctx, const uint8_t *rgbL_dev, int32_t pitch_bytes, const int32_t *dispL,
+                      const int32_t *dispR, int32_t w, int32_t h, int32_t dmax, int32_t *out, void *stream);
+
+/*
+ * The whole method for one pair with HOST buffers: copies both views to the device, runs
+ * describe (both views), cost_aggregate_wta and refine, and copies the refined left map back.
+ * Device buffers come from a workspace the context owns and grows on demand (this call may
+ * allocate). Synchronous: returns after the result is in out_host.
+ *   rgbL_host, rgbR_host  host RGB images, h rows of pitch_bytes (pinned memory is fastest)
+ *   out_host              host int32 [h][w]
+ */
+bsm_status bsm_match_host(bsm_ctx *ctx, const uint8_t *rgbL_host, const uint8_t *rgbR_host, int32_t w, int32_t h,
+                          int32_t pitch_bytes, int32_t dmax, int32_t *out_host, void *stream);
+
+/*
+ * Read and clear the device status word that kernels latch errors into (BSM_OK if none).
+ * Synchronises the context's device.
+ */
+bsm_status bsm_last_error(bsm_ctx *ctx);
+
+/* Static, human-readable name of a status code. */
+const char *bsm_status_string(bsm_status s);
+
+/*
+ * Copy the context's colour table to dst_dev (device uint32 [2^24], index (R << 16) | (G << 8) | B):
+ * byte 0 = L, byte 1 = a + 128, byte 2 = b + 128 (integer CIELAB, D65, each rounded half away from
+ * zero), byte 3 = intensity I. Asynchronous on `stream`.
+ */
+bsm_status bsm_copy_color_table(bsm_ctx *ctx, uint32_t *dst_dev, void *stream);
+
+/*
+ * Host-side integer vote tables of Eq. 10 (no GPU needed): Ec[c] for c in [0, nc), Es[e2] for
+ * e2 in [0, ne). Returns BSM_ERR_INVALID_ARG for non-positive lambdas or sizes.
+ */
+bsm_status bsm_vote_tables(int32_t lambda_c, int32_t lambda_e, int32_t nc, int32_t ne, uint32_t *Ec, uint32_t *Es);
+
+/* Validate parameters without touching the GPU: the checks bsm_create performs first. */
+bsm_status bsm_validate_params(const bsm_params *params);
+
+/* ABI version of this header (incremented on any incompatible change). */
+int32_t bsm_abi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BSM_H */

@@ -134,6 +134,22 @@ void oracle_lab(int R, int G, int B, int32_t *out) {
   out[2] = v[2];
 }
 
+// CIELAB (reading R2) and intensity (reading R1) of every 24-bit colour, index (R << 16) | (G << 8) | B.
+void oracle_lab_all(int8_t *L, int8_t *A, int8_t *Bc, uint8_t *I) {
+  for (int R = 0; R < 256; ++R)
+    for (int G = 0; G < 256; ++G)
+      for (int B = 0; B < 256; ++B) {
+        const size_t i = ((size_t)R << 16) | ((size_t)G << 8) | (size_t)B;
+        int v[3];
+        lab_of(R, G, B, v);
+        L[i] = (int8_t)v[0];
+        A[i] = (int8_t)v[1];
+        Bc[i] = (int8_t)v[2];
+        const uint8_t px[3] = {(uint8_t)R, (uint8_t)G, (uint8_t)B};
+        I[i] = (uint8_t)intensity(px);
+      }
+}
+
 // Eq. 2-3 (descriptor B) and Eq. 5-7 (mask Phi) for every pixel of rows [y0, y1) of one view.
 // rgb: h rows of pitch bytes, pixel = 3 bytes R, G, B. pairs: n entries (px, py, qx, qy), offsets from x.
 // B, Phi: full-image planes [h][w][n/32]; pair i (0-based) is bit i % 32 of word i / 32, which is the
@@ -251,26 +267,33 @@ void oracle_vote_tables(double lambda_c, double lambda_e, int nc, int ne, uint32
   for (int e = 0; e < ne; ++e) Es[e] = (uint32_t)std::lround(32768.0 * std::exp(-std::sqrt((double)e) / lambda_e));
 }
 
-// Eq. 9-10: voting refinement of the invalid pixels of the left map (reading R9).
-// rgb is the left view; dL the left WTA map; valid from the left/right check; out[y][x] the refined map.
-int oracle_refine(const uint8_t *rgb, int pitch, const int32_t *dL, const uint8_t *valid, int w, int h, int dmax,
-                  int R, double lambda_c, double lambda_e, int32_t *out) {
-  if (w <= 0 || h <= 0 || dmax < 1 || R < 0) return -1;
-  std::vector<int> lab((size_t)w * h * 3);
-  for (int y = 0; y < h; ++y)
-    for (int x = 0; x < w; ++x) {
+// Eq. 9-10: voting refinement of the invalid pixels of the left map (reading R9), for the output
+// region [x0, x1) x [y0, y1). rgb is the left view; dL the left WTA map; valid from the left/right
+// check (both full-image); out[y - y0][x - x0] receives the refined map of the region.
+int oracle_refine_region(const uint8_t *rgb, int pitch, const int32_t *dL, const uint8_t *valid, int w, int h,
+                         int dmax, int R, double lambda_c, double lambda_e, int x0, int x1, int y0, int y1,
+                         int32_t *out) {
+  if (w <= 0 || h <= 0 || dmax < 1 || R < 0 || x0 < 0 || x1 > w || y0 < 0 || y1 > h || x0 > x1 || y0 > y1) return -1;
+  // CIELAB of every pixel a window of the region can reach.
+  const int lx0 = std::max(0, x0 - R), lx1 = std::min(w, x1 + R), ly0 = std::max(0, y0 - R), ly1 = std::min(h, y1 + R);
+  const int lw = std::max(0, lx1 - lx0);
+  std::vector<int> lab((size_t)lw * std::max(0, ly1 - ly0) * 3);
+  for (int y = ly0; y < ly1; ++y)
+    for (int x = lx0; x < lx1; ++x) {
       const uint8_t *px = rgb + (size_t)y * pitch + 3 * x;
-      lab_of(px[0], px[1], px[2], &lab[((size_t)y * w + x) * 3]);
+      lab_of(px[0], px[1], px[2], &lab[((size_t)(y - ly0) * lw + (x - lx0)) * 3]);
     }
+  auto lab_at = [&](int x, int y) { return &lab[((size_t)(y - ly0) * lw + (x - lx0)) * 3]; };
   const int nc = 3 * 255 + 1, ne = 2 * R * R + 1;
   std::vector<uint32_t> Ec(nc), Es(ne);
   oracle_vote_tables(lambda_c, lambda_e, nc, ne, Ec.data(), Es.data());
   std::vector<uint32_t> W(dmax);
-  for (int y = 0; y < h; ++y)
-    for (int x = 0; x < w; ++x) {
+  for (int y = y0; y < y1; ++y)
+    for (int x = x0; x < x1; ++x) {
       const size_t i = (size_t)y * w + x;
+      int32_t &o = out[(size_t)(y - y0) * (x1 - x0) + (x - x0)];
       if (valid[i]) {
-        out[i] = dL[i];
+        o = dL[i];
         continue;
       }
       std::fill(W.begin(), W.end(), 0u);
@@ -278,7 +301,7 @@ int oracle_refine(const uint8_t *rgb, int pitch, const int32_t *dL, const uint8_
         for (int xx = std::max(0, x - R); xx <= std::min(w - 1, x + R); ++xx) {
           const size_t j = (size_t)yy * w + xx;
           if (!valid[j]) continue;
-          const int c = lab_sad(&lab[i * 3], &lab[j * 3]);
+          const int c = lab_sad(lab_at(x, y), lab_at(xx, yy));
           const int e2 = (xx - x) * (xx - x) + (yy - y) * (yy - y);
           const uint32_t v = (uint32_t)(((uint64_t)Ec[c] * Es[e2]) >> 15);
           const int d = dL[j];
@@ -310,9 +333,15 @@ int oracle_refine(const uint8_t *rgb, int pitch, const int32_t *dL, const uint8_
         else if (right >= 0) arg = right;
         else arg = 0;
       }
-      out[i] = arg;
+      o = arg;
     }
   return 0;
+}
+
+// Eq. 9-10 over the whole image.
+int oracle_refine(const uint8_t *rgb, int pitch, const int32_t *dL, const uint8_t *valid, int w, int h, int dmax,
+                  int R, double lambda_c, double lambda_e, int32_t *out) {
+  return oracle_refine_region(rgb, pitch, dL, valid, w, h, dmax, R, lambda_c, lambda_e, 0, w, 0, h, out);
 }
 
 }  // extern "C"

@@ -27,6 +27,8 @@ def lib():
         L.oracle_intensity.restype = I
         L.oracle_lab.argtypes = [I, I, I, P]
         L.oracle_lab.restype = None
+        L.oracle_lab_all.argtypes = [P, P, P, P]
+        L.oracle_lab_all.restype = None
         L.oracle_describe.argtypes = [P, I, I, I, P, I, I, I, I, P, P]
         L.oracle_describe.restype = I
         L.oracle_cost_at.argtypes = [P, P, P, I, I, I, I, I, I, I]
@@ -41,6 +43,8 @@ def lib():
         L.oracle_vote_tables.restype = None
         L.oracle_refine.argtypes = [P, I, P, P, I, I, I, I, D, D, P]
         L.oracle_refine.restype = I
+        L.oracle_refine_region.argtypes = [P, I, P, P, I, I, I, I, D, D, I, I, I, I, P]
+        L.oracle_refine_region.restype = I
         _lib = L
     return _lib
 
@@ -65,6 +69,17 @@ def lab(R, G, B):
     out = np.zeros(3, np.int32)
     lib().oracle_lab(int(R), int(G), int(B), _p(out))
     return tuple(int(v) for v in out)
+
+
+def lab_all():
+    """(L, a, b, I) of all 2^24 colours, index (R << 16) | (G << 8) | B (int8, int8, int8, uint8)."""
+    n = 1 << 24
+    L = np.zeros(n, np.int8)
+    A = np.zeros(n, np.int8)
+    Bc = np.zeros(n, np.int8)
+    I = np.zeros(n, np.uint8)
+    lib().oracle_lab_all(_p(L), _p(A), _p(Bc), _p(I))
+    return L, A, Bc, I
 
 
 def describe(img, pairs, k=None, y0=0, y1=None, out=None):
@@ -159,6 +174,20 @@ def refine(imgL, dL, valid, dmax, R=15, lambda_c=9.0, lambda_e=16.0):
                              float(lambda_e), _p(out))
     if rc != 0:
         raise ValueError("oracle_refine rejected its arguments")
+    return out
+
+
+def refine_region(imgL, dL, valid, dmax, x0, x1, y0, y1, R=15, lambda_c=9.0, lambda_e=16.0):
+    """Eq. 9-10 for the output region [x0, x1) x [y0, y1) (inputs are full-image maps)."""
+    imgL = _rgb(imgL)
+    h, w, _ = imgL.shape
+    dL = np.ascontiguousarray(dL, dtype=np.int32)
+    valid = np.ascontiguousarray(valid, dtype=np.uint8)
+    out = np.zeros((y1 - y0, x1 - x0), np.int32)
+    rc = lib().oracle_refine_region(_p(imgL), w * 3, _p(dL), _p(valid), w, h, dmax, int(R), float(lambda_c),
+                                    float(lambda_e), x0, x1, y0, y1, _p(out))
+    if rc != 0:
+        raise ValueError("oracle_refine_region rejected its arguments")
     return out
 
 

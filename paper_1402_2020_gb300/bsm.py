@@ -1,0 +1,252 @@
+"""Thin Python binding of libbsm.so (include/bsm.h): argument marshalling only.
+
+Every computation runs in the library's CUDA kernels. Functions take PyTorch CUDA tensors (device
+memory and streams come from PyTorch) or raw integer addresses, and raise ``BsmError`` on any
+non-OK status. If the compiled library is missing this module raises at load time: there is no
+CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libbsm.so")
+
+BSM_OK = 0
+BSM_ERR_INVALID_ARG = 1
+BSM_ERR_OUT_OF_MEMORY = 2
+BSM_ERR_CUDA = 3
+BSM_ERR_TIMEOUT = 4
+BSM_ERR_UNSUPPORTED = 5
+
+# Every symbol include/bsm.h declares.
+EXPORTED = (
+    "bsm_create", "bsm_destroy", "bsm_describe", "bsm_cost_aggregate_wta", "bsm_refine", "bsm_match_host",
+    "bsm_last_error", "bsm_status_string", "bsm_copy_color_table", "bsm_vote_tables", "bsm_validate_params",
+    "bsm_abi_version",
+)
+
+
+class BsmError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = int(status)
+        super().__init__(f"{where}: {status_name(status)} ({status})")
+
+
+class bsm_params(ctypes.Structure):
+    _fields_ = [
+        ("n_bits", ctypes.c_int32),
+        ("window_S", ctypes.c_int32),
+        ("pairs", ctypes.POINTER(ctypes.c_int8)),
+        ("agg_window", ctypes.c_int32),
+        ("mask_rank", ctypes.c_int32),
+        ("dmax", ctypes.c_int32),
+        ("lr_tol", ctypes.c_int32),
+        ("vote_radius", ctypes.c_int32),
+        ("lambda_c", ctypes.c_int32),
+        ("lambda_e", ctypes.c_int32),
+    ]
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"libbsm.so is not built ({LIB_PATH}); run __graft_entry__.build() first")
+        L = ctypes.CDLL(LIB_PATH)
+        P, I, S = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int
+        L.bsm_create.argtypes = [ctypes.POINTER(bsm_params), ctypes.POINTER(P)]
+        L.bsm_create.restype = S
+        L.bsm_destroy.argtypes = [P]
+        L.bsm_destroy.restype = None
+        L.bsm_describe.argtypes = [P, P, I, I, I, P, P, P]
+        L.bsm_describe.restype = S
+        L.bsm_cost_aggregate_wta.argtypes = [P, P, P, P, P, I, I, I, P, P, P, P]
+        L.bsm_cost_aggregate_wta.restype = S
+        L.bsm_refine.argtypes = [P, P, I, P, P, I, I, I, P, P]
+        L.bsm_refine.restype = S
+        L.bsm_match_host.argtypes = [P, P, P, I, I, I, I, P, P]
+        L.bsm_match_host.restype = S
+        L.bsm_last_error.argtypes = [P]
+        L.bsm_last_error.restype = S
+        L.bsm_status_string.argtypes = [S]
+        L.bsm_status_string.restype = ctypes.c_char_p
+        L.bsm_copy_color_table.argtypes = [P, P, P]
+        L.bsm_copy_color_table.restype = S
+        L.bsm_vote_tables.argtypes = [I, I, I, I, P, P]
+        L.bsm_vote_tables.restype = S
+        L.bsm_validate_params.argtypes = [ctypes.POINTER(bsm_params)]
+        L.bsm_validate_params.restype = S
+        L.bsm_abi_version.argtypes = []
+        L.bsm_abi_version.restype = I
+        _lib = L
+    return _lib
+
+
+def status_name(s: int) -> str:
+    return lib().bsm_status_string(int(s)).decode()
+
+
+def _check(s: int, where: str):
+    if s != BSM_OK:
+        raise BsmError(s, where)
+
+
+def _ptr(t) -> int:
+    """Device/host address of a torch tensor, a numpy array, an int address, or None -> 0."""
+    if t is None:
+        return 0
+    if isinstance(t, int):
+        return t
+    if isinstance(t, np.ndarray):
+        return t.ctypes.data
+    return t.data_ptr()
+
+
+def _stream(stream) -> int:
+    if stream is None:
+        import torch
+
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def make_params(pairs: np.ndarray, window_S: int = 31, agg_window: int = 5, mask_rank: int = 0, dmax: int = 256,
+                lr_tol: int = 1, vote_radius: int = 15, lambda_c: int = 9, lambda_e: int = 16):
+    """bsm_params for a pair table (int8 [n][4]); keeps the table alive on the returned object."""
+    pairs = np.ascontiguousarray(pairs, dtype=np.int8)
+    p = bsm_params()
+    p.n_bits = pairs.shape[0]
+    p.window_S = window_S
+    p.pairs = pairs.ctypes.data_as(ctypes.POINTER(ctypes.c_int8))
+    p.agg_window = agg_window
+    p.mask_rank = mask_rank
+    p.dmax = dmax
+    p.lr_tol = lr_tol
+    p.vote_radius = vote_radius
+    p.lambda_c = lambda_c
+    p.lambda_e = lambda_e
+    p._keep = pairs
+    return p
+
+
+def bsm_abi_version() -> int:
+    return lib().bsm_abi_version()
+
+
+def bsm_validate_params(params: bsm_params) -> int:
+    return lib().bsm_validate_params(ctypes.byref(params))
+
+
+def bsm_vote_tables(lambda_c: int, lambda_e: int, nc: int, ne: int):
+    Ec = np.zeros(nc, np.uint32)
+    Es = np.zeros(ne, np.uint32)
+    _check(lib().bsm_vote_tables(lambda_c, lambda_e, nc, ne, Ec.ctypes.data, Es.ctypes.data), "bsm_vote_tables")
+    return Ec, Es
+
+
+def bsm_create(params: bsm_params) -> int:
+    h = ctypes.c_void_p()
+    _check(lib().bsm_create(ctypes.byref(params), ctypes.byref(h)), "bsm_create")
+    return h.value
+
+
+def bsm_destroy(ctx: int) -> None:
+    lib().bsm_destroy(ctx)
+
+
+def bsm_describe(ctx: int, rgb, w: int, h: int, pitch: int, B, Phi, stream=None) -> None:
+    _check(lib().bsm_describe(ctx, _ptr(rgb), w, h, pitch, _ptr(B), _ptr(Phi), _stream(stream)), "bsm_describe")
+
+
+def bsm_cost_aggregate_wta(ctx: int, BL, PhiL, BR, PhiR, w: int, h: int, dmax: int, dispL, dispR, cost=None,
+                           stream=None) -> None:
+    _check(lib().bsm_cost_aggregate_wta(ctx, _ptr(BL), _ptr(PhiL), _ptr(BR), _ptr(PhiR), w, h, dmax, _ptr(dispL),
+                                        _ptr(dispR), _ptr(cost), _stream(stream)), "bsm_cost_aggregate_wta")
+
+
+def bsm_refine(ctx: int, rgbL, pitch: int, dispL, dispR, w: int, h: int, dmax: int, out, stream=None) -> None:
+    _check(lib().bsm_refine(ctx, _ptr(rgbL), pitch, _ptr(dispL), _ptr(dispR), w, h, dmax, _ptr(out),
+                            _stream(stream)), "bsm_refine")
+
+
+def bsm_match_host(ctx: int, rgbL_host, rgbR_host, w: int, h: int, pitch: int, dmax: int, out_host,
+                   stream=None) -> None:
+    _check(lib().bsm_match_host(ctx, _ptr(rgbL_host), _ptr(rgbR_host), w, h, pitch, dmax, _ptr(out_host),
+                                _stream(stream)), "bsm_match_host")
+
+
+def bsm_last_error(ctx: int) -> int:
+    return lib().bsm_last_error(ctx)
+
+
+def bsm_status_string(s: int) -> str:
+    return status_name(s)
+
+
+def bsm_copy_color_table(ctx: int, dst, stream=None) -> None:
+    _check(lib().bsm_copy_color_table(ctx, _ptr(dst), _stream(stream)), "bsm_copy_color_table")
+
+
+class Matcher:
+    """Convenience owner of one context plus torch-allocated outputs (still only marshalling)."""
+
+    def __init__(self, pairs, **kw):
+        import torch
+
+        self.torch = torch
+        self.params = make_params(pairs, **kw)
+        self.n_bits = self.params.n_bits
+        self.ctx = bsm_create(self.params)
+
+    def close(self):
+        if self.ctx:
+            bsm_destroy(self.ctx)
+            self.ctx = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def planes(self, h, w, device="cuda"):
+        t = self.torch
+        nw = self.n_bits // 32
+        return (t.empty((h, w, nw), dtype=t.int32, device=device), t.empty((h, w, nw), dtype=t.int32, device=device))
+
+    def describe(self, rgb, stream=None):
+        h, w, _ = rgb.shape
+        B, Phi = self.planes(h, w, rgb.device)
+        bsm_describe(self.ctx, rgb, w, h, rgb.stride(0), B, Phi, stream)
+        return B, Phi
+
+    def cost_wta(self, BL, PhiL, BR, PhiR, dmax, want_cost=False, stream=None):
+        t = self.torch
+        h, w, _ = BL.shape
+        dL = t.empty((h, w), dtype=t.int32, device=BL.device)
+        dR = t.empty((h, w), dtype=t.int32, device=BL.device)
+        cost = t.empty((h, w, dmax), dtype=t.int16, device=BL.device) if want_cost else None
+        bsm_cost_aggregate_wta(self.ctx, BL, PhiL, BR, PhiR, w, h, dmax, dL, dR, cost, stream)
+        return dL, dR, cost
+
+    def refine(self, rgbL, dL, dR, dmax, stream=None):
+        t = self.torch
+        h, w, _ = rgbL.shape
+        out = t.empty((h, w), dtype=t.int32, device=rgbL.device)
+        bsm_refine(self.ctx, rgbL, rgbL.stride(0), dL, dR, w, h, dmax, out, stream)
+        return out
+
+    def match(self, rgbL, rgbR, dmax, stream=None):
+        BL, PhiL = self.describe(rgbL, stream)
+        BR, PhiR = self.describe(rgbR, stream)
+        dL, dR, _ = self.cost_wta(BL, PhiL, BR, PhiR, dmax, stream=stream)
+        return self.refine(rgbL, dL, dR, dmax, stream)

@@ -1,0 +1,229 @@
+// Host side of the C ABI declared in include/bsm.h: parameter validation, context set-up (sampling
+// pairs, colour table, vote tables), argument checks and kernel launches.
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+
+#include "bsm_internal.cuh"
+
+namespace {
+
+bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
+
+bsm_status from_cuda(cudaError_t e) {
+  if (e == cudaSuccess) return BSM_OK;
+  if (e == cudaErrorMemoryAllocation) return BSM_ERR_OUT_OF_MEMORY;
+  return BSM_ERR_CUDA;
+}
+
+bool size_ok(int32_t w, int32_t h) { return w >= 1 && h >= 1 && w <= 16384 && h <= 16384; }
+
+// sRGB transfer curve (IEC 61966-2-1) for the 256 channel values; the colour-table kernel takes
+// the rest of the CIELAB conversion from here.
+void srgb_linear_table(double *lin) {
+  for (int v = 0; v < 256; ++v) {
+    const double c = v / 255.0;
+    lin[v] = c <= 0.04045 ? c / 12.92 : std::pow((c + 0.055) / 1.055, 2.4);
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+int32_t bsm_abi_version(void) { return 1; }
+
+const char *bsm_status_string(bsm_status s) {
+  switch (s) {
+    case BSM_OK: return "ok";
+    case BSM_ERR_INVALID_ARG: return "invalid argument";
+    case BSM_ERR_OUT_OF_MEMORY: return "out of memory";
+    case BSM_ERR_CUDA: return "CUDA error";
+    case BSM_ERR_TIMEOUT: return "device-side wait timed out";
+    case BSM_ERR_UNSUPPORTED: return "unsupported by this version";
+  }
+  return "unknown status";
+}
+
+bsm_status bsm_validate_params(const bsm_params *p) {
+  if (p == nullptr || p->pairs == nullptr) return BSM_ERR_INVALID_ARG;
+  if (p->n_bits < 32 || p->n_bits % 32 != 0 || p->n_bits > 4096) return BSM_ERR_INVALID_ARG;
+  if (p->window_S < 3 || p->window_S > 2 * bsm::kMaxHalo + 1) return BSM_ERR_INVALID_ARG;
+  if (p->agg_window < 1 || p->agg_window % 2 == 0) return BSM_ERR_INVALID_ARG;
+  if ((int64_t)p->n_bits * p->agg_window * p->agg_window > 65535) return BSM_ERR_INVALID_ARG;
+  if (p->mask_rank < 0 || p->mask_rank > p->n_bits) return BSM_ERR_INVALID_ARG;
+  if (p->dmax < 1 || p->dmax > 1024) return BSM_ERR_INVALID_ARG;
+  if (p->lr_tol < 0) return BSM_ERR_INVALID_ARG;
+  if (p->vote_radius < 0 || p->vote_radius > bsm::kMaxVoteRadius) return BSM_ERR_INVALID_ARG;
+  if (p->lambda_c <= 0 || p->lambda_e <= 0) return BSM_ERR_INVALID_ARG;
+  const int half = p->window_S / 2;
+  for (int i = 0; i < 4 * p->n_bits; ++i)
+    if (std::abs((int)p->pairs[i]) > half) return BSM_ERR_INVALID_ARG;
+  // Valid per the method, not built in this version.
+  if (p->n_bits != 32 && p->n_bits != 64 && p->n_bits != 128 && p->n_bits != 256) return BSM_ERR_UNSUPPORTED;
+  if (p->agg_window > 7) return BSM_ERR_UNSUPPORTED;
+  if (p->dmax > bsm::kMaxDmax) return BSM_ERR_UNSUPPORTED;
+  return BSM_OK;
+}
+
+bsm_status bsm_vote_tables(int32_t lambda_c, int32_t lambda_e, int32_t nc, int32_t ne, uint32_t *Ec, uint32_t *Es) {
+  if (lambda_c <= 0 || lambda_e <= 0 || nc <= 0 || ne <= 0 || Ec == nullptr || Es == nullptr)
+    return BSM_ERR_INVALID_ARG;
+  // Eq. 10 with integer weights: Ec[c] = round(2^15 exp(-c / lambda_c)), Es[e2] = round(2^15 exp(-sqrt(e2) / lambda_e)).
+  for (int32_t c = 0; c < nc; ++c) Ec[c] = (uint32_t)std::lround(32768.0 * std::exp(-(double)c / (double)lambda_c));
+  for (int32_t e = 0; e < ne; ++e)
+    Es[e] = (uint32_t)std::lround(32768.0 * std::exp(-std::sqrt((double)e) / (double)lambda_e));
+  return BSM_OK;
+}
+
+void bsm_destroy(bsm_ctx *ctx) {
+  if (ctx == nullptr) return;
+  int prev = 0;
+  cudaGetDevice(&prev);
+  cudaSetDevice(ctx->device);
+  cudaDeviceSynchronize();
+  cudaFree(ctx->color_table);
+  cudaFree(ctx->vote_ec);
+  cudaFree(ctx->vote_es);
+  cudaFree(ctx->status);
+  cudaFree(ctx->ws);
+  cudaSetDevice(prev);
+  delete ctx;
+}
+
+bsm_status bsm_create(const bsm_params *p, bsm_ctx **out) {
+  if (out == nullptr) return BSM_ERR_INVALID_ARG;
+  const bsm_status v = bsm_validate_params(p);
+  if (v != BSM_OK) return v;
+  bsm_ctx *ctx = new (std::nothrow) bsm_ctx();
+  if (ctx == nullptr) return BSM_ERR_OUT_OF_MEMORY;
+  ctx->p = *p;
+  ctx->p.pairs = nullptr;  // the copy below is the context's own
+  ctx->nw = p->n_bits / 32;
+  ctx->mask_rank = p->mask_rank == 0 ? p->n_bits / 4 : p->mask_rank;
+  std::memcpy(ctx->pairs, p->pairs, (size_t)4 * p->n_bits);
+  int halo = 0;
+  for (int i = 0; i < 4 * p->n_bits; ++i) halo = std::max(halo, std::abs((int)p->pairs[i]));
+  ctx->halo = halo;
+
+  cudaError_t e = cudaGetDevice(&ctx->device);
+  const int ne = 2 * p->vote_radius * p->vote_radius + 1;
+  double *lin_dev = nullptr;
+  if (e == cudaSuccess) e = cudaMalloc(&ctx->color_table, sizeof(uint32_t) << 24);
+  if (e == cudaSuccess) e = cudaMalloc(&ctx->vote_ec, sizeof(uint32_t) * (bsm::kMaxSad + 1));
+  if (e == cudaSuccess) e = cudaMalloc(&ctx->vote_es, sizeof(uint32_t) * ne);
+  if (e == cudaSuccess) e = cudaMalloc(&ctx->status, sizeof(uint32_t));
+  if (e == cudaSuccess) e = cudaMalloc(&lin_dev, sizeof(double) * 256);
+  if (e == cudaSuccess) {
+    double lin[256];
+    srgb_linear_table(lin);
+    uint32_t Ec[bsm::kMaxSad + 1];
+    uint32_t *Es = new (std::nothrow) uint32_t[ne];
+    if (Es == nullptr) {
+      e = cudaErrorMemoryAllocation;
+    } else {
+      bsm_vote_tables(p->lambda_c, p->lambda_e, bsm::kMaxSad + 1, ne, Ec, Es);
+      e = cudaMemcpy(lin_dev, lin, sizeof(lin), cudaMemcpyHostToDevice);
+      if (e == cudaSuccess) e = cudaMemcpy(ctx->vote_ec, Ec, sizeof(Ec), cudaMemcpyHostToDevice);
+      if (e == cudaSuccess) e = cudaMemcpy(ctx->vote_es, Es, sizeof(uint32_t) * ne, cudaMemcpyHostToDevice);
+      delete[] Es;
+    }
+  }
+  if (e == cudaSuccess) e = cudaMemset(ctx->status, 0, sizeof(uint32_t));
+  if (e == cudaSuccess) e = bsm::build_color_table(ctx->color_table, lin_dev, 0);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  cudaFree(lin_dev);
+  if (e != cudaSuccess) {
+    const bsm_status st = from_cuda(e);
+    bsm_destroy(ctx);
+    return st;
+  }
+  *out = ctx;
+  return BSM_OK;
+}
+
+bsm_status bsm_describe(bsm_ctx *ctx, const uint8_t *rgb_dev, int32_t w, int32_t h, int32_t pitch_bytes,
+                        uint32_t *B_dev, uint32_t *Phi_dev, void *stream) {
+  if (ctx == nullptr || rgb_dev == nullptr || B_dev == nullptr || Phi_dev == nullptr) return BSM_ERR_INVALID_ARG;
+  if (!size_ok(w, h) || pitch_bytes < 3 * w || !aligned16(B_dev) || !aligned16(Phi_dev)) return BSM_ERR_INVALID_ARG;
+  return from_cuda(bsm::launch_describe(ctx, rgb_dev, w, h, pitch_bytes, B_dev, Phi_dev, (cudaStream_t)stream));
+}
+
+bsm_status bsm_cost_aggregate_wta(bsm_ctx *ctx, const uint32_t *BL, const uint32_t *PhiL, const uint32_t *BR,
+                                  const uint32_t *PhiR, int32_t w, int32_t h, int32_t dmax, int32_t *dispL,
+                                  int32_t *dispR, uint16_t *costL_or_null, void *stream) {
+  if (ctx == nullptr || BL == nullptr || PhiL == nullptr || BR == nullptr || PhiR == nullptr || dispL == nullptr ||
+      dispR == nullptr)
+    return BSM_ERR_INVALID_ARG;
+  if (!size_ok(w, h) || dmax < 1 || dmax > ctx->p.dmax) return BSM_ERR_INVALID_ARG;
+  if (!aligned16(BL) || !aligned16(PhiL) || !aligned16(BR) || !aligned16(PhiR)) return BSM_ERR_INVALID_ARG;
+  return from_cuda(bsm::launch_cost_wta(ctx, BL, PhiL, BR, PhiR, w, h, dmax, dispL, dispR, costL_or_null,
+                                        (cudaStream_t)stream));
+}
+
+bsm_status bsm_refine(bsm_ctx *ctx, const uint8_t *rgbL_dev, int32_t pitch_bytes, const int32_t *dispL,
+                      const int32_t *dispR, int32_t w, int32_t h, int32_t dmax, int32_t *out, void *stream) {
+  if (ctx == nullptr || rgbL_dev == nullptr || dispL == nullptr || dispR == nullptr || out == nullptr)
+    return BSM_ERR_INVALID_ARG;
+  if (!size_ok(w, h) || pitch_bytes < 3 * w || dmax < 1 || dmax > ctx->p.dmax) return BSM_ERR_INVALID_ARG;
+  return from_cuda(bsm::launch_refine(ctx, rgbL_dev, pitch_bytes, dispL, dispR, w, h, dmax, out,
+                                      (cudaStream_t)stream));
+}
+
+bsm_status bsm_match_host(bsm_ctx *ctx, const uint8_t *rgbL_host, const uint8_t *rgbR_host, int32_t w, int32_t h,
+                          int32_t pitch_bytes, int32_t dmax, int32_t *out_host, void *stream) {
+  if (ctx == nullptr || rgbL_host == nullptr || rgbR_host == nullptr || out_host == nullptr) return BSM_ERR_INVALID_ARG;
+  if (!size_ok(w, h) || pitch_bytes < 3 * w || dmax < 1 || dmax > ctx->p.dmax) return BSM_ERR_INVALID_ARG;
+  const size_t img = ((size_t)h * pitch_bytes + 255) & ~(size_t)255;
+  const size_t plane = ((size_t)w * h * ctx->nw * 4 + 255) & ~(size_t)255;
+  const size_t map = ((size_t)w * h * 4 + 255) & ~(size_t)255;
+  const size_t need = 2 * img + 4 * plane + 3 * map;
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e = cudaSuccess;
+  if (ctx->ws_bytes < need) {
+    e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess) {
+      cudaFree(ctx->ws);
+      ctx->ws = nullptr;
+      ctx->ws_bytes = 0;
+      e = cudaMalloc(&ctx->ws, need);
+      if (e == cudaSuccess) ctx->ws_bytes = need;
+    }
+    if (e != cudaSuccess) return from_cuda(e);
+  }
+  uint8_t *base = (uint8_t *)ctx->ws;
+  uint8_t *dl = base, *dr = base + img;
+  uint32_t *BL = (uint32_t *)(base + 2 * img), *PhiL = (uint32_t *)(base + 2 * img + plane);
+  uint32_t *BR = (uint32_t *)(base + 2 * img + 2 * plane), *PhiR = (uint32_t *)(base + 2 * img + 3 * plane);
+  int32_t *dispL = (int32_t *)(base + 2 * img + 4 * plane);
+  int32_t *dispR = (int32_t *)(base + 2 * img + 4 * plane + map);
+  int32_t *out = (int32_t *)(base + 2 * img + 4 * plane + 2 * map);
+  e = cudaMemcpyAsync(dl, rgbL_host, (size_t)h * pitch_bytes, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dr, rgbR_host, (size_t)h * pitch_bytes, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = bsm::launch_describe(ctx, dl, w, h, pitch_bytes, BL, PhiL, s);
+  if (e == cudaSuccess) e = bsm::launch_describe(ctx, dr, w, h, pitch_bytes, BR, PhiR, s);
+  if (e == cudaSuccess) e = bsm::launch_cost_wta(ctx, BL, PhiL, BR, PhiR, w, h, dmax, dispL, dispR, nullptr, s);
+  if (e == cudaSuccess) e = bsm::launch_refine(ctx, dl, pitch_bytes, dispL, dispR, w, h, dmax, out, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(out_host, out, (size_t)w * h * 4, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  return from_cuda(e);
+}
+
+bsm_status bsm_last_error(bsm_ctx *ctx) {
+  if (ctx == nullptr) return BSM_ERR_INVALID_ARG;
+  uint32_t v = 0;
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e == cudaSuccess) e = cudaMemcpy(&v, ctx->status, sizeof(v), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemset(ctx->status, 0, sizeof(uint32_t));
+  if (e != cudaSuccess) return BSM_ERR_CUDA;
+  return (bsm_status)v;
+}
+
+bsm_status bsm_copy_color_table(bsm_ctx *ctx, uint32_t *dst_dev, void *stream) {
+  if (ctx == nullptr || dst_dev == nullptr) return BSM_ERR_INVALID_ARG;
+  return from_cuda(cudaMemcpyAsync(dst_dev, ctx->color_table, sizeof(uint32_t) << 24, cudaMemcpyDeviceToDevice,
+                                   (cudaStream_t)stream));
+}
+
+}  // extern "C"

@@ -74,6 +74,7 @@ def left_view(w: int, h: int, rng: np.random.Generator) -> np.ndarray:
         rh = int(rng.integers(max(2, h // 30), max(3, h // 6)))
         x0 = int(rng.integers(0, max(1, w - rw)))
         y0 = int(rng.integers(0, max(1, h - rh)))
+        rw, rh = min(rw, w - x0), min(rh, h - y0)
         tone = rng.integers(30, 226, size=3).astype(np.float32)
         img[y0 : y0 + rh, x0 : x0 + rw] = tone + rng.normal(0.0, 40.0, size=(rh, rw, 3)).astype(np.float32)
     return np.clip(np.rint(img), 0, 255).astype(np.uint8)
