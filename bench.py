@@ -51,6 +51,8 @@ def parse():
     ap.add_argument("--config", default="c2", choices=sorted(CONFIGS))
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cost-rows", type=int, default=0, help="rows per CTA of the cost kernel (0: heuristic)")
+    ap.add_argument("--cost-popc-plain", type=int, default=0, help="1: plain popcount in the cost kernel")
     return ap.parse_args()
 
 
@@ -191,6 +193,7 @@ def main():
     pairs = synth.pair_table(N_BITS, WINDOW_S, seed=PAIR_SEED)
     params = bsm.make_params(pairs, window_S=WINDOW_S, agg_window=AGG, dmax=dmax, vote_radius=VOTE_R)
     ctx = bsm.bsm_create(params)
+    bsm.bsm_set_tuning(ctx, args.cost_rows, args.cost_popc_plain)
     stream = torch.cuda.Stream(device=dev)
     s = stream.cuda_stream
     nw = N_BITS // 32
@@ -289,6 +292,7 @@ def main():
                      "work_per_launch": word_ops,
                      "peak_basis": f"{SMS} SMs x {POPC_PER_CLK_SM} POPC/clk x {MAX_SM_MHZ} MHz"},
         "clocks": clocks,
+        "tuning": bsm.bsm_get_tuning(ctx),
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         dt, u = oracle_sample(cfg, 32)

@@ -46,15 +46,16 @@ typedef enum {
 
 /* Parameters of the method, fixed at bsm_create. */
 typedef struct {
-  int32_t n_bits;        /* descriptor length n (Eq. 2): multiple of 32, 32..256 in this version
-                            (the paper uses 4096, Sec. 4.1) */
+  int32_t n_bits;        /* descriptor length n (Eq. 2): a multiple of 32; this version builds
+                            32, 64, 128 and 256 (the paper uses 4096, Sec. 4.1) */
   int32_t window_S;      /* sampling window S (Sec. 3): every offset satisfies |off| <= S / 2;
                             3..63 */
   const int8_t *pairs;   /* HOST pointer to n_bits entries of 4 int8 (px, py, qx, qy): the offsets of
                             p_i and q_i from the centre pixel (Eq. 2). Copied at create; the caller
                             keeps ownership. */
   int32_t agg_window;    /* odd side of the square box window that sums Eq. 8's cost before Eq. 1;
-                            1 is the paper's method exactly. n_bits * agg_window^2 <= 65535. */
+                            1 is the paper's method exactly. n_bits * agg_window^2 <= 65535;
+                            this version builds 1, 3, 5 and 7. */
   int32_t mask_rank;     /* k: T of Eq. 6 is the k-th smallest weight (1-based), 1..n_bits;
                             0 selects n_bits / 4 (the paper's "quarter smallest value") */
   int32_t dmax;          /* largest disparity range any call will use: d in [0, dmax-1]
@@ -151,6 +152,22 @@ bsm_status bsm_copy_color_table(bsm_ctx *ctx, uint32_t *dst_dev, void *stream);
  * e2 in [0, ne). Returns BSM_ERR_INVALID_ARG for non-positive lambdas or sizes.
  */
 bsm_status bsm_vote_tables(int32_t lambda_c, int32_t lambda_e, int32_t nc, int32_t ne, uint32_t *Ec, uint32_t *Es);
+
+/*
+ * Launch shapes of a context's kernels. Results never depend on them (every shape computes the same
+ * bits); only speed does. The autotuner of the Python package searches them per GPU and workload.
+ * A zero field selects the library's heuristic.
+ */
+typedef struct {
+  int32_t cost_rows;       /* rows per CTA band of the cost/aggregation/WTA kernel: 0 or 8..512 */
+  int32_t cost_popc_plain; /* 1: plain POPC per word in the cost kernel; 0: carry-save adder tree
+                              (n_bits = 256 only) */
+  int32_t reserved[6];     /* must be zero */
+} bsm_tuning;
+
+/* Set / read the context's launch shapes. Synchronous, host only. */
+bsm_status bsm_set_tuning(bsm_ctx *ctx, const bsm_tuning *tuning);
+bsm_status bsm_get_tuning(bsm_ctx *ctx, bsm_tuning *tuning);
 
 /* Validate parameters without touching the GPU: the checks bsm_create performs first. */
 bsm_status bsm_validate_params(const bsm_params *params);

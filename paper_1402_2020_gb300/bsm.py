@@ -26,7 +26,7 @@ BSM_ERR_UNSUPPORTED = 5
 EXPORTED = (
     "bsm_create", "bsm_destroy", "bsm_describe", "bsm_cost_aggregate_wta", "bsm_refine", "bsm_match_host",
     "bsm_last_error", "bsm_status_string", "bsm_copy_color_table", "bsm_vote_tables", "bsm_validate_params",
-    "bsm_abi_version",
+    "bsm_abi_version", "bsm_set_tuning", "bsm_get_tuning",
 )
 
 
@@ -49,6 +49,11 @@ class bsm_params(ctypes.Structure):
         ("lambda_c", ctypes.c_int32),
         ("lambda_e", ctypes.c_int32),
     ]
+
+
+class bsm_tuning(ctypes.Structure):
+    _fields_ = [("cost_rows", ctypes.c_int32), ("cost_popc_plain", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 6)]
 
 
 _lib = None
@@ -83,6 +88,10 @@ def lib():
         L.bsm_vote_tables.restype = S
         L.bsm_validate_params.argtypes = [ctypes.POINTER(bsm_params)]
         L.bsm_validate_params.restype = S
+        L.bsm_set_tuning.argtypes = [P, ctypes.POINTER(bsm_tuning)]
+        L.bsm_set_tuning.restype = S
+        L.bsm_get_tuning.argtypes = [P, ctypes.POINTER(bsm_tuning)]
+        L.bsm_get_tuning.restype = S
         L.bsm_abi_version.argtypes = []
         L.bsm_abi_version.restype = I
         _lib = L
@@ -194,6 +203,19 @@ def bsm_status_string(s: int) -> str:
 
 def bsm_copy_color_table(ctx: int, dst, stream=None) -> None:
     _check(lib().bsm_copy_color_table(ctx, _ptr(dst), _stream(stream)), "bsm_copy_color_table")
+
+
+def bsm_set_tuning(ctx: int, cost_rows: int = 0, cost_popc_plain: int = 0) -> None:
+    t = bsm_tuning()
+    t.cost_rows = cost_rows
+    t.cost_popc_plain = cost_popc_plain
+    _check(lib().bsm_set_tuning(ctx, ctypes.byref(t)), "bsm_set_tuning")
+
+
+def bsm_get_tuning(ctx: int) -> dict:
+    t = bsm_tuning()
+    _check(lib().bsm_get_tuning(ctx, ctypes.byref(t)), "bsm_get_tuning")
+    return {"cost_rows": t.cost_rows, "cost_popc_plain": t.cost_popc_plain}
 
 
 class Matcher:

@@ -210,6 +210,25 @@ bsm_status bsm_match_host(bsm_ctx *ctx, const uint8_t *rgbL_host, const uint8_t 
   return from_cuda(e);
 }
 
+bsm_status bsm_set_tuning(bsm_ctx *ctx, const bsm_tuning *t) {
+  if (ctx == nullptr || t == nullptr) return BSM_ERR_INVALID_ARG;
+  for (int i = 0; i < 6; ++i)
+    if (t->reserved[i] != 0) return BSM_ERR_INVALID_ARG;
+  if (t->cost_rows != 0 && (t->cost_rows < 8 || t->cost_rows > 512)) return BSM_ERR_INVALID_ARG;
+  if (t->cost_popc_plain != 0 && t->cost_popc_plain != 1) return BSM_ERR_INVALID_ARG;
+  ctx->cost_rows = t->cost_rows;
+  ctx->cost_plain_popc = t->cost_popc_plain;
+  return BSM_OK;
+}
+
+bsm_status bsm_get_tuning(bsm_ctx *ctx, bsm_tuning *t) {
+  if (ctx == nullptr || t == nullptr) return BSM_ERR_INVALID_ARG;
+  std::memset(t, 0, sizeof(*t));
+  t->cost_rows = ctx->cost_rows;
+  t->cost_popc_plain = ctx->cost_plain_popc;
+  return BSM_OK;
+}
+
 bsm_status bsm_last_error(bsm_ctx *ctx) {
   if (ctx == nullptr) return BSM_ERR_INVALID_ARG;
   uint32_t v = 0;

@@ -5,24 +5,30 @@
 // warp owns column x0 + l (the outer r lanes on each side only feed the horizontal window), and warp
 // k owns disparities [8k, 8k + 8). The CTA walks down its band one row at a time:
 //   - the reference row's B and Phi for the 32 columns and the other view's B row for the
-//     32 + dmax - 1 columns any of them can match are staged in shared memory;
-//   - each thread computes C(x, y, d) = popc((B_ref ^ B_other) & Phi_ref) for its 8 disparities
-//     (a match outside the image costs n), two 16-bit costs per 32-bit register;
-//   - vertical box sums run in registers over a ring of the last WIN rows (V += C_new - C_old);
+//     32 + dmax - 1 columns any of them can match are contiguous in HBM; one thread stages them in
+//     shared memory with bulk asynchronous copies (TMA, cp.async.bulk) completing on an mbarrier,
+//     double-buffered so that row y + 1 is in flight while row y is computed; every wait is bounded
+//     and a wait that gives up latches BSM_ERR_TIMEOUT in the status word;
+//   - each thread computes C(x, y, d) = popc((B_ref ^ B_other) & Phi_ref) for its 8 disparities (a
+//     match outside the image costs n), two 16-bit costs per 32-bit register. For n = 256 the eight
+//     masked words go through a carry-save adder tree (Harley-Seal), so 4 POPC replace 8;
+//   - vertical box sums: V += C_new - C_old, the last WIN rows of C kept per thread in a shared ring;
 //   - the horizontal box sum takes V from the neighbouring lanes with warp shuffles;
-//   - each thread reduces its 8 aggregated costs to a key (A << 10 | d), whose minimum over the
-//     warps gives the smallest d with the minimum cost; the cost volume never reaches HBM unless
-//     the caller asks for it.
+//   - each thread reduces its 8 aggregated costs to a key (A << 10 | d); warp 0 takes the minimum over
+//     the warps one row later, which gives the smallest d with the minimum cost. The cost volume never
+//     reaches HBM unless the caller asks for it.
 // For n = 256 a lane reads the two 16-byte halves of a descriptor in an order that depends on bit 2
-// of its lane index (both for the reference and the other view), which keeps every 128-bit shared
+// of its lane index (for the reference and the other view alike), which keeps every 128-bit shared
 // load conflict free; the popcount sum does not depend on word order.
 #include "bsm_internal.cuh"
 
 namespace bsm {
 namespace {
 
-constexpr int kDC = 8;  // disparities per thread
+constexpr int kDC = 8;   // disparities per thread
 constexpr int kDP = kDC / 2;
+constexpr int kPad = 8;  // guard columns on both sides of the staged other-view row
+constexpr long long kWaitCycles = 1LL << 31;  // about one second at the GB300 clock
 
 struct CostArgs {
   const uint32_t *B[2];    // reference descriptors per direction
@@ -30,13 +36,53 @@ struct CostArgs {
   const uint32_t *O[2];    // other view's descriptors per direction
   int32_t *disp[2];
   uint16_t *cost;          // optional, direction 0 only
+  uint32_t *status;
   int w, h, dmax, rows;
 };
 
+// ---------------------------------------------------------------- TMA bulk copies and mbarriers
+
+__device__ __forceinline__ uint32_t saddr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(saddr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(saddr(bar)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(saddr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait: false after about a second without completion.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity))
+    if (clock64() - t0 > kWaitCycles) return false;
+  return true;
+}
+
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   saddr(dst)),
+               "l"(src), "r"(bytes), "r"(saddr(bar))
+               : "memory");
+}
+
+// ---------------------------------------------------------------- per-pixel masked Hamming cost
+
 template <int NW>
-__device__ __forceinline__ void load_desc(const uint32_t *p, int lane, uint32_t (&v)[NW]) {
+__device__ __forceinline__ void load_desc(const uint32_t *p, int q, uint32_t (&v)[NW]) {
   if constexpr (NW == 8) {
-    const int q = (lane >> 2) & 1;
     const uint4 a = *reinterpret_cast<const uint4 *>(p + 4 * q);
     const uint4 b = *reinterpret_cast<const uint4 *>(p + 4 * (1 - q));
     v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
@@ -53,94 +99,223 @@ __device__ __forceinline__ void load_desc(const uint32_t *p, int lane, uint32_t 
   }
 }
 
-template <int NW, int WIN>
-__global__ void __launch_bounds__(1024, 1) cost_wta_kernel(const CostArgs a) {
+__device__ __forceinline__ uint32_t lop3_xor3(uint32_t a, uint32_t b, uint32_t c) {
+  uint32_t r;
+  asm("lop3.b32 %0, %1, %2, %3, 0x96;" : "=r"(r) : "r"(a), "r"(b), "r"(c));
+  return r;
+}
+__device__ __forceinline__ uint32_t lop3_maj(uint32_t a, uint32_t b, uint32_t c) {
+  uint32_t r;
+  asm("lop3.b32 %0, %1, %2, %3, 0xE8;" : "=r"(r) : "r"(a), "r"(b), "r"(c));
+  return r;
+}
+// (a ^ b) & m
+__device__ __forceinline__ uint32_t lop3_xor_and(uint32_t a, uint32_t b, uint32_t m) {
+  uint32_t r;
+  asm("lop3.b32 %0, %1, %2, %3, 0x28;" : "=r"(r) : "r"(a), "r"(b), "r"(m));
+  return r;
+}
+
+// popcount over NW words of (b ^ o) & m (Eq. 8).
+template <int NW, bool CSA>
+__device__ __forceinline__ uint32_t masked_hamming(const uint32_t (&b)[NW], const uint32_t (&o)[NW],
+                                                   const uint32_t (&m)[NW]) {
+  uint32_t v[NW];
+#pragma unroll
+  for (int j = 0; j < NW; ++j) v[j] = lop3_xor_and(b[j], o[j], m[j]);
+  if constexpr (CSA && NW == 8) {
+    // Carry-save adders: every bit position's count of ones across the 8 words, in binary.
+    const uint32_t s1 = lop3_xor3(v[0], v[1], v[2]), c1 = lop3_maj(v[0], v[1], v[2]);
+    const uint32_t s2 = lop3_xor3(v[3], v[4], v[5]), c2 = lop3_maj(v[3], v[4], v[5]);
+    const uint32_t s3 = lop3_xor3(s1, s2, v[6]), c3 = lop3_maj(s1, s2, v[6]);
+    const uint32_t s4 = lop3_xor3(c1, c2, c3), c4 = lop3_maj(c1, c2, c3);
+    return (uint32_t)__popc(s3) + (uint32_t)__popc(v[7]) + 2u * (uint32_t)__popc(s4) + 4u * (uint32_t)__popc(c4);
+  } else {
+    uint32_t c = 0;
+#pragma unroll
+    for (int j = 0; j < NW; ++j) c += (uint32_t)__popc(v[j]);
+    return c;
+  }
+}
+
+// ---------------------------------------------------------------- kernel
+
+template <int NW>
+struct Layout {
+  static constexpr bool kTma = NW >= 4;  // 16-byte granules: every row segment is a legal bulk copy
+  int ocols;                             // staged other-view columns including guards
+  int stage_words;                       // one stage: ref B, ref Phi, other row
+  __device__ __host__ explicit Layout(int dmax) {
+    ocols = 32 + dmax - 1 + 2 * kPad;
+    stage_words = (2 * 32 * NW + ocols * NW + 3) & ~3;  // 16-byte multiple: every stage stays aligned
+  }
+};
+
+template <int NW>
+size_t cost_smem_bytes(int dmax, int win, int nthreads) {
+  const Layout<NW> L(dmax);
+  size_t b = 2 * sizeof(uint64_t);                 // mbarriers
+  b += 2 * (size_t)L.stage_words * 4;              // two stages
+  b += 2 * 32 * 32 * 4;                            // keys, double-buffered
+  if (win > 1) b += (size_t)win * nthreads * 16;   // vertical ring (uint4 per thread per row)
+  return b;
+}
+
+template <int NW, int WIN, int DIR, bool CSA>
+__device__ __forceinline__ void cost_rows(const CostArgs &a, uint8_t *smem_raw) {
   constexpr int R = WIN / 2;
   constexpr int OUTC = 32 - 2 * R;
   constexpr int NBITS = 32 * NW;
-  __shared__ __align__(16) uint32_t sref[2][32 * NW];
-  __shared__ __align__(16) uint32_t soth[(32 + kMaxDmax - 1) * NW];
-  __shared__ uint32_t skey[32][32];
+  const Layout<NW> L(a.dmax);
+  uint64_t *full = reinterpret_cast<uint64_t *>(smem_raw);
+  uint32_t *stages = reinterpret_cast<uint32_t *>(smem_raw + 16);
+  uint32_t *keys = stages + 2 * L.stage_words;     // [2][32][32]
+  uint4 *ring = reinterpret_cast<uint4 *>(keys + 2 * 32 * 32);
 
-  const int dir = blockIdx.z;
-  const uint32_t *__restrict__ Bref = dir == 0 ? a.B[0] : a.B[1];
-  const uint32_t *__restrict__ Phiref = dir == 0 ? a.Phi[0] : a.Phi[1];
-  const uint32_t *__restrict__ Both = dir == 0 ? a.O[0] : a.O[1];
-  int32_t *__restrict__ disp = dir == 0 ? a.disp[0] : a.disp[1];
+  const uint32_t *__restrict__ Bref = a.B[DIR];
+  const uint32_t *__restrict__ Phiref = a.Phi[DIR];
+  const uint32_t *__restrict__ Both = a.O[DIR];
+  int32_t *__restrict__ disp = a.disp[DIR];
   const int w = a.w, h = a.h, dmax = a.dmax;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-  const int x0 = blockIdx.x * OUTC - R;  // column of lane 0
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+  const int x0 = blockIdx.x * OUTC - R;
   const int x = x0 + lane;
   const int yb = blockIdx.y * a.rows;
   const int ye = min(h, yb + a.rows);
   const int d0 = warp * kDC;
-  const int ox0 = dir == 0 ? x0 - (dmax - 1) : x0;  // first staged column of the other view
+  const int ox0 = DIR == 0 ? x0 - (dmax - 1) : x0;  // first staged other-view column (before guards)
   const int nocols = 32 + dmax - 1;
   const bool col_in = x >= 0 && x < w;
   const bool out_lane = lane >= R && lane < 32 - R && col_in;
+  const int q = NW == 8 ? (lane >> 2) & 1 : 0;
+  const int y_first = yb - R, n_it = (ye + R) - y_first;
+  // warp-uniform: every lane's x is in the image and every one of the warp's d matches in the image
+  const bool fast_cols =
+      DIR == 0 ? (x0 >= d0 + kDC - 1 && x0 + 31 < w) : (x0 >= 0 && x0 + 31 + d0 + kDC - 1 < w);
 
-  uint32_t ring[WIN > 1 ? WIN : 1][kDP];
-  uint32_t V[kDP];
-#pragma unroll
-  for (int j = 0; j < kDP; ++j) {
-    V[j] = 0;
-#pragma unroll
-    for (int s = 0; s < (WIN > 1 ? WIN : 1); ++s) ring[s][j] = 0;
+  auto issue = [&](int y, int s) {  // one thread: stage row y into buffer s
+    uint32_t *st = stages + s * L.stage_words;
+    if (y >= 0 && y < h) {
+      const int c0 = max(x0, 0), c1 = min(x0 + 32, w);
+      const int o0 = max(ox0, 0), o1 = min(ox0 + nocols, w);
+      uint32_t bytes = 0;
+      if (c1 > c0) bytes += 2u * (uint32_t)((c1 - c0) * NW * 4);
+      if (o1 > o0) bytes += (uint32_t)((o1 - o0) * NW * 4);
+      mbar_arrive_expect_tx(&full[s], bytes);
+      if (c1 > c0) {
+        const uint32_t nb = (uint32_t)((c1 - c0) * NW * 4);
+        bulk_g2s(st + (c0 - x0) * NW, Bref + ((size_t)y * w + c0) * NW, nb, &full[s]);
+        bulk_g2s(st + 32 * NW + (c0 - x0) * NW, Phiref + ((size_t)y * w + c0) * NW, nb, &full[s]);
+      }
+      if (o1 > o0)
+        bulk_g2s(st + 64 * NW + (kPad + o0 - ox0) * NW, Both + ((size_t)y * w + o0) * NW,
+                 (uint32_t)((o1 - o0) * NW * 4), &full[s]);
+    } else {
+      mbar_arrive_expect_tx(&full[s], 0);
+    }
+  };
+  auto load_plain = [&](int y, int s) {  // all threads: stage row y into buffer s with plain loads
+    uint32_t *st = stages + s * L.stage_words;
+    if (y < 0 || y >= h) return;
+    for (int i = tid; i < 64 * NW; i += blockDim.x) {
+      const int half = i / (32 * NW), j = i - half * 32 * NW;
+      const int gx = x0 + j / NW;
+      const uint32_t *src = half ? Phiref : Bref;
+      if (gx >= 0 && gx < w) st[i] = __ldg(src + (size_t)y * w * NW + (ptrdiff_t)x0 * NW + j);
+    }
+    for (int i = tid; i < nocols * NW; i += blockDim.x) {
+      const int gx = ox0 + i / NW;
+      if (gx >= 0 && gx < w)
+        st[64 * NW + kPad * NW + i] = __ldg(Both + (size_t)y * w * NW + (ptrdiff_t)ox0 * NW + i);
+    }
+  };
+  auto reduce_keys = [&](int it) {  // warp 0: minimum key over the warps -> disparity of row yo
+    const int yo = y_first + it - R;
+    const uint32_t *kb = keys + (it & 1) * 1024;
+    uint32_t best = kb[lane];
+    for (int k = 1; k < nwarps; ++k) best = min(best, kb[k * 32 + lane]);
+    if (out_lane) disp[(size_t)yo * w + x] = (int32_t)(best & 1023u);
+  };
+
+  if (tid == 0) {
+    mbar_init(&full[0], 1);
+    mbar_init(&full[1], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if constexpr (WIN > 1) {
+    for (int s = 0; s < WIN; ++s) ring[s * blockDim.x + tid] = make_uint4(0, 0, 0, 0);
+  }
+  __syncthreads();
+  if constexpr (Layout<NW>::kTma) {
+    if (tid == 0) issue(y_first, 0);
+  } else {
+    load_plain(y_first, 0);
   }
 
-  for (int y = yb - R; y < ye + R; ++y) {
-    const bool row_in = y >= 0 && y < h;
-    __syncthreads();
-    if (row_in) {
-      const uint32_t *rB = Bref + (size_t)y * w * NW;
-      const uint32_t *rP = Phiref + (size_t)y * w * NW;
-      for (int i = threadIdx.x; i < 32 * NW; i += blockDim.x) {
-        const int gx = x0 + i / NW;
-        const bool in = gx >= 0 && gx < w;
-        sref[0][i] = in ? __ldg(rB + (ptrdiff_t)x0 * NW + i) : 0u;
-        sref[1][i] = in ? __ldg(rP + (ptrdiff_t)x0 * NW + i) : 0u;
+  uint32_t V[kDP] = {0, 0, 0, 0};
+  for (int it = 0; it < n_it; ++it) {
+    const int y = y_first + it, s = it & 1;
+    bool ok = true;
+    if constexpr (Layout<NW>::kTma) ok = mbar_wait(&full[s], (uint32_t)(it >> 1) & 1u);
+    if (!__syncthreads_and(ok)) {
+      if (tid == 0) {
+        atomicCAS(a.status, 0u, (uint32_t)BSM_ERR_TIMEOUT);
+        if (Layout<NW>::kTma) mbar_wait(&full[s], (uint32_t)(it >> 1) & 1u);  // let the late copy land
       }
-      const uint32_t *rO = Both + (size_t)y * w * NW;
-      for (int i = threadIdx.x; i < nocols * NW; i += blockDim.x) {
-        const int gx = ox0 + i / NW;
-        soth[i] = (gx >= 0 && gx < w) ? __ldg(rO + (ptrdiff_t)ox0 * NW + i) : 0u;
+      return;
+    }
+    // Every thread finished iteration it - 1: its buffer and its keys may be reused.
+    if (it + 1 < n_it) {
+      if constexpr (Layout<NW>::kTma) {
+        if (tid == 0) {
+          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+          issue(y + 1, s ^ 1);
+        }
+      } else {
+        load_plain(y + 1, s ^ 1);
       }
     }
-    __syncthreads();
+    if (warp == 0 && it >= 1 && y - 1 - R >= yb) reduce_keys(it - 1);
 
-    uint32_t C[kDP];
-#pragma unroll
-    for (int j = 0; j < kDP; ++j) C[j] = 0;
-    if (row_in && col_in) {
+    const uint32_t *st = stages + s * L.stage_words;
+    uint32_t C[kDP] = {0, 0, 0, 0};
+    const bool row_in = y >= 0 && y < h;
+    if (row_in && (col_in || !fast_cols)) {
       uint32_t b[NW], m[NW];
-      load_desc<NW>(&sref[0][lane * NW], lane, b);
-      load_desc<NW>(&sref[1][lane * NW], lane, m);
+      load_desc<NW>(st + lane * NW, q, b);
+      load_desc<NW>(st + 32 * NW + lane * NW, q, m);
+      const uint32_t *ob = st + 64 * NW + (kPad + (DIR == 0 ? lane + dmax - 1 - d0 : lane + d0)) * NW;
+      if (fast_cols) {
 #pragma unroll
-      for (int dd = 0; dd < kDC; ++dd) {
-        const int d = d0 + dd;
-        if (d < dmax) {
-          const int idx = dir == 0 ? lane + (dmax - 1) - d : lane + d;
+        for (int dd = 0; dd < kDC; ++dd) {
           uint32_t o[NW];
-          load_desc<NW>(&soth[idx * NW], lane, o);
-          uint32_t c = 0;
+          load_desc<NW>(ob + (DIR == 0 ? -dd : dd) * NW, q, o);
+          const uint32_t c = masked_hamming<NW, CSA>(b, o, m);
+          C[dd >> 1] += c << (16 * (dd & 1));
+        }
+      } else {
 #pragma unroll
-          for (int j = 0; j < NW; ++j) c += __popc((b[j] ^ o[j]) & m[j]);
-          const int xo = dir == 0 ? x - d : x + d;
-          if (xo < 0 || xo >= w) c = NBITS;
-          C[dd >> 1] |= c << (16 * (dd & 1));
+        for (int dd = 0; dd < kDC; ++dd) {
+          uint32_t o[NW];
+          load_desc<NW>(ob + (DIR == 0 ? -dd : dd) * NW, q, o);
+          uint32_t c = masked_hamming<NW, CSA>(b, o, m);
+          const int d = d0 + dd;
+          const bool match_in = DIR == 0 ? x - d >= 0 : x + d < w;
+          c = col_in ? (match_in ? c : (uint32_t)NBITS) : 0u;
+          C[dd >> 1] += c << (16 * (dd & 1));
         }
       }
     }
 
     // vertical box sum over the last WIN rows
     if constexpr (WIN > 1) {
-#pragma unroll
-      for (int j = 0; j < kDP; ++j) {
-        V[j] = V[j] + C[j] - ring[0][j];
-#pragma unroll
-        for (int s = 0; s < WIN - 1; ++s) ring[s][j] = ring[s + 1][j];
-        ring[WIN - 1][j] = C[j];
-      }
+      uint4 *slot = ring + (it % WIN) * blockDim.x + tid;
+      const uint4 old = *slot;
+      *slot = make_uint4(C[0], C[1], C[2], C[3]);
+      V[0] += C[0] - old.x;
+      V[1] += C[1] - old.y;
+      V[2] += C[2] - old.z;
+      V[3] += C[3] - old.w;
     } else {
 #pragma unroll
       for (int j = 0; j < kDP; ++j) V[j] = C[j];
@@ -148,53 +323,76 @@ __global__ void __launch_bounds__(1024, 1) cost_wta_kernel(const CostArgs a) {
 
     const int yo = y - R;
     if (yo >= yb) {
-      uint32_t A[kDP];
-#pragma unroll
-      for (int j = 0; j < kDP; ++j) {
-        A[j] = V[j];
-#pragma unroll
-        for (int s = 1; s <= R; ++s)
-          A[j] += __shfl_up_sync(0xFFFFFFFFu, V[j], s) + __shfl_down_sync(0xFFFFFFFFu, V[j], s);
-      }
       uint32_t key = 0xFFFFFFFFu;
 #pragma unroll
-      for (int dd = 0; dd < kDC; ++dd) {
-        const int d = d0 + dd;
-        if (d < dmax) {
-          const uint32_t av = (A[dd >> 1] >> (16 * (dd & 1))) & 0xFFFFu;
-          key = min(key, (av << 10) | (uint32_t)d);
-          if (dir == 0 && a.cost != nullptr && out_lane) a.cost[((size_t)yo * w + x) * dmax + d] = (uint16_t)av;
+      for (int j = 0; j < kDP; ++j) {
+        uint32_t A = V[j];
+        if constexpr (R == 2) {
+          const uint32_t s1 = V[j] + __shfl_down_sync(0xFFFFFFFFu, V[j], 1);  // V(x) + V(x+1)
+          A = __shfl_up_sync(0xFFFFFFFFu, s1, 2) + s1 + __shfl_down_sync(0xFFFFFFFFu, V[j], 2);
+        } else {
+#pragma unroll
+          for (int t = 1; t <= R; ++t)
+            A += __shfl_up_sync(0xFFFFFFFFu, V[j], t) + __shfl_down_sync(0xFFFFFFFFu, V[j], t);
+        }
+        const int de = d0 + 2 * j;
+        const uint32_t ae = A & 0xFFFFu, ao = A >> 16;
+        if (de < dmax) key = min(key, (ae << 10) | (uint32_t)de);
+        if (de + 1 < dmax) key = min(key, (ao << 10) | (uint32_t)(de + 1));
+        if (DIR == 0 && a.cost != nullptr && out_lane) {
+          uint16_t *cp = a.cost + ((size_t)yo * w + x) * dmax;
+          if (de < dmax) cp[de] = (uint16_t)ae;
+          if (de + 1 < dmax) cp[de + 1] = (uint16_t)ao;
         }
       }
-      skey[warp][lane] = key;
-      __syncthreads();
-      if (warp == 0) {
-        uint32_t best = skey[0][lane];
-        for (int k = 1; k < nwarps; ++k) best = min(best, skey[k][lane]);
-        if (out_lane) disp[(size_t)yo * w + x] = (int32_t)(best & 1023u);
-      }
+      keys[s * 1024 + warp * 32 + lane] = key;
     }
   }
+  __syncthreads();
+  if (warp == 0 && y_first + n_it - 1 - R >= yb) reduce_keys(n_it - 1);
 }
 
-template <int NW, int WIN>
+template <int NW, int WIN, bool CSA>
+__global__ void __launch_bounds__(1024, 1) cost_wta_kernel(const CostArgs a) {
+  extern __shared__ __align__(16) uint8_t smem_raw[];
+  if (blockIdx.z == 0) cost_rows<NW, WIN, 0, CSA>(a, smem_raw);
+  else cost_rows<NW, WIN, 1, CSA>(a, smem_raw);
+}
+
+template <int NW, int WIN, bool CSA>
 cudaError_t launch_t(const CostArgs &a, cudaStream_t s) {
   constexpr int OUTC = 32 - 2 * (WIN / 2);
   const int nwarps = (a.dmax + kDC - 1) / kDC;
+  const size_t smem = cost_smem_bytes<NW>(a.dmax, WIN, nwarps * 32);
+  cudaError_t e = cudaFuncSetAttribute(cost_wta_kernel<NW, WIN, CSA>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
   dim3 grid((a.w + OUTC - 1) / OUTC, (a.h + a.rows - 1) / a.rows, 2);
-  cost_wta_kernel<NW, WIN><<<grid, nwarps * 32, 0, s>>>(a);
+  cost_wta_kernel<NW, WIN, CSA><<<grid, nwarps * 32, smem, s>>>(a);
   return cudaGetLastError();
 }
 
-template <int NW>
+template <int NW, bool CSA>
 cudaError_t launch_win(int win, const CostArgs &a, cudaStream_t s) {
   switch (win) {
-    case 1: return launch_t<NW, 1>(a, s);
-    case 3: return launch_t<NW, 3>(a, s);
-    case 5: return launch_t<NW, 5>(a, s);
-    case 7: return launch_t<NW, 7>(a, s);
+    case 1: return launch_t<NW, 1, CSA>(a, s);
+    case 3: return launch_t<NW, 3, CSA>(a, s);
+    case 5: return launch_t<NW, 5, CSA>(a, s);
+    case 7: return launch_t<NW, 7, CSA>(a, s);
     default: return cudaErrorInvalidValue;
   }
+}
+
+// Rows per CTA: long bands amortise the 2r halo rows, short bands give small images enough CTAs.
+int pick_rows(int w, int h, int win, int dmax) {
+  const int outc = 32 - 2 * (win / 2);
+  const long cols = (w + outc - 1) / outc;
+  const int nwarps = (dmax + kDC - 1) / kDC;
+  const long ctas_per_sm = nwarps >= 16 ? 1 : (nwarps >= 8 ? 2 : 4);
+  const long target = 2L * 152 * ctas_per_sm;  // two full waves of both directions
+  long rows = 128;
+  while (rows > 8 && cols * ((h + rows - 1) / rows) * 2 < target) rows /= 2;
+  return (int)rows;
 }
 
 }  // namespace
@@ -206,13 +404,16 @@ cudaError_t launch_cost_wta(const bsm_ctx *ctx, const uint32_t *BL, const uint32
   a.B[0] = BL; a.Phi[0] = PhiL; a.O[0] = BR; a.disp[0] = dL;
   a.B[1] = BR; a.Phi[1] = PhiR; a.O[1] = BL; a.disp[1] = dR;
   a.cost = cost;
+  a.status = ctx->status;
   a.w = w; a.h = h; a.dmax = dmax;
-  a.rows = h >= 512 ? 64 : 32;
+  a.rows = ctx->cost_rows > 0 ? ctx->cost_rows : pick_rows(w, h, ctx->p.agg_window, dmax);
   switch (ctx->nw) {
-    case 1: return launch_win<1>(ctx->p.agg_window, a, s);
-    case 2: return launch_win<2>(ctx->p.agg_window, a, s);
-    case 4: return launch_win<4>(ctx->p.agg_window, a, s);
-    case 8: return launch_win<8>(ctx->p.agg_window, a, s);
+    case 1: return launch_win<1, false>(ctx->p.agg_window, a, s);
+    case 2: return launch_win<2, false>(ctx->p.agg_window, a, s);
+    case 4: return launch_win<4, false>(ctx->p.agg_window, a, s);
+    case 8:
+      return ctx->cost_plain_popc ? launch_win<8, false>(ctx->p.agg_window, a, s)
+                                  : launch_win<8, true>(ctx->p.agg_window, a, s);
     default: return cudaErrorInvalidValue;
   }
 }

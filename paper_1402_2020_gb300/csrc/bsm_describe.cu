@@ -10,16 +10,23 @@
 //     shared buffer. All 32 lanes read the same offset relative to their own pixel, so tile reads
 //     are bank-conflict free.
 //  2. Warp per pixel: lane l holds the weights of pairs l, l+32, l+64, ... . T (Eq. 6) is the
-//     k-th smallest weight, found by bisection on the value range [0, 765] with one warp-wide
-//     reduction per step; Phi's words are then __ballot_sync(w <= T) directly, because pair i sits
-//     in lane i % 32.
+//     k-th smallest weight, found by bisection between the smallest and the largest weight with
+//     one warp-wide reduction per step. The weights are stored as fp16 bit patterns of 1024 + w
+//     (exact: every integer below 2048 is an fp16 value), so one fp16x2 compare tests two weights
+//     and the per-lane counts run on the FMA pipe; the bisections of kG pixels are interleaved so
+//     that their reductions overlap. Phi's words are then __ballot_sync(w <= T) directly, because
+//     pair i sits in lane i % 32.
 //  3. The warp writes its 32 pixels' B and Phi words with coalesced stores.
+#include <cuda_fp16.h>
+
 #include "bsm_internal.cuh"
 
 namespace bsm {
 namespace {
 
 constexpr int kTY = 4;  // rows (warps) per CTA
+constexpr int kG = 4;   // pixels whose T searches are interleaved in phase 2
+constexpr uint32_t kHalfBias = 0x64006400u;  // fp16 1024.0 in both halves
 
 struct DescribeArgs {
   const uint8_t *rgb;
@@ -90,14 +97,14 @@ __global__ void __launch_bounds__(kTY * 32) describe_kernel(const DescribeArgs a
         const uint32_t p0 = c[pt.off[i0][0]], q0 = c[pt.off[i0][1]];
         b0 |= (uint32_t)(p0 > (q0 | kLabMask)) << s;
         const uint32_t w0 = max(lab_sad(cw, p0), lab_sad(cw, q0));
-        uint32_t w1 = 0x7FFu;  // padding slot: never <= T
+        uint32_t w1 = 0x3FFu;  // padding slot: 1024 + 1023 as fp16, above every T
         if (2 * m + 1 < NW) {
           const int i1 = i0 + 32;
           const uint32_t p1 = c[pt.off[i1][0]], q1 = c[pt.off[i1][1]];
           b1 |= (uint32_t)(p1 > (q1 | kLabMask)) << s;
           w1 = max(lab_sad(cw, p1), lab_sad(cw, q1));
         }
-        wmine[m * 32 + s] = w0 | (w1 << 16);
+        wmine[m * 32 + s] = (w0 | (w1 << 16)) | kHalfBias;
       }
       stB[lane * NW + 2 * m] = b0;
       if (2 * m + 1 < NW) stB[lane * NW + 2 * m + 1] = b1;
@@ -105,29 +112,71 @@ __global__ void __launch_bounds__(kTY * 32) describe_kernel(const DescribeArgs a
   }
   __syncwarp();
 
-  // 2. warp per pixel
+  // 2. warp per pixel, kG pixels at a time
   const int npx = min(32, a.w - x0);
-  for (int px = 0; px < npx; ++px) {
-    uint32_t v[L::NH];
+  for (int px0 = 0; px0 < npx; px0 += kG) {
+    __half2 v[kG][L::NH];
+    uint32_t lo[kG], hi[kG];
 #pragma unroll
-    for (int m = 0; m < L::NH; ++m) v[m] = wb[px * L::kStride + m * 32 + lane];
-    int lo = 0, hi = kMaxSad;
-    while (lo < hi) {
-      const int mid = (lo + hi) >> 1;
-      int cnt = 0;
+    for (int g = 0; g < kG; ++g) {
+      const int px = min(px0 + g, npx - 1);
 #pragma unroll
-      for (int m = 0; m < L::NH; ++m) cnt += ((int)(v[m] & 0xFFFFu) <= mid) + ((int)(v[m] >> 16) <= mid);
-      cnt = (int)__reduce_add_sync(0xFFFFFFFFu, (unsigned)cnt);
-      if (cnt >= a.k) hi = mid;
-      else lo = mid + 1;
+      for (int m = 0; m < L::NH; ++m) {
+        const uint32_t word = wb[px * L::kStride + m * 32 + lane];
+        v[g][m] = *reinterpret_cast<const __half2 *>(&word);
+      }
+      __half2 mn = v[g][0], mx = v[g][0];
+#pragma unroll
+      for (int m = 1; m < L::NH; ++m) {
+        mn = __hmin2(mn, v[g][m]);
+        mx = __hmax2(mx, v[g][m]);
+      }
+      const uint32_t mnb = *reinterpret_cast<const uint32_t *>(&mn), mxb = *reinterpret_cast<const uint32_t *>(&mx);
+      lo[g] = __reduce_min_sync(0xFFFFFFFFu, min(mnb & 0xFFFFu, mnb >> 16)) & 0x3FFu;
+      hi[g] = __reduce_max_sync(0xFFFFFFFFu, max(mxb & 0xFFFFu, mxb >> 16)) & 0x3FFu;
+    }
+    // T lies in [lo, hi] and count(w <= hi) >= k; every step halves the interval.
+    bool open = false;
+#pragma unroll
+    for (int g = 0; g < kG; ++g) open |= lo[g] < hi[g];
+    while (open) {
+      uint32_t mid[kG], cnt[kG];
+#pragma unroll
+      for (int g = 0; g < kG; ++g) {
+        mid[g] = (lo[g] + hi[g]) >> 1;
+        const uint32_t tb = (0x6400u | mid[g]) * 0x10001u;
+        const __half2 t2 = *reinterpret_cast<const __half2 *>(&tb);
+        __half2 acc = __hle2(v[g][0], t2);
+#pragma unroll
+        for (int m = 1; m < L::NH; ++m) acc = __hadd2(acc, __hle2(v[g][m], t2));
+        const __half c = __hadd(__hadd(__low2half(acc), __high2half(acc)), __ushort_as_half((unsigned short)0x6400));
+        cnt[g] = (uint32_t)__half_as_ushort(c) & 0x3FFu;  // 1024 + count, count <= 2 NH
+      }
+#pragma unroll
+      for (int g = 0; g < kG; ++g) cnt[g] = __reduce_add_sync(0xFFFFFFFFu, cnt[g]);
+      open = false;
+#pragma unroll
+      for (int g = 0; g < kG; ++g) {
+        if (lo[g] < hi[g]) {
+          if ((int)cnt[g] >= a.k) hi[g] = mid[g];
+          else lo[g] = mid[g] + 1;
+        }
+        open |= lo[g] < hi[g];
+      }
     }
 #pragma unroll
-    for (int m = 0; m < L::NH; ++m) {
-      const uint32_t f0 = __ballot_sync(0xFFFFFFFFu, (int)(v[m] & 0xFFFFu) <= lo);
-      const uint32_t f1 = __ballot_sync(0xFFFFFFFFu, (int)(v[m] >> 16) <= lo);
-      if (lane == 0) {
-        stPhi[px * NW + 2 * m] = f0;
-        if (2 * m + 1 < NW) stPhi[px * NW + 2 * m + 1] = f1;
+    for (int g = 0; g < kG; ++g) {
+      if (px0 + g >= npx) break;
+      const uint32_t tb = 0x6400u | lo[g];
+#pragma unroll
+      for (int m = 0; m < L::NH; ++m) {
+        const uint32_t word = *reinterpret_cast<const uint32_t *>(&v[g][m]);
+        const uint32_t f0 = __ballot_sync(0xFFFFFFFFu, (word & 0xFFFFu) <= tb);
+        const uint32_t f1 = __ballot_sync(0xFFFFFFFFu, (word >> 16) <= tb);
+        if (lane == 0) {
+          stPhi[(px0 + g) * NW + 2 * m] = f0;
+          if (2 * m + 1 < NW) stPhi[(px0 + g) * NW + 2 * m + 1] = f1;
+        }
       }
     }
   }

@@ -40,6 +40,9 @@ struct bsm_ctx {
   uint32_t *vote_ec = nullptr;      // device, kMaxSad + 1 entries
   uint32_t *vote_es = nullptr;      // device, 2 R^2 + 1 entries
   uint32_t *status = nullptr;       // device status word (bsm_status latched by kernels)
+  // Launch shapes (bsm_set_tuning); 0 selects the library's heuristic.
+  int cost_rows = 0;        // rows per CTA band of the cost kernel
+  int cost_plain_popc = 0;  // 1: plain popcount in the cost kernel instead of the carry-save tree
   // Workspace of bsm_match_host (grown on demand).
   void *ws = nullptr;
   size_t ws_bytes = 0;

@@ -120,6 +120,27 @@ def test_cost_volume_bit_exact(B, orc, win, n):
     c.close()
 
 
+@pytest.mark.parametrize("rows,plain", [(8, 0), (8, 1), (16, 1), (128, 0), (512, 1)])
+def test_tuning_does_not_change_bits(B, orc, rows, plain):
+    w, h, dmax = 77, 41, 40
+    l, r, _ = synth.stereo_pair(w, h, dmax, seed=250)
+    pairs = synth.pair_table(256, 31, seed=251)
+    c = Ctx(B, pairs, agg_window=5, dmax=dmax)
+    B.bsm_set_tuning(c.ctx, rows, plain)
+    assert B.bsm_get_tuning(c.ctx) == {"cost_rows": rows, "cost_popc_plain": plain}
+    BL, PL, _, _ = c.describe(l)
+    BR, PR, _, _ = c.describe(r)
+    dL, dR, cost = c.cost_wta(BL, PL, BR, PR, dmax, want_cost=True)
+    torch.cuda.synchronize()
+    oBL, oPL = orc.describe(l, pairs)
+    oBR, oPR = orc.describe(r, pairs)
+    A = orc.aggregate(oBL, oPL, oBR, dmax, 5, 0)
+    assert (cost.cpu().numpy().view(np.uint16).astype(np.uint32) == A).all()
+    assert (dL.cpu().numpy() == np.argmin(A, axis=2)).all()
+    assert (dR.cpu().numpy() == orc.wta(oBR, oPR, oBL, dmax, 5, 1)).all()
+    c.close()
+
+
 @pytest.mark.parametrize("win", [1, 5])
 def test_wta_and_refine_teddy_shape(B, orc, win):
     w, h, dmax = 450, 375, 60
