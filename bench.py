@@ -286,7 +286,7 @@ def main():
         "pairs_per_s": world / (t_step * 1e-3),
         "e2e": {"value": e2e_value, "unit": METRIC, "h2d_bytes_per_step": 2 * h * pitch,
                 "d2h_bytes_per_step": 4 * w * h, "ms_per_step": e2e_s * 1e3},
-        "gpu_launches": 4 * args.steps,
+        "gpu_launches": 6 * args.steps,  # colour pre-pass + describe per view, cost, refine
         "roofline": {"bound": "alu", "kernel": "cost_wta_kernel", "achieved": achieved, "peak": peak,
                      "unit": "Gpopc/s", "frac": achieved / peak, "traffic": traffic,
                      "work_per_launch": word_ops,

@@ -20,8 +20,12 @@
  *     asynchronously on it; argument errors are returned synchronously before anything is
  *     enqueued. Errors detected inside a kernel (a bounded wait that gave up) are latched in a
  *     device status word read by bsm_last_error().
- *   - A context is not thread-safe: use one context per host thread (it may serve many streams
- *     only if calls on it are serialised by the caller).
+ *   - A context is not thread-safe: use one context per host thread. Its calls share the
+ *     context's scratch memory, so calls on one context must not overlap on the GPU: issue them on
+ *     one stream, or order the streams with events.
+ *   - Calls allocate nothing except where stated: bsm_describe grows the context's scratch the
+ *     first time it sees an image larger than any before (bsm_reserve sizes it up front, which
+ *     is required before capturing calls into a CUDA graph).
  *   - No C++ exception crosses this ABI.
  */
 #ifndef BSM_H
@@ -79,6 +83,12 @@ bsm_status bsm_create(const bsm_params *params, bsm_ctx **out);
 void bsm_destroy(bsm_ctx *ctx);
 
 /*
+ * Size the context's scratch for images of up to max_w x max_h pixels (synchronises the device if
+ * the scratch grows). Afterwards no call on images within that size allocates.
+ */
+bsm_status bsm_reserve(bsm_ctx *ctx, int32_t max_w, int32_t max_h);
+
+/*
  * Eq. 2-3 and Eq. 5-7 for every pixel of one view.
  *   rgb_dev      device RGB image, h rows of pitch_bytes
  *   B_dev        device uint32 [h][w][n_bits/32] output: B(x), bit i = [I(p_i) > I(q_i)]
@@ -87,7 +97,7 @@ void bsm_destroy(bsm_ctx *ctx);
  *                smallest w_i
  * Intensity is I = (77 R + 150 G + 29 B + 128) >> 8. Sampling positions outside the image are
  * clamped to the border. Sizes: 1 <= w, h <= 16384, pitch_bytes >= 3 w. B and Phi must be
- * 16-byte aligned.
+ * 16-byte aligned. Uses the context's scratch (a w * h colour plane), grown here if too small.
  */
 bsm_status bsm_describe(bsm_ctx *ctx, const uint8_t *rgb_dev, int32_t w, int32_t h, int32_t pitch_bytes,
                         uint32_t *B_dev, uint32_t *Phi_dev, void *stream);

@@ -26,7 +26,7 @@ BSM_ERR_UNSUPPORTED = 5
 EXPORTED = (
     "bsm_create", "bsm_destroy", "bsm_describe", "bsm_cost_aggregate_wta", "bsm_refine", "bsm_match_host",
     "bsm_last_error", "bsm_status_string", "bsm_copy_color_table", "bsm_vote_tables", "bsm_validate_params",
-    "bsm_abi_version", "bsm_set_tuning", "bsm_get_tuning",
+    "bsm_abi_version", "bsm_set_tuning", "bsm_get_tuning", "bsm_reserve",
 )
 
 
@@ -92,6 +92,8 @@ def lib():
         L.bsm_set_tuning.restype = S
         L.bsm_get_tuning.argtypes = [P, ctypes.POINTER(bsm_tuning)]
         L.bsm_get_tuning.restype = S
+        L.bsm_reserve.argtypes = [P, I, I]
+        L.bsm_reserve.restype = S
         L.bsm_abi_version.argtypes = []
         L.bsm_abi_version.restype = I
         _lib = L
@@ -203,6 +205,10 @@ def bsm_status_string(s: int) -> str:
 
 def bsm_copy_color_table(ctx: int, dst, stream=None) -> None:
     _check(lib().bsm_copy_color_table(ctx, _ptr(dst), _stream(stream)), "bsm_copy_color_table")
+
+
+def bsm_reserve(ctx: int, max_w: int, max_h: int) -> None:
+    _check(lib().bsm_reserve(ctx, max_w, max_h), "bsm_reserve")
 
 
 def bsm_set_tuning(ctx: int, cost_rows: int = 0, cost_popc_plain: int = 0) -> None:

@@ -28,6 +28,20 @@ void srgb_linear_table(double *lin) {
   }
 }
 
+// Grow the context's colour-plane scratch to at least `pixels` words. Growing waits for all work on
+// the device, because earlier calls may still read the old plane.
+cudaError_t ensure_plane(bsm_ctx *ctx, size_t pixels) {
+  if (ctx->plane_px >= pixels) return cudaSuccess;
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return e;
+  cudaFree(ctx->plane);
+  ctx->plane = nullptr;
+  ctx->plane_px = 0;
+  e = cudaMalloc(&ctx->plane, pixels * sizeof(uint32_t));
+  if (e == cudaSuccess) ctx->plane_px = pixels;
+  return e;
+}
+
 }  // namespace
 
 extern "C" {
@@ -88,6 +102,7 @@ void bsm_destroy(bsm_ctx *ctx) {
   cudaFree(ctx->vote_es);
   cudaFree(ctx->status);
   cudaFree(ctx->ws);
+  cudaFree(ctx->plane);
   cudaSetDevice(prev);
   delete ctx;
 }
@@ -147,7 +162,10 @@ bsm_status bsm_describe(bsm_ctx *ctx, const uint8_t *rgb_dev, int32_t w, int32_t
                         uint32_t *B_dev, uint32_t *Phi_dev, void *stream) {
   if (ctx == nullptr || rgb_dev == nullptr || B_dev == nullptr || Phi_dev == nullptr) return BSM_ERR_INVALID_ARG;
   if (!size_ok(w, h) || pitch_bytes < 3 * w || !aligned16(B_dev) || !aligned16(Phi_dev)) return BSM_ERR_INVALID_ARG;
-  return from_cuda(bsm::launch_describe(ctx, rgb_dev, w, h, pitch_bytes, B_dev, Phi_dev, (cudaStream_t)stream));
+  cudaError_t e = ensure_plane(ctx, (size_t)w * h);
+  if (e != cudaSuccess) return from_cuda(e);
+  return from_cuda(
+      bsm::launch_describe(ctx, rgb_dev, w, h, pitch_bytes, ctx->plane, B_dev, Phi_dev, (cudaStream_t)stream));
 }
 
 bsm_status bsm_cost_aggregate_wta(bsm_ctx *ctx, const uint32_t *BL, const uint32_t *PhiL, const uint32_t *BR,
@@ -180,7 +198,8 @@ bsm_status bsm_match_host(bsm_ctx *ctx, const uint8_t *rgbL_host, const uint8_t 
   const size_t map = ((size_t)w * h * 4 + 255) & ~(size_t)255;
   const size_t need = 2 * img + 4 * plane + 3 * map;
   cudaStream_t s = (cudaStream_t)stream;
-  cudaError_t e = cudaSuccess;
+  cudaError_t e = ensure_plane(ctx, (size_t)w * h);
+  if (e != cudaSuccess) return from_cuda(e);
   if (ctx->ws_bytes < need) {
     e = cudaStreamSynchronize(s);
     if (e == cudaSuccess) {
@@ -201,13 +220,18 @@ bsm_status bsm_match_host(bsm_ctx *ctx, const uint8_t *rgbL_host, const uint8_t 
   int32_t *out = (int32_t *)(base + 2 * img + 4 * plane + 2 * map);
   e = cudaMemcpyAsync(dl, rgbL_host, (size_t)h * pitch_bytes, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(dr, rgbR_host, (size_t)h * pitch_bytes, cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess) e = bsm::launch_describe(ctx, dl, w, h, pitch_bytes, BL, PhiL, s);
-  if (e == cudaSuccess) e = bsm::launch_describe(ctx, dr, w, h, pitch_bytes, BR, PhiR, s);
+  if (e == cudaSuccess) e = bsm::launch_describe(ctx, dl, w, h, pitch_bytes, ctx->plane, BL, PhiL, s);
+  if (e == cudaSuccess) e = bsm::launch_describe(ctx, dr, w, h, pitch_bytes, ctx->plane, BR, PhiR, s);
   if (e == cudaSuccess) e = bsm::launch_cost_wta(ctx, BL, PhiL, BR, PhiR, w, h, dmax, dispL, dispR, nullptr, s);
   if (e == cudaSuccess) e = bsm::launch_refine(ctx, dl, pitch_bytes, dispL, dispR, w, h, dmax, out, s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(out_host, out, (size_t)w * h * 4, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   return from_cuda(e);
+}
+
+bsm_status bsm_reserve(bsm_ctx *ctx, int32_t max_w, int32_t max_h) {
+  if (ctx == nullptr || !size_ok(max_w, max_h)) return BSM_ERR_INVALID_ARG;
+  return from_cuda(ensure_plane(ctx, (size_t)max_w * max_h));
 }
 
 bsm_status bsm_set_tuning(bsm_ctx *ctx, const bsm_tuning *t) {

@@ -1,22 +1,26 @@
 // Descriptor B(x) (Eq. 2-3) and binary mask Phi(x) (Eq. 5-7) for every pixel of one view.
 //
-// One CTA covers a 32 x kTY block of pixels; warp r owns row r of the block, lane l column l.
-//  0. The CTA stages its block plus a halo of the pair table's largest |offset| in shared memory as
-//     packed colour words (L, a+128, b+128, I), clamping coordinates to the image (border
-//     replicate). One colour-table fetch per staged pixel.
+// Pre-pass (color_plane_kernel): one thread per pixel turns the RGB8 image into a plane of packed
+// colour words (L, a+128, b+128, I) with one colour-table fetch per pixel. The plane lives in the
+// context's scratch memory.
+//
+// Describe (describe_kernel): one CTA covers a 32 x kTY block of pixels; warp r owns row r of the
+// block, lane l column l.
+//  0. The CTA copies its block plus a halo of the pair table's largest |offset| from the plane into
+//     shared memory with 4-byte cp.async copies, clamping coordinates to the image (border
+//     replicate).
 //  1. Thread per pixel: for every sampling pair, tau = [I(p) > I(q)] goes into the descriptor word
 //     held in a register; w = max(SAD(x, p), SAD(x, q)) (Eq. 5) is computed with byte-wise
 //     absolute differences and a byte dot product, and stored as a 16-bit value in a per-warp
 //     shared buffer. All 32 lanes read the same offset relative to their own pixel, so tile reads
-//     are bank-conflict free.
+//     are bank-conflict free. The finished descriptor goes straight to HBM (two 16-byte stores).
 //  2. Warp per pixel: lane l holds the weights of pairs l, l+32, l+64, ... . T (Eq. 6) is the
 //     k-th smallest weight, found by bisection between the smallest and the largest weight with
 //     one warp-wide reduction per step. The weights are stored as fp16 bit patterns of 1024 + w
 //     (exact: every integer below 2048 is an fp16 value), so one fp16x2 compare tests two weights
 //     and the per-lane counts run on the FMA pipe; the bisections of kG pixels are interleaved so
 //     that their reductions overlap. Phi's words are then __ballot_sync(w <= T) directly, because
-//     pair i sits in lane i % 32.
-//  3. The warp writes its 32 pixels' B and Phi words with coalesced stores.
+//     pair i sits in lane i % 32, and lanes 0..n/32-1 store them.
 #include <cuda_fp16.h>
 
 #include "bsm_internal.cuh"
@@ -29,11 +33,10 @@ constexpr int kG = 4;   // pixels whose T searches are interleaved in phase 2
 constexpr uint32_t kHalfBias = 0x64006400u;  // fp16 1024.0 in both halves
 
 struct DescribeArgs {
-  const uint8_t *rgb;
-  const uint32_t *table;
+  const uint32_t *plane;  // packed colour words, w * h
   uint32_t *B;
   uint32_t *Phi;
-  int w, h, pitch;
+  int w, h;
   int k;      // mask rank
   int halo;   // tile halo
 };
@@ -41,6 +44,15 @@ struct DescribeArgs {
 __device__ __forceinline__ uint32_t lab_sad(uint32_t a, uint32_t b) {
   // |dL| + |da| + |db|: byte 3 (intensity) has weight 0.
   return __dp4a(__vabsdiffu4(a, b), 0x00010101u, 0u);
+}
+
+__global__ void __launch_bounds__(256) color_plane_kernel(const uint8_t *__restrict__ rgb, int w, int h, int pitch,
+                                                          const uint32_t *__restrict__ table,
+                                                          uint32_t *__restrict__ plane) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
+  if (x >= w) return;
+  const uint8_t *px = rgb + (size_t)y * pitch + 3 * x;
+  plane[(size_t)y * w + x] = __ldg(table + (((uint32_t)px[0] << 16) | ((uint32_t)px[1] << 8) | (uint32_t)px[2]));
 }
 
 // Shared-memory words per pixel of the weight buffer: NH groups of 32 words, each word holding the
@@ -52,6 +64,11 @@ struct WLayout {
   static constexpr int kStride = NH * 32 + 1;
 };
 
+__device__ __forceinline__ void cp_async4(uint32_t *dst, const uint32_t *src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
+               : "memory");
+}
+
 template <int NW>
 __global__ void __launch_bounds__(kTY * 32) describe_kernel(const DescribeArgs a, const __grid_constant__ PairTable pt) {
   using L = WLayout<NW>;
@@ -61,7 +78,6 @@ __global__ void __launch_bounds__(kTY * 32) describe_kernel(const DescribeArgs a
   const int th = kTY + 2 * halo;
   uint32_t *tile = smem;
   uint32_t *wbuf = tile + ((th * tp + 3) & ~3);
-  uint32_t *stage = wbuf + kTY * 32 * L::kStride;
 
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int x0 = blockIdx.x * 32, y0 = blockIdx.y * kTY;
@@ -71,23 +87,22 @@ __global__ void __launch_bounds__(kTY * 32) describe_kernel(const DescribeArgs a
     const int ty = i / tp, tx = i - ty * tp;
     const int gx = min(max(x0 + tx - halo, 0), a.w - 1);
     const int gy = min(max(y0 + ty - halo, 0), a.h - 1);
-    const uint8_t *px = a.rgb + (size_t)gy * a.pitch + 3 * gx;
-    tile[i] = __ldg(a.table + (((uint32_t)px[0] << 16) | ((uint32_t)px[1] << 8) | (uint32_t)px[2]));
+    cp_async4(tile + i, a.plane + (size_t)gy * a.w + gx);
   }
+  asm volatile("cp.async.wait_all;" ::: "memory");
   __syncthreads();
 
   const int y = y0 + warp;
   if (y >= a.h) return;  // whole warp; no CTA-wide barrier follows
-
   uint32_t *wb = wbuf + warp * 32 * L::kStride;
-  uint32_t *stB = stage + warp * 2 * 32 * NW;
-  uint32_t *stPhi = stB + 32 * NW;
+  const int x = x0 + lane;
 
   // 1. thread per pixel
   {
     const uint32_t *c = tile + (warp + halo) * tp + (lane + halo);
     const uint32_t cw = *c;
     uint32_t *wmine = wb + lane * L::kStride;
+    uint32_t bw[NW];
 #pragma unroll
     for (int m = 0; m < L::NH; ++m) {
       uint32_t b0 = 0, b1 = 0;
@@ -106,8 +121,19 @@ __global__ void __launch_bounds__(kTY * 32) describe_kernel(const DescribeArgs a
         }
         wmine[m * 32 + s] = (w0 | (w1 << 16)) | kHalfBias;
       }
-      stB[lane * NW + 2 * m] = b0;
-      if (2 * m + 1 < NW) stB[lane * NW + 2 * m + 1] = b1;
+      bw[2 * m] = b0;
+      if (2 * m + 1 < NW) bw[2 * m + 1] = b1;
+    }
+    if (x < a.w) {
+      uint32_t *gB = a.B + ((size_t)y * a.w + x) * NW;
+      if constexpr (NW % 4 == 0) {
+#pragma unroll
+        for (int j = 0; j < NW; j += 4)
+          *reinterpret_cast<uint4 *>(gB + j) = make_uint4(bw[j], bw[j + 1], bw[j + 2], bw[j + 3]);
+      } else {
+#pragma unroll
+        for (int j = 0; j < NW; ++j) gB[j] = bw[j];
+      }
     }
   }
   __syncwarp();
@@ -168,33 +194,24 @@ __global__ void __launch_bounds__(kTY * 32) describe_kernel(const DescribeArgs a
     for (int g = 0; g < kG; ++g) {
       if (px0 + g >= npx) break;
       const uint32_t tb = 0x6400u | lo[g];
+      uint32_t mine = 0;
 #pragma unroll
       for (int m = 0; m < L::NH; ++m) {
         const uint32_t word = *reinterpret_cast<const uint32_t *>(&v[g][m]);
         const uint32_t f0 = __ballot_sync(0xFFFFFFFFu, (word & 0xFFFFu) <= tb);
         const uint32_t f1 = __ballot_sync(0xFFFFFFFFu, (word >> 16) <= tb);
-        if (lane == 0) {
-          stPhi[(px0 + g) * NW + 2 * m] = f0;
-          if (2 * m + 1 < NW) stPhi[(px0 + g) * NW + 2 * m + 1] = f1;
-        }
+        mine = lane == 2 * m ? f0 : mine;
+        mine = lane == 2 * m + 1 ? f1 : mine;
       }
+      if (lane < NW) a.Phi[((size_t)y * a.w + x0 + px0 + g) * NW + lane] = mine;
     }
-  }
-  __syncwarp();
-
-  // 3. coalesced write-out of the row segment
-  uint32_t *gB = a.B + ((size_t)y * a.w + x0) * NW;
-  uint32_t *gPhi = a.Phi + ((size_t)y * a.w + x0) * NW;
-  for (int i = lane; i < npx * NW; i += 32) {
-    gB[i] = stB[i];
-    gPhi[i] = stPhi[i];
   }
 }
 
 template <int NW>
 size_t describe_smem(int halo) {
   const int tp = 32 + 2 * halo, th = kTY + 2 * halo;
-  return sizeof(uint32_t) * (size_t)(((th * tp + 3) & ~3) + kTY * 32 * WLayout<NW>::kStride + kTY * 2 * 32 * NW);
+  return sizeof(uint32_t) * (size_t)(((th * tp + 3) & ~3) + kTY * 32 * WLayout<NW>::kStride);
 }
 
 template <int NW>
@@ -209,9 +226,16 @@ cudaError_t launch_nw(const DescribeArgs &a, const PairTable &pt, cudaStream_t s
 
 }  // namespace
 
-cudaError_t launch_describe(const bsm_ctx *ctx, const uint8_t *rgb, int w, int h, int pitch, uint32_t *B,
-                            uint32_t *Phi, cudaStream_t s) {
-  DescribeArgs a{rgb, ctx->color_table, B, Phi, w, h, pitch, ctx->mask_rank, ctx->halo};
+cudaError_t launch_color_plane(const bsm_ctx *ctx, const uint8_t *rgb, int w, int h, int pitch, uint32_t *plane,
+                               cudaStream_t s) {
+  dim3 grid((w + 255) / 256, h);
+  color_plane_kernel<<<grid, 256, 0, s>>>(rgb, w, h, pitch, ctx->color_table, plane);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_describe_plane(const bsm_ctx *ctx, const uint32_t *plane, int w, int h, uint32_t *B,
+                                  uint32_t *Phi, cudaStream_t s) {
+  DescribeArgs a{plane, B, Phi, w, h, ctx->mask_rank, ctx->halo};
   const int tp = 32 + 2 * ctx->halo;
   PairTable pt{};
   for (int i = 0; i < ctx->p.n_bits; ++i) {
@@ -222,14 +246,17 @@ cudaError_t launch_describe(const bsm_ctx *ctx, const uint8_t *rgb, int w, int h
   switch (ctx->nw) {
     case 1: return launch_nw<1>(a, pt, s);
     case 2: return launch_nw<2>(a, pt, s);
-    case 3: return launch_nw<3>(a, pt, s);
     case 4: return launch_nw<4>(a, pt, s);
-    case 5: return launch_nw<5>(a, pt, s);
-    case 6: return launch_nw<6>(a, pt, s);
-    case 7: return launch_nw<7>(a, pt, s);
     case 8: return launch_nw<8>(a, pt, s);
     default: return cudaErrorInvalidValue;
   }
+}
+
+cudaError_t launch_describe(const bsm_ctx *ctx, const uint8_t *rgb, int w, int h, int pitch, uint32_t *plane,
+                            uint32_t *B, uint32_t *Phi, cudaStream_t s) {
+  cudaError_t e = launch_color_plane(ctx, rgb, w, h, pitch, plane, s);
+  if (e != cudaSuccess) return e;
+  return launch_describe_plane(ctx, plane, w, h, B, Phi, s);
 }
 
 }  // namespace bsm

@@ -43,6 +43,9 @@ struct bsm_ctx {
   // Launch shapes (bsm_set_tuning); 0 selects the library's heuristic.
   int cost_rows = 0;        // rows per CTA band of the cost kernel
   int cost_plain_popc = 0;  // 1: plain popcount in the cost kernel instead of the carry-save tree
+  // Scratch: packed colour plane of the describe pre-pass (grown on demand, or by bsm_reserve).
+  uint32_t *plane = nullptr;
+  size_t plane_px = 0;
   // Workspace of bsm_match_host (grown on demand).
   void *ws = nullptr;
   size_t ws_bytes = 0;
@@ -52,8 +55,12 @@ namespace bsm {
 
 // Launchers (each returns cudaGetLastError() after enqueueing).
 cudaError_t build_color_table(uint32_t *table, const double *lin256, cudaStream_t s);
-cudaError_t launch_describe(const bsm_ctx *ctx, const uint8_t *rgb, int w, int h, int pitch, uint32_t *B,
-                            uint32_t *Phi, cudaStream_t s);
+cudaError_t launch_color_plane(const bsm_ctx *ctx, const uint8_t *rgb, int w, int h, int pitch, uint32_t *plane,
+                               cudaStream_t s);
+cudaError_t launch_describe_plane(const bsm_ctx *ctx, const uint32_t *plane, int w, int h, uint32_t *B,
+                                  uint32_t *Phi, cudaStream_t s);
+cudaError_t launch_describe(const bsm_ctx *ctx, const uint8_t *rgb, int w, int h, int pitch, uint32_t *plane,
+                            uint32_t *B, uint32_t *Phi, cudaStream_t s);
 cudaError_t launch_cost_wta(const bsm_ctx *ctx, const uint32_t *BL, const uint32_t *PhiL, const uint32_t *BR,
                             const uint32_t *PhiR, int w, int h, int dmax, int32_t *dL, int32_t *dR, uint16_t *cost,
                             cudaStream_t s);

@@ -4,10 +4,13 @@
 // each pixel's CIELAB word (from the colour table) and its disparity if that pixel passes the
 // left/right check (-1 otherwise), together with the two integer vote tables. Valid pixels keep
 // their disparity. Invalid pixels are collected into a list that the CTA's warps share: a warp takes
-// one invalid pixel at a time, its lanes stride over the (2R+1)^2 window and add each valid
-// neighbour's vote floor(Ec[c] * Es[e2] / 2^15) into a per-warp shared histogram over d, and the
-// warp then takes the smallest d with the largest weight (Eq. 9). When no vote is positive the warp
-// scans the row outward, 32 positions per step, for the nearest valid pixels on each side.
+// one invalid pixel at a time; lane l owns window column l (and l + 32 when 2R+1 > 32) and walks
+// down its rows, summing each valid neighbour's vote floor(Ec[c] * Es[e2] / 2^15) in a register
+// while consecutive voters share a disparity and adding the run to a per-warp shared histogram over
+// d when the disparity changes (disparities are piecewise smooth, so runs are long and shared
+// atomics few). The warp then takes the smallest d with the largest weight (Eq. 9). When no vote
+// is positive the warp scans the row outward, 32 positions per step, for the nearest valid pixels
+// on each side.
 #include "bsm_internal.cuh"
 
 namespace bsm {
@@ -91,18 +94,28 @@ __global__ void __launch_bounds__(kTX *kTY) refine_kernel(const RefineArgs a) {
     const int x = x0 + tx, y = y0 + ty;
     for (int d = lane; d < a.dmax; d += 32) hist[d] = 0;
     __syncwarp();
-    const int cidx = (ty + R) * tp + tx + R;
-    const uint32_t labx = slab[cidx];
-    for (int j = lane; j < side * side; j += 32) {
-      const int wy = j / side, wx = j - wy * side;
-      const int ti = (ty + wy) * tp + (tx + wx);
-      const int dv = sd[ti];
-      if (dv >= 0) {
-        const int dx = wx - R, dy = wy - R;
-        const uint32_t c = lab_sad(labx, slab[ti]);
-        const uint32_t v = (sEc[c] * sEs[dx * dx + dy * dy]) >> kVoteShift;
-        if (v) atomicAdd(&hist[dv], v);
+    const uint32_t labx = slab[(ty + R) * tp + tx + R];
+    for (int wx = lane; wx < side; wx += 32) {
+      const int dx2 = (wx - R) * (wx - R);
+      const int16_t *dcol = sd + ty * tp + tx + wx;     // window row 0 of this column
+      const uint32_t *lcol = slab + ty * tp + tx + wx;
+      int run_d = -1;
+      uint32_t run = 0;
+      for (int wy = 0; wy < side; ++wy) {
+        const int dv = dcol[wy * tp];
+        if (dv >= 0) {
+          const int dy = wy - R;
+          const uint32_t c = lab_sad(labx, lcol[wy * tp]);
+          const uint32_t v = (sEc[c] * sEs[dx2 + dy * dy]) >> kVoteShift;
+          if (dv != run_d) {
+            if (run) atomicAdd(&hist[run_d], run);
+            run_d = dv;
+            run = 0;
+          }
+          run += v;
+        }
       }
+      if (run) atomicAdd(&hist[run_d], run);
     }
     __syncwarp();
     uint32_t bv = 0;
