@@ -116,6 +116,29 @@ bsm_status bsm_cost_aggregate_wta(bsm_ctx *ctx, const uint32_t *BL, const uint32
                                   const uint32_t *PhiR, int32_t w, int32_t h, int32_t dmax, int32_t *dispL,
                                   int32_t *dispR, uint16_t *costL_or_null, void *stream);
 
+/* Largest image, in pixels (width * height), that bsm_describe_noalloc accepts: 2^22. */
+#define BSM_NOALLOC_MAX_PIXELS 4194304
+
+/*
+ * bsm_describe for callers that cannot allocate device memory. The paper has no counterpart; this is
+ * a deployment variant of the same computation. bsm_describe grows its scratch with cudaMalloc the
+ * first time it sees a larger image; callers that capture streams into graphs, that run under a
+ * device-memory budget fixed up front, or that cannot accept the device synchronisation of an
+ * allocation use this call instead. It computes exactly what bsm_describe computes, with the same
+ * arguments, requirements and outputs, and allocates nothing:
+ *   - its scratch is one fixed array of BSM_NOALLOC_MAX_PIXELS colour words (16 MiB) in the
+ *     library's device code, which every GPU that loads the library holds until the process exits;
+ *   - images with w * h > BSM_NOALLOC_MAX_PIXELS are rejected with BSM_ERR_INVALID_ARG;
+ *   - the context must already exist (bsm_create allocates; create it during set-up);
+ *   - the first call on a device looks up that device's address of the array (a host-side lookup,
+ *     no allocation); make that first call before any stream capture;
+ *   - every call on a device shares the one array, and each call overwrites every word it reads,
+ *     so nothing needs clearing between calls; two calls that overlap on the GPU (different streams
+ *     without ordering) race on the array and give undefined results.
+ */
+bsm_status bsm_describe_noalloc(bsm_ctx *ctx, const uint8_t *rgb_dev, int32_t w, int32_t h, int32_t pitch_bytes,
+                                uint32_t *B_dev, uint32_t *Phi_dev, void *stream);
+
 /*
  * Left/right check and the voting refinement of Eq. 9-10 on the left map.
  *   valid(x) = x - dL(x) >= 0 and |dL(x) - dR(x - dL(x))| <= lr_tol. Valid pixels keep dL(x).

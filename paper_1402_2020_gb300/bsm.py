@@ -26,8 +26,10 @@ BSM_ERR_UNSUPPORTED = 5
 EXPORTED = (
     "bsm_create", "bsm_destroy", "bsm_describe", "bsm_cost_aggregate_wta", "bsm_refine", "bsm_match_host",
     "bsm_last_error", "bsm_status_string", "bsm_copy_color_table", "bsm_vote_tables", "bsm_validate_params",
-    "bsm_abi_version", "bsm_set_tuning", "bsm_get_tuning", "bsm_reserve",
+    "bsm_abi_version", "bsm_set_tuning", "bsm_get_tuning", "bsm_reserve", "bsm_describe_noalloc",
 )
+
+BSM_NOALLOC_MAX_PIXELS = 4194304
 
 
 class BsmError(RuntimeError):
@@ -92,6 +94,8 @@ def lib():
         L.bsm_set_tuning.restype = S
         L.bsm_get_tuning.argtypes = [P, ctypes.POINTER(bsm_tuning)]
         L.bsm_get_tuning.restype = S
+        L.bsm_describe_noalloc.argtypes = [P, P, I, I, I, P, P, P]
+        L.bsm_describe_noalloc.restype = S
         L.bsm_reserve.argtypes = [P, I, I]
         L.bsm_reserve.restype = S
         L.bsm_abi_version.argtypes = []
@@ -176,6 +180,12 @@ def bsm_destroy(ctx: int) -> None:
 
 def bsm_describe(ctx: int, rgb, w: int, h: int, pitch: int, B, Phi, stream=None) -> None:
     _check(lib().bsm_describe(ctx, _ptr(rgb), w, h, pitch, _ptr(B), _ptr(Phi), _stream(stream)), "bsm_describe")
+
+
+def bsm_describe_noalloc(ctx: int, rgb, w: int, h: int, pitch: int, B, Phi, stream=None) -> None:
+    """bsm_describe with its scratch in a fixed device array: allocates nothing (see include/bsm.h)."""
+    _check(lib().bsm_describe_noalloc(ctx, _ptr(rgb), w, h, pitch, _ptr(B), _ptr(Phi), _stream(stream)),
+           "bsm_describe_noalloc")
 
 
 def bsm_cost_aggregate_wta(ctx: int, BL, PhiL, BR, PhiR, w: int, h: int, dmax: int, dispL, dispR, cost=None,
