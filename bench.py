@@ -34,6 +34,7 @@ CONFIGS = {
                name="1390x1110 RGB8 pair, dmax 256, radiometric right view"),
     "c4": dict(w=3840, h=2160, dmax=256, radiometric=False, seed=4,
                name="3840x2160 RGB8 pair, dmax 256"),
+    "c3": dict(count=64, seed=3, name="batch of 64 uneven pairs: w U[320,1920], h U[240,1080], dmax {64,128,192,256}"),
 }
 N_BITS, WINDOW_S, AGG, VOTE_R = 256, 31, 5, 15
 PAIR_SEED = 11
@@ -53,6 +54,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cost-rows", type=int, default=0, help="rows per CTA of the cost kernel (0: heuristic)")
     ap.add_argument("--cost-popc-plain", type=int, default=0, help="1: plain popcount in the cost kernel")
+    ap.add_argument("--batch-rows", type=int, default=0, help="rows per task of the batched cost kernel (0: 64)")
     return ap.parse_args()
 
 
@@ -131,6 +133,9 @@ def oracle_sample(cfg, rows):
     from oracle import oracle
     from paper_1402_2020_gb300 import synth
 
+    if "count" in cfg:  # batch workload: sample the first pair of the batch
+        w, h, dmax, seed = synth.batch_shapes(cfg["count"], seed=cfg["seed"])[0]
+        cfg = dict(w=w, h=h, dmax=dmax, seed=seed, radiometric=False)
     left, right, _ = synth.stereo_pair(cfg["w"], cfg["h"], cfg["dmax"], cfg["seed"], cfg["radiometric"])
     pairs = synth.pair_table(N_BITS, WINDOW_S, seed=PAIR_SEED)
     y0 = cfg["h"] // 2 - rows // 2
@@ -157,6 +162,11 @@ def run_reference(args, cfg, world, rank):
     if rank != 0:
         return
     rows = 16
+    if "count" in cfg:
+        from paper_1402_2020_gb300 import synth
+
+        w0 = synth.batch_shapes(cfg["count"], seed=cfg["seed"])[0][0]
+        cfg = dict(cfg, w=w0)
     times = []
     for i in range(args.warmup + args.steps):
         dt, units = oracle_sample(cfg, rows)
@@ -175,12 +185,114 @@ def run_reference(args, cfg, world, rank):
     print(json.dumps(line), flush=True)
 
 
+def run_batch(args, cfg, world, rank, local):
+    """Config 3: one bsm_batch_run per step (persistent launches from a CUDA graph) against the same 64 pairs
+    through the per-pair calls (four C-ABI calls, six launches per pair)."""
+    import torch
+
+    from paper_1402_2020_gb300 import bsm, synth
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    shapes = synth.batch_shapes(cfg["count"], seed=cfg["seed"] + 1000 * rank)
+    pairs = synth.pair_table(N_BITS, WINDOW_S, seed=PAIR_SEED)
+    params = bsm.make_params(pairs, window_S=WINDOW_S, agg_window=AGG, dmax=256, vote_radius=VOTE_R)
+    ctx = bsm.bsm_create(params)
+    bsm.bsm_set_tuning(ctx, args.cost_rows, args.cost_popc_plain, args.batch_rows)
+    nw = N_BITS // 32
+    ts = []
+    for (w, h, dmax, seed) in shapes:
+        l, r, _ = synth.stereo_pair(w, h, dmax, seed)
+        t = {"w": w, "h": h, "dmax": dmax, "rgbL": torch.from_numpy(l).to(dev), "rgbR": torch.from_numpy(r).to(dev)}
+        for k in ("BL", "PhiL", "BR", "PhiR"):
+            t[k] = torch.empty((h, w, nw), dtype=torch.int32, device=dev)
+        for k in ("dispL", "dispR", "out"):
+            t[k] = torch.empty((h, w), dtype=torch.int32, device=dev)
+        ts.append(t)
+    descs = [bsm.pair_desc(t["rgbL"], t["rgbR"], t["w"], t["h"], 3 * t["w"], t["dmax"], t["BL"], t["PhiL"], t["BR"],
+                           t["PhiR"], t["dispL"], t["dispR"], t["out"]) for t in ts]
+    units = sum(t["w"] * t["h"] * t["dmax"] for t in ts)
+    stream = torch.cuda.Stream(device=dev)
+    s = stream.cuda_stream
+    bsm.bsm_reserve(ctx, max(t["w"] for t in ts), max(t["h"] for t in ts))
+    bsm.bsm_reserve_batch(ctx, sum(t["w"] * t["h"] for t in ts))
+
+    def batched():
+        bsm.bsm_batch_run(ctx, descs, s)
+
+    def plain():
+        for t in ts:
+            w, h, dmax = t["w"], t["h"], t["dmax"]
+            bsm.bsm_describe(ctx, t["rgbL"], w, h, 3 * w, t["BL"], t["PhiL"], s)
+            bsm.bsm_describe(ctx, t["rgbR"], w, h, 3 * w, t["BR"], t["PhiR"], s)
+            bsm.bsm_cost_aggregate_wta(ctx, t["BL"], t["PhiL"], t["BR"], t["PhiR"], w, h, dmax, t["dispL"],
+                                       t["dispR"], None, s)
+            bsm.bsm_refine(ctx, t["rgbL"], 3 * w, t["dispL"], t["dispR"], w, h, dmax, t["out"], s)
+
+    def timed(fn):
+        with torch.cuda.stream(stream):
+            for _ in range(max(3, args.warmup)):
+                fn()
+            torch.cuda.synchronize()
+            if world > 1:
+                torch.distributed.barrier()
+            e0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+            e1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+            for i in range(args.steps):
+                e0[i].record(stream)
+                fn()
+                e1[i].record(stream)
+            torch.cuda.synchronize()
+        return float(np.mean([a.elapsed_time(b) for a, b in zip(e0, e1)]))
+
+    clk = Clocks(local)
+    clk.start()
+    t_batch = timed(batched)
+    clocks = clk.stop()
+    t_plain = timed(plain)
+    assert bsm.bsm_last_error(ctx) == bsm.BSM_OK
+    if world > 1:
+        tt = torch.tensor([t_batch, t_plain], device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        t_batch, t_plain = float(tt[0]), float(tt[1])
+    value = world * units / (t_batch * 1e-3) / 1e9
+    line = {
+        "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_batch, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": cfg["name"], "n_bits": N_BITS, "agg_window": AGG, "pairs": len(ts),
+                   "pixels": sum(t["w"] * t["h"] for t in ts), "parallelism": f"replicas x{world}",
+                   "l2": "inputs larger than L2 (all 64 pairs' planes resident, about 7 GB)"},
+        "pairs_per_s": world * len(ts) / (t_batch * 1e-3),
+        "plain": {"value": world * units / (t_plain * 1e-3) / 1e9, "ms_per_step": t_plain,
+                  "pairs_per_s": world * len(ts) / (t_plain * 1e-3), "launches_per_step": 6 * len(ts)},
+        "batched_over_plain": t_plain / t_batch,
+        "gpu_launches": 4 * args.steps,
+        "clocks": clocks,
+        "tuning": bsm.bsm_get_tuning(ctx),
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    bsm.bsm_destroy(ctx)
+
+
+def torch_dist_done():
+    import torch.distributed as dist
+
+    dist.destroy_process_group()
+
+
 def main():
     args = parse()
     cfg = CONFIGS[args.config]
     world, rank, local = dist_init(args)
     if args.impl == "reference":
         run_reference(args, cfg, world, rank)
+        return
+    if args.config == "c3":
+        run_batch(args, cfg, world, rank, local)
+        if world > 1:
+            torch_dist_done()
         return
     import torch
 
@@ -193,7 +305,7 @@ def main():
     pairs = synth.pair_table(N_BITS, WINDOW_S, seed=PAIR_SEED)
     params = bsm.make_params(pairs, window_S=WINDOW_S, agg_window=AGG, dmax=dmax, vote_radius=VOTE_R)
     ctx = bsm.bsm_create(params)
-    bsm.bsm_set_tuning(ctx, args.cost_rows, args.cost_popc_plain)
+    bsm.bsm_set_tuning(ctx, args.cost_rows, args.cost_popc_plain, args.batch_rows)
     stream = torch.cuda.Stream(device=dev)
     s = stream.cuda_stream
     nw = N_BITS // 32

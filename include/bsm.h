@@ -116,6 +116,33 @@ bsm_status bsm_cost_aggregate_wta(bsm_ctx *ctx, const uint32_t *BL, const uint32
                                   const uint32_t *PhiR, int32_t w, int32_t h, int32_t dmax, int32_t *dispL,
                                   int32_t *dispR, uint16_t *costL_or_null, void *stream);
 
+/* One stereo pair of a batch: every pointer is a DEVICE pointer owned by the caller. */
+typedef struct {
+  const uint8_t *rgbL, *rgbR;  /* RGB views, h rows of pitch_bytes each */
+  int32_t w, h, pitch_bytes;   /* 1 <= w, h <= 16384, pitch_bytes >= 3 w */
+  int32_t dmax;                /* 1 <= dmax <= the context's dmax */
+  uint32_t *BL, *PhiL, *BR, *PhiR; /* [h][w][n_bits/32] descriptor and mask outputs, 16-byte aligned */
+  int32_t *dispL, *dispR;      /* [h][w] WTA outputs (left and right reference) */
+  int32_t *out;                /* [h][w] refined left map */
+} bsm_pair_desc;
+
+/* Largest number of pairs in one bsm_batch_run call. */
+#define BSM_MAX_BATCH 1024
+
+/*
+ * The whole method (describe both views, cost_aggregate_wta, refine) for `count` pairs of any sizes
+ * and dmax in four persistent launches, replayed from one CUDA graph the context captures on its
+ * first batch. Every pair's outputs are bit-identical to the per-pair calls. `pairs` is a HOST array
+ * read before the call returns. Work is asynchronous on `stream`. The context's batch scratch (the
+ * colour planes of all 2 * count views) grows here if too small (bsm_reserve_batch sizes it up
+ * front); the call waits until the previous batch's ticket table has been copied to the device.
+ * Errors: BSM_ERR_INVALID_ARG for a bad descriptor or count outside 1..BSM_MAX_BATCH.
+ */
+bsm_status bsm_batch_run(bsm_ctx *ctx, const bsm_pair_desc *pairs, int32_t count, void *stream);
+
+/* Size the batch scratch for batches of up to `total_pixels` pixels per view summed over the pairs. */
+bsm_status bsm_reserve_batch(bsm_ctx *ctx, int64_t total_pixels);
+
 /* Largest image, in pixels (width * height), that bsm_describe_noalloc accepts: 2^22. */
 #define BSM_NOALLOC_MAX_PIXELS 4194304
 
@@ -170,6 +197,9 @@ bsm_status bsm_match_host(bsm_ctx *ctx, const uint8_t *rgbL_host, const uint8_t 
  */
 bsm_status bsm_last_error(bsm_ctx *ctx);
 
+/* Name of the CUDA runtime error behind the context's most recent BSM_ERR_CUDA ("" if none). */
+const char *bsm_last_cuda_error(bsm_ctx *ctx);
+
 /* Static, human-readable name of a status code. */
 const char *bsm_status_string(bsm_status s);
 
@@ -195,7 +225,8 @@ typedef struct {
   int32_t cost_rows;       /* rows per CTA band of the cost/aggregation/WTA kernel: 0 or 8..512 */
   int32_t cost_popc_plain; /* 1: plain POPC per word in the cost kernel; 0: carry-save adder tree
                               (n_bits = 256 only) */
-  int32_t reserved[6];     /* must be zero */
+  int32_t batch_rows;      /* rows per task of bsm_batch_run's cost stage: 0 (64) or 8..512 */
+  int32_t reserved[5];     /* must be zero */
 } bsm_tuning;
 
 /* Set / read the context's launch shapes. Synchronous, host only. */

@@ -27,7 +27,9 @@ EXPORTED = (
     "bsm_create", "bsm_destroy", "bsm_describe", "bsm_cost_aggregate_wta", "bsm_refine", "bsm_match_host",
     "bsm_last_error", "bsm_status_string", "bsm_copy_color_table", "bsm_vote_tables", "bsm_validate_params",
     "bsm_abi_version", "bsm_set_tuning", "bsm_get_tuning", "bsm_reserve", "bsm_describe_noalloc",
+    "bsm_batch_run", "bsm_reserve_batch", "bsm_last_cuda_error",
 )
+BSM_MAX_BATCH = 1024
 
 BSM_NOALLOC_MAX_PIXELS = 4194304
 
@@ -54,8 +56,15 @@ class bsm_params(ctypes.Structure):
 
 
 class bsm_tuning(ctypes.Structure):
-    _fields_ = [("cost_rows", ctypes.c_int32), ("cost_popc_plain", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 6)]
+    _fields_ = [("cost_rows", ctypes.c_int32), ("cost_popc_plain", ctypes.c_int32), ("batch_rows", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 5)]
+
+
+class bsm_pair_desc(ctypes.Structure):
+    _fields_ = [("rgbL", ctypes.c_void_p), ("rgbR", ctypes.c_void_p), ("w", ctypes.c_int32), ("h", ctypes.c_int32),
+                ("pitch_bytes", ctypes.c_int32), ("dmax", ctypes.c_int32), ("BL", ctypes.c_void_p),
+                ("PhiL", ctypes.c_void_p), ("BR", ctypes.c_void_p), ("PhiR", ctypes.c_void_p),
+                ("dispL", ctypes.c_void_p), ("dispR", ctypes.c_void_p), ("out", ctypes.c_void_p)]
 
 
 _lib = None
@@ -96,6 +105,12 @@ def lib():
         L.bsm_get_tuning.restype = S
         L.bsm_describe_noalloc.argtypes = [P, P, I, I, I, P, P, P]
         L.bsm_describe_noalloc.restype = S
+        L.bsm_last_cuda_error.argtypes = [P]
+        L.bsm_last_cuda_error.restype = ctypes.c_char_p
+        L.bsm_batch_run.argtypes = [P, ctypes.POINTER(bsm_pair_desc), I, P]
+        L.bsm_batch_run.restype = S
+        L.bsm_reserve_batch.argtypes = [P, ctypes.c_int64]
+        L.bsm_reserve_batch.restype = S
         L.bsm_reserve.argtypes = [P, I, I]
         L.bsm_reserve.restype = S
         L.bsm_abi_version.argtypes = []
@@ -108,9 +123,14 @@ def status_name(s: int) -> str:
     return lib().bsm_status_string(int(s)).decode()
 
 
-def _check(s: int, where: str):
+def _check(s: int, where: str, ctx: int = 0):
     if s != BSM_OK:
-        raise BsmError(s, where)
+        detail = lib().bsm_last_cuda_error(ctx).decode() if ctx and s == BSM_ERR_CUDA else ""
+        raise BsmError(s, where + (f" [{detail}]" if detail else ""))
+
+
+def bsm_last_cuda_error(ctx: int) -> str:
+    return lib().bsm_last_cuda_error(ctx).decode()
 
 
 def _ptr(t) -> int:
@@ -179,30 +199,30 @@ def bsm_destroy(ctx: int) -> None:
 
 
 def bsm_describe(ctx: int, rgb, w: int, h: int, pitch: int, B, Phi, stream=None) -> None:
-    _check(lib().bsm_describe(ctx, _ptr(rgb), w, h, pitch, _ptr(B), _ptr(Phi), _stream(stream)), "bsm_describe")
+    _check(lib().bsm_describe(ctx, _ptr(rgb), w, h, pitch, _ptr(B), _ptr(Phi), _stream(stream)), "bsm_describe", ctx)
 
 
 def bsm_describe_noalloc(ctx: int, rgb, w: int, h: int, pitch: int, B, Phi, stream=None) -> None:
     """bsm_describe with its scratch in a fixed device array: allocates nothing (see include/bsm.h)."""
     _check(lib().bsm_describe_noalloc(ctx, _ptr(rgb), w, h, pitch, _ptr(B), _ptr(Phi), _stream(stream)),
-           "bsm_describe_noalloc")
+           "bsm_describe_noalloc", ctx)
 
 
 def bsm_cost_aggregate_wta(ctx: int, BL, PhiL, BR, PhiR, w: int, h: int, dmax: int, dispL, dispR, cost=None,
                            stream=None) -> None:
     _check(lib().bsm_cost_aggregate_wta(ctx, _ptr(BL), _ptr(PhiL), _ptr(BR), _ptr(PhiR), w, h, dmax, _ptr(dispL),
-                                        _ptr(dispR), _ptr(cost), _stream(stream)), "bsm_cost_aggregate_wta")
+                                        _ptr(dispR), _ptr(cost), _stream(stream)), "bsm_cost_aggregate_wta", ctx)
 
 
 def bsm_refine(ctx: int, rgbL, pitch: int, dispL, dispR, w: int, h: int, dmax: int, out, stream=None) -> None:
     _check(lib().bsm_refine(ctx, _ptr(rgbL), pitch, _ptr(dispL), _ptr(dispR), w, h, dmax, _ptr(out),
-                            _stream(stream)), "bsm_refine")
+                            _stream(stream)), "bsm_refine", ctx)
 
 
 def bsm_match_host(ctx: int, rgbL_host, rgbR_host, w: int, h: int, pitch: int, dmax: int, out_host,
                    stream=None) -> None:
     _check(lib().bsm_match_host(ctx, _ptr(rgbL_host), _ptr(rgbR_host), w, h, pitch, dmax, _ptr(out_host),
-                                _stream(stream)), "bsm_match_host")
+                                _stream(stream)), "bsm_match_host", ctx)
 
 
 def bsm_last_error(ctx: int) -> int:
@@ -221,17 +241,32 @@ def bsm_reserve(ctx: int, max_w: int, max_h: int) -> None:
     _check(lib().bsm_reserve(ctx, max_w, max_h), "bsm_reserve")
 
 
-def bsm_set_tuning(ctx: int, cost_rows: int = 0, cost_popc_plain: int = 0) -> None:
+def bsm_set_tuning(ctx: int, cost_rows: int = 0, cost_popc_plain: int = 0, batch_rows: int = 0) -> None:
     t = bsm_tuning()
     t.cost_rows = cost_rows
     t.cost_popc_plain = cost_popc_plain
+    t.batch_rows = batch_rows
     _check(lib().bsm_set_tuning(ctx, ctypes.byref(t)), "bsm_set_tuning")
 
 
 def bsm_get_tuning(ctx: int) -> dict:
     t = bsm_tuning()
     _check(lib().bsm_get_tuning(ctx, ctypes.byref(t)), "bsm_get_tuning")
-    return {"cost_rows": t.cost_rows, "cost_popc_plain": t.cost_popc_plain}
+    return {"cost_rows": t.cost_rows, "cost_popc_plain": t.cost_popc_plain, "batch_rows": t.batch_rows}
+
+
+def pair_desc(rgbL, rgbR, w, h, pitch, dmax, BL, PhiL, BR, PhiR, dispL, dispR, out) -> bsm_pair_desc:
+    return bsm_pair_desc(_ptr(rgbL), _ptr(rgbR), w, h, pitch, dmax, _ptr(BL), _ptr(PhiL), _ptr(BR), _ptr(PhiR),
+                         _ptr(dispL), _ptr(dispR), _ptr(out))
+
+
+def bsm_batch_run(ctx: int, descs, stream=None) -> None:
+    arr = (bsm_pair_desc * len(descs))(*descs)
+    _check(lib().bsm_batch_run(ctx, arr, len(descs), _stream(stream)), "bsm_batch_run", ctx)
+
+
+def bsm_reserve_batch(ctx: int, total_pixels: int) -> None:
+    _check(lib().bsm_reserve_batch(ctx, int(total_pixels)), "bsm_reserve_batch", ctx)
 
 
 class Matcher:

@@ -17,6 +17,11 @@ bsm_status from_cuda(cudaError_t e) {
   return BSM_ERR_CUDA;
 }
 
+bsm_status from_cuda(bsm_ctx *ctx, cudaError_t e) {
+  if (e != cudaSuccess) ctx->last_cuda = e;
+  return from_cuda(e);
+}
+
 bool size_ok(int32_t w, int32_t h) { return w >= 1 && h >= 1 && w <= 16384 && h <= 16384; }
 
 // sRGB transfer curve (IEC 61966-2-1) for the 256 channel values; the colour-table kernel takes
@@ -103,6 +108,12 @@ void bsm_destroy(bsm_ctx *ctx) {
   cudaFree(ctx->status);
   cudaFree(ctx->ws);
   cudaFree(ctx->plane);
+  if (ctx->batch_graph) cudaGraphExecDestroy(ctx->batch_graph);
+  if (ctx->batch_copied) cudaEventDestroy(ctx->batch_copied);
+  if (ctx->batch_capture) cudaStreamDestroy(ctx->batch_capture);
+  cudaFreeHost(ctx->batch_table_host);
+  cudaFree(ctx->batch_table_dev);
+  cudaFree(ctx->batch_plane);
   cudaSetDevice(prev);
   delete ctx;
 }
@@ -163,9 +174,9 @@ bsm_status bsm_describe(bsm_ctx *ctx, const uint8_t *rgb_dev, int32_t w, int32_t
   if (ctx == nullptr || rgb_dev == nullptr || B_dev == nullptr || Phi_dev == nullptr) return BSM_ERR_INVALID_ARG;
   if (!size_ok(w, h) || pitch_bytes < 3 * w || !aligned16(B_dev) || !aligned16(Phi_dev)) return BSM_ERR_INVALID_ARG;
   cudaError_t e = ensure_plane(ctx, (size_t)w * h);
-  if (e != cudaSuccess) return from_cuda(e);
-  return from_cuda(
-      bsm::launch_describe(ctx, rgb_dev, w, h, pitch_bytes, ctx->plane, B_dev, Phi_dev, (cudaStream_t)stream));
+  if (e != cudaSuccess) return from_cuda(ctx, e);
+  return from_cuda(ctx, bsm::launch_describe(ctx, rgb_dev, w, h, pitch_bytes, ctx->plane, B_dev, Phi_dev,
+                                             (cudaStream_t)stream));
 }
 
 bsm_status bsm_cost_aggregate_wta(bsm_ctx *ctx, const uint32_t *BL, const uint32_t *PhiL, const uint32_t *BR,
@@ -176,8 +187,8 @@ bsm_status bsm_cost_aggregate_wta(bsm_ctx *ctx, const uint32_t *BL, const uint32
     return BSM_ERR_INVALID_ARG;
   if (!size_ok(w, h) || dmax < 1 || dmax > ctx->p.dmax) return BSM_ERR_INVALID_ARG;
   if (!aligned16(BL) || !aligned16(PhiL) || !aligned16(BR) || !aligned16(PhiR)) return BSM_ERR_INVALID_ARG;
-  return from_cuda(bsm::launch_cost_wta(ctx, BL, PhiL, BR, PhiR, w, h, dmax, dispL, dispR, costL_or_null,
-                                        (cudaStream_t)stream));
+  return from_cuda(ctx, bsm::launch_cost_wta(ctx, BL, PhiL, BR, PhiR, w, h, dmax, dispL, dispR, costL_or_null,
+                                             (cudaStream_t)stream));
 }
 
 bsm_status bsm_refine(bsm_ctx *ctx, const uint8_t *rgbL_dev, int32_t pitch_bytes, const int32_t *dispL,
@@ -185,8 +196,8 @@ bsm_status bsm_refine(bsm_ctx *ctx, const uint8_t *rgbL_dev, int32_t pitch_bytes
   if (ctx == nullptr || rgbL_dev == nullptr || dispL == nullptr || dispR == nullptr || out == nullptr)
     return BSM_ERR_INVALID_ARG;
   if (!size_ok(w, h) || pitch_bytes < 3 * w || dmax < 1 || dmax > ctx->p.dmax) return BSM_ERR_INVALID_ARG;
-  return from_cuda(bsm::launch_refine(ctx, rgbL_dev, pitch_bytes, dispL, dispR, w, h, dmax, out,
-                                      (cudaStream_t)stream));
+  return from_cuda(ctx, bsm::launch_refine(ctx, rgbL_dev, pitch_bytes, dispL, dispR, w, h, dmax, out,
+                                           (cudaStream_t)stream));
 }
 
 bsm_status bsm_match_host(bsm_ctx *ctx, const uint8_t *rgbL_host, const uint8_t *rgbR_host, int32_t w, int32_t h,
@@ -236,12 +247,14 @@ bsm_status bsm_reserve(bsm_ctx *ctx, int32_t max_w, int32_t max_h) {
 
 bsm_status bsm_set_tuning(bsm_ctx *ctx, const bsm_tuning *t) {
   if (ctx == nullptr || t == nullptr) return BSM_ERR_INVALID_ARG;
-  for (int i = 0; i < 6; ++i)
+  for (int i = 0; i < 5; ++i)
     if (t->reserved[i] != 0) return BSM_ERR_INVALID_ARG;
   if (t->cost_rows != 0 && (t->cost_rows < 8 || t->cost_rows > 512)) return BSM_ERR_INVALID_ARG;
+  if (t->batch_rows != 0 && (t->batch_rows < 8 || t->batch_rows > 512)) return BSM_ERR_INVALID_ARG;
   if (t->cost_popc_plain != 0 && t->cost_popc_plain != 1) return BSM_ERR_INVALID_ARG;
   ctx->cost_rows = t->cost_rows;
   ctx->cost_plain_popc = t->cost_popc_plain;
+  ctx->batch_rows = t->batch_rows;
   return BSM_OK;
 }
 
@@ -250,6 +263,7 @@ bsm_status bsm_get_tuning(bsm_ctx *ctx, bsm_tuning *t) {
   std::memset(t, 0, sizeof(*t));
   t->cost_rows = ctx->cost_rows;
   t->cost_popc_plain = ctx->cost_plain_popc;
+  t->batch_rows = ctx->batch_rows;
   return BSM_OK;
 }
 
@@ -261,6 +275,11 @@ bsm_status bsm_last_error(bsm_ctx *ctx) {
   if (e == cudaSuccess) e = cudaMemset(ctx->status, 0, sizeof(uint32_t));
   if (e != cudaSuccess) return BSM_ERR_CUDA;
   return (bsm_status)v;
+}
+
+const char *bsm_last_cuda_error(bsm_ctx *ctx) {
+  if (ctx == nullptr || ctx->last_cuda == cudaSuccess) return "";
+  return cudaGetErrorName(ctx->last_cuda);
 }
 
 bsm_status bsm_copy_color_table(bsm_ctx *ctx, uint32_t *dst_dev, void *stream) {

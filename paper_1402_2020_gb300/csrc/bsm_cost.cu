@@ -145,15 +145,15 @@ struct Layout {
   static constexpr bool kTma = NW >= 4;  // 16-byte granules: every row segment is a legal bulk copy
   int ocols;                             // staged other-view columns including guards
   int stage_words;                       // one stage: ref B, ref Phi, other row
-  __device__ __host__ explicit Layout(int dmax) {
-    ocols = 32 + dmax - 1 + 2 * kPad;
+  __device__ __host__ explicit Layout(int nd) {
+    ocols = 32 + nd - 1 + 2 * kPad;
     stage_words = (2 * 32 * NW + ocols * NW + 3) & ~3;  // 16-byte multiple: every stage stays aligned
   }
 };
 
 template <int NW>
-size_t cost_smem_bytes(int dmax, int win, int nthreads) {
-  const Layout<NW> L(dmax);
+size_t cost_smem_bytes(int nd, int win, int nthreads) {
+  const Layout<NW> L(nd);
   size_t b = 2 * sizeof(uint64_t);                 // mbarriers
   b += 2 * (size_t)L.stage_words * 4;              // two stages
   b += 2 * 32 * 32 * 4;                            // keys, double-buffered
@@ -161,30 +161,41 @@ size_t cost_smem_bytes(int dmax, int win, int nthreads) {
   return b;
 }
 
-template <int NW, int WIN, int DIR, bool CSA>
-__device__ __forceinline__ void cost_rows(const CostArgs &a, uint8_t *smem_raw) {
+// One band of one reference view: output rows [yb, ye) of the columns whose lane is an output lane
+// (lane 0 sits at column x0), for the disparities [dbase, dbase + 8 * warps).
+struct CostTask {
+  const uint32_t *Bref, *Phiref, *Both;
+  int32_t *disp;
+  uint16_t *cost;  // optional cost volume (left reference only), or nullptr
+  int w, h, dmax;
+  int x0, yb, ye, dbase;
+};
+
+// Runs one task. `g` counts the rows this CTA has staged so far (it selects the stage buffer and the
+// mbarrier phase, and carries over between the tasks of a persistent CTA). Returns false, in every
+// thread, if a bounded wait gave up.
+template <int NW, int WIN, int DIR, bool CSA, bool ATOMIC>
+__device__ __forceinline__ bool cost_task(const CostTask &t, uint8_t *smem_raw, uint32_t &g, uint32_t *status) {
   constexpr int R = WIN / 2;
-  constexpr int OUTC = 32 - 2 * R;
   constexpr int NBITS = 32 * NW;
-  const Layout<NW> L(a.dmax);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+  const int nd = nwarps * kDC;
+  const Layout<NW> L(nd);
   uint64_t *full = reinterpret_cast<uint64_t *>(smem_raw);
   uint32_t *stages = reinterpret_cast<uint32_t *>(smem_raw + 16);
   uint32_t *keys = stages + 2 * L.stage_words;     // [2][32][32]
   uint4 *ring = reinterpret_cast<uint4 *>(keys + 2 * 32 * 32);
 
-  const uint32_t *__restrict__ Bref = a.B[DIR];
-  const uint32_t *__restrict__ Phiref = a.Phi[DIR];
-  const uint32_t *__restrict__ Both = a.O[DIR];
-  int32_t *__restrict__ disp = a.disp[DIR];
-  const int w = a.w, h = a.h, dmax = a.dmax;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
-  const int x0 = blockIdx.x * OUTC - R;
-  const int x = x0 + lane;
-  const int yb = blockIdx.y * a.rows;
-  const int ye = min(h, yb + a.rows);
-  const int d0 = warp * kDC;
-  const int ox0 = DIR == 0 ? x0 - (dmax - 1) : x0;  // first staged other-view column (before guards)
-  const int nocols = 32 + dmax - 1;
+  const uint32_t *__restrict__ Bref = t.Bref;
+  const uint32_t *__restrict__ Phiref = t.Phiref;
+  const uint32_t *__restrict__ Both = t.Both;
+  const int w = t.w, h = t.h, dmax = t.dmax;
+  const int x0 = t.x0, x = x0 + lane;
+  const int yb = t.yb, ye = t.ye;
+  const int d0 = t.dbase + warp * kDC;               // this warp's first disparity
+  // first staged other-view column (before guards) and the count of staged columns
+  const int ox0 = DIR == 0 ? x0 - (t.dbase + nd - 1) : x0 + t.dbase;
+  const int nocols = 32 + nd - 1;
   const bool col_in = x >= 0 && x < w;
   const bool out_lane = lane >= R && lane < 32 - R && col_in;
   const int q = NW == 8 ? (lane >> 2) & 1 : 0;
@@ -229,40 +240,43 @@ __device__ __forceinline__ void cost_rows(const CostArgs &a, uint8_t *smem_raw) 
         st[64 * NW + kPad * NW + i] = __ldg(Both + (size_t)y * w * NW + (ptrdiff_t)ox0 * NW + i);
     }
   };
-  auto reduce_keys = [&](int it) {  // warp 0: minimum key over the warps -> disparity of row yo
+  auto reduce_keys = [&](int it) {  // warp 0: minimum key over the warps -> the row's result
     const int yo = y_first + it - R;
     const uint32_t *kb = keys + (it & 1) * 1024;
     uint32_t best = kb[lane];
     for (int k = 1; k < nwarps; ++k) best = min(best, kb[k * 32 + lane]);
-    if (out_lane) disp[(size_t)yo * w + x] = (int32_t)(best & 1023u);
+    if (out_lane) {
+      if constexpr (ATOMIC) atomicMin(reinterpret_cast<unsigned *>(t.disp) + (size_t)yo * w + x, best);
+      else t.disp[(size_t)yo * w + x] = (int32_t)(best & 1023u);
+    }
   };
 
-  if (tid == 0) {
-    mbar_init(&full[0], 1);
-    mbar_init(&full[1], 1);
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
   if constexpr (WIN > 1) {
     for (int s = 0; s < WIN; ++s) ring[s * blockDim.x + tid] = make_uint4(0, 0, 0, 0);
   }
-  __syncthreads();
+  __syncthreads();  // the previous task is done with every buffer
   if constexpr (Layout<NW>::kTma) {
-    if (tid == 0) issue(y_first, 0);
+    if (tid == 0) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      issue(y_first, g & 1);
+    }
   } else {
-    load_plain(y_first, 0);
+    load_plain(y_first, g & 1);
   }
 
   uint32_t V[kDP] = {0, 0, 0, 0};
   for (int it = 0; it < n_it; ++it) {
-    const int y = y_first + it, s = it & 1;
+    const int y = y_first + it;
+    const uint32_t G = g + (uint32_t)it;
+    const int s = (int)(G & 1u);
     bool ok = true;
-    if constexpr (Layout<NW>::kTma) ok = mbar_wait(&full[s], (uint32_t)(it >> 1) & 1u);
+    if constexpr (Layout<NW>::kTma) ok = mbar_wait(&full[s], (G >> 1) & 1u);
     if (!__syncthreads_and(ok)) {
       if (tid == 0) {
-        atomicCAS(a.status, 0u, (uint32_t)BSM_ERR_TIMEOUT);
-        if (Layout<NW>::kTma) mbar_wait(&full[s], (uint32_t)(it >> 1) & 1u);  // let the late copy land
+        atomicCAS(status, 0u, (uint32_t)BSM_ERR_TIMEOUT);
+        if (Layout<NW>::kTma) mbar_wait(&full[s], (G >> 1) & 1u);  // let the late copy land
       }
-      return;
+      return false;
     }
     // Every thread finished iteration it - 1: its buffer and its keys may be reused.
     if (it + 1 < n_it) {
@@ -284,7 +298,8 @@ __device__ __forceinline__ void cost_rows(const CostArgs &a, uint8_t *smem_raw) 
       uint32_t b[NW], m[NW];
       load_desc<NW>(st + lane * NW, q, b);
       load_desc<NW>(st + 32 * NW + lane * NW, q, m);
-      const uint32_t *ob = st + 64 * NW + (kPad + (DIR == 0 ? lane + dmax - 1 - d0 : lane + d0)) * NW;
+      const uint32_t *ob =
+          st + 64 * NW + (kPad + (DIR == 0 ? lane + nd - 1 - warp * kDC : lane + warp * kDC)) * NW;
       if (fast_cols) {
 #pragma unroll
         for (int dd = 0; dd < kDC; ++dd) {
@@ -332,43 +347,132 @@ __device__ __forceinline__ void cost_rows(const CostArgs &a, uint8_t *smem_raw) 
           A = __shfl_up_sync(0xFFFFFFFFu, s1, 2) + s1 + __shfl_down_sync(0xFFFFFFFFu, V[j], 2);
         } else {
 #pragma unroll
-          for (int t = 1; t <= R; ++t)
-            A += __shfl_up_sync(0xFFFFFFFFu, V[j], t) + __shfl_down_sync(0xFFFFFFFFu, V[j], t);
+          for (int u = 1; u <= R; ++u)
+            A += __shfl_up_sync(0xFFFFFFFFu, V[j], u) + __shfl_down_sync(0xFFFFFFFFu, V[j], u);
         }
         const int de = d0 + 2 * j;
         const uint32_t ae = A & 0xFFFFu, ao = A >> 16;
         if (de < dmax) key = min(key, (ae << 10) | (uint32_t)de);
         if (de + 1 < dmax) key = min(key, (ao << 10) | (uint32_t)(de + 1));
-        if (DIR == 0 && a.cost != nullptr && out_lane) {
-          uint16_t *cp = a.cost + ((size_t)yo * w + x) * dmax;
+        if (DIR == 0 && t.cost != nullptr && out_lane) {
+          uint16_t *cp = t.cost + ((size_t)yo * w + x) * dmax;
           if (de < dmax) cp[de] = (uint16_t)ae;
           if (de + 1 < dmax) cp[de + 1] = (uint16_t)ao;
         }
       }
-      keys[s * 1024 + warp * 32 + lane] = key;
+      keys[(it & 1) * 1024 + warp * 32 + lane] = key;
     }
   }
   __syncthreads();
   if (warp == 0 && y_first + n_it - 1 - R >= yb) reduce_keys(n_it - 1);
+  g += (uint32_t)n_it;
+  return true;
 }
 
+__device__ __forceinline__ void init_barriers(uint8_t *smem_raw) {
+  if (threadIdx.x == 0) {
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem_raw);
+    mbar_init(&full[0], 1);
+    mbar_init(&full[1], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+}
+
+// One CTA per (column block, row band, reference view); its warps cover all of [0, dmax).
 template <int NW, int WIN, bool CSA>
 __global__ void __launch_bounds__(1024, 1) cost_wta_kernel(const CostArgs a) {
   extern __shared__ __align__(16) uint8_t smem_raw[];
-  if (blockIdx.z == 0) cost_rows<NW, WIN, 0, CSA>(a, smem_raw);
-  else cost_rows<NW, WIN, 1, CSA>(a, smem_raw);
+  constexpr int OUTC = 32 - 2 * (WIN / 2);
+  init_barriers(smem_raw);
+  const int dir = blockIdx.z;
+  CostTask t;
+  t.Bref = dir == 0 ? a.B[0] : a.B[1];
+  t.Phiref = dir == 0 ? a.Phi[0] : a.Phi[1];
+  t.Both = dir == 0 ? a.O[0] : a.O[1];
+  t.disp = dir == 0 ? a.disp[0] : a.disp[1];
+  t.cost = dir == 0 ? a.cost : nullptr;
+  t.w = a.w; t.h = a.h; t.dmax = a.dmax;
+  t.x0 = blockIdx.x * OUTC - WIN / 2;
+  t.yb = blockIdx.y * a.rows;
+  t.ye = min(a.h, t.yb + a.rows);
+  t.dbase = 0;
+  uint32_t g = 0;
+  if (dir == 0) cost_task<NW, WIN, 0, CSA, false>(t, smem_raw, g, a.status);
+  else cost_task<NW, WIN, 1, CSA, false>(t, smem_raw, g, a.status);
+}
+
+// Persistent batch kernel: 8 warps (64 disparities) per CTA; every CTA takes tasks
+// (pair, reference view, row band, column block, disparity range) from the batch's ticket counter and
+// merges its partial minimum into the pair's disparity buffers with atomicMin on (A << 10 | d) keys.
+template <int NW, int WIN, bool CSA>
+__global__ void __launch_bounds__(256, 2) cost_batch_kernel(BatchHeader *hdr, const BatchPair *pairs,
+                                                             uint32_t *status) {
+  extern __shared__ __align__(16) uint8_t smem_raw[];
+  constexpr int OUTC = 32 - 2 * (WIN / 2);
+  __shared__ int s_ticket;
+  init_barriers(smem_raw);
+  const int total = hdr->total[2], count = hdr->count, band = hdr->band_rows;
+  uint32_t g = 0;
+  for (;;) {
+    __syncthreads();
+    if (threadIdx.x == 0) s_ticket = (int)atomicAdd(&hdr->counters[2], 1u);
+    __syncthreads();
+    const int tk = s_ticket;
+    if (tk >= total) break;
+    int lo = 0, hi = count - 1;  // last pair whose first ticket <= tk
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (pairs[mid].cost_base <= tk) lo = mid;
+      else hi = mid - 1;
+    }
+    const BatchPair &p = pairs[lo];
+    int r = tk - p.cost_base;
+    const int dr = r % p.cost_dr; r /= p.cost_dr;
+    const int cb = r % p.cost_cb; r /= p.cost_cb;
+    const int bd = r % p.cost_bands; r /= p.cost_bands;
+    const int dir = r;
+    CostTask t;
+    t.Bref = p.B[dir]; t.Phiref = p.Phi[dir]; t.Both = p.B[1 - dir];
+    t.disp = p.disp[dir]; t.cost = nullptr;
+    t.w = p.w; t.h = p.h; t.dmax = p.dmax;
+    t.x0 = cb * OUTC - WIN / 2;
+    t.yb = bd * band;
+    t.ye = min(p.h, t.yb + band);
+    t.dbase = dr * 8 * (int)(blockDim.x >> 5);
+    const bool ok = dir == 0 ? cost_task<NW, WIN, 0, CSA, true>(t, smem_raw, g, status)
+                             : cost_task<NW, WIN, 1, CSA, true>(t, smem_raw, g, status);
+    if (!ok) return;
+  }
 }
 
 template <int NW, int WIN, bool CSA>
 cudaError_t launch_t(const CostArgs &a, cudaStream_t s) {
   constexpr int OUTC = 32 - 2 * (WIN / 2);
   const int nwarps = (a.dmax + kDC - 1) / kDC;
-  const size_t smem = cost_smem_bytes<NW>(a.dmax, WIN, nwarps * 32);
+  const size_t smem = cost_smem_bytes<NW>(nwarps * kDC, WIN, nwarps * 32);
   cudaError_t e = cudaFuncSetAttribute(cost_wta_kernel<NW, WIN, CSA>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;
   dim3 grid((a.w + OUTC - 1) / OUTC, (a.h + a.rows - 1) / a.rows, 2);
   cost_wta_kernel<NW, WIN, CSA><<<grid, nwarps * 32, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <int NW, int WIN, bool CSA>
+cudaError_t launch_batch_t(BatchHeader *hdr, const BatchPair *pairs, uint32_t *status, int grid, bool prepare,
+                           int *grid_out, cudaStream_t s) {
+  constexpr int kThreads = kBatchDisp / kDC * 32;
+  const size_t smem = cost_smem_bytes<NW>(kBatchDisp, WIN, kThreads);
+  if (prepare) {
+    cudaError_t e = cudaFuncSetAttribute(cost_batch_kernel<NW, WIN, CSA>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cost_batch_kernel<NW, WIN, CSA>, kThreads, smem);
+    *grid_out = max(1, per_sm) * grid;  // `grid` carries the SM count when preparing
+    return e;
+  }
+  cost_batch_kernel<NW, WIN, CSA><<<grid, kThreads, smem, s>>>(hdr, pairs, status);
   return cudaGetLastError();
 }
 
@@ -379,6 +483,33 @@ cudaError_t launch_win(int win, const CostArgs &a, cudaStream_t s) {
     case 3: return launch_t<NW, 3, CSA>(a, s);
     case 5: return launch_t<NW, 5, CSA>(a, s);
     case 7: return launch_t<NW, 7, CSA>(a, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <int NW, bool CSA>
+cudaError_t launch_batch_win(int win, BatchHeader *hdr, const BatchPair *pairs, uint32_t *status, int grid,
+                             bool prepare, int *grid_out, cudaStream_t s) {
+  switch (win) {
+    case 1: return launch_batch_t<NW, 1, CSA>(hdr, pairs, status, grid, prepare, grid_out, s);
+    case 3: return launch_batch_t<NW, 3, CSA>(hdr, pairs, status, grid, prepare, grid_out, s);
+    case 5: return launch_batch_t<NW, 5, CSA>(hdr, pairs, status, grid, prepare, grid_out, s);
+    case 7: return launch_batch_t<NW, 7, CSA>(hdr, pairs, status, grid, prepare, grid_out, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t cost_batch_dispatch(const bsm_ctx *ctx, BatchHeader *hdr, const BatchPair *pairs, int grid, bool prepare,
+                                int *grid_out, cudaStream_t s) {
+  const int win = ctx->p.agg_window;
+  switch (ctx->nw) {
+    case 1: return launch_batch_win<1, false>(win, hdr, pairs, ctx->status, grid, prepare, grid_out, s);
+    case 2: return launch_batch_win<2, false>(win, hdr, pairs, ctx->status, grid, prepare, grid_out, s);
+    case 4: return launch_batch_win<4, false>(win, hdr, pairs, ctx->status, grid, prepare, grid_out, s);
+    case 8:
+      return ctx->cost_plain_popc
+                 ? launch_batch_win<8, false>(win, hdr, pairs, ctx->status, grid, prepare, grid_out, s)
+                 : launch_batch_win<8, true>(win, hdr, pairs, ctx->status, grid, prepare, grid_out, s);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -416,6 +547,14 @@ cudaError_t launch_cost_wta(const bsm_ctx *ctx, const uint32_t *BL, const uint32
                                   : launch_win<8, true>(ctx->p.agg_window, a, s);
     default: return cudaErrorInvalidValue;
   }
+}
+
+cudaError_t prepare_cost_batch(const bsm_ctx *ctx, int *grid) {
+  return cost_batch_dispatch(ctx, nullptr, nullptr, ctx->sms, true, grid, nullptr);
+}
+
+cudaError_t launch_cost_batch(const bsm_ctx *ctx, BatchHeader *hdr, const BatchPair *pairs, int grid, cudaStream_t s) {
+  return cost_batch_dispatch(ctx, hdr, pairs, grid, false, nullptr, s);
 }
 
 }  // namespace bsm

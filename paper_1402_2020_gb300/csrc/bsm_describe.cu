@@ -69,10 +69,12 @@ __device__ __forceinline__ void cp_async4(uint32_t *dst, const uint32_t *src) {
                : "memory");
 }
 
+// One 32 x kTY block of pixels with top-left corner (x0, y0). Contains one CTA-wide barrier, which
+// every thread of the CTA reaches.
 template <int NW>
-__global__ void __launch_bounds__(kTY * 32) describe_kernel(const DescribeArgs a, const __grid_constant__ PairTable pt) {
+__device__ __forceinline__ void describe_tile(const DescribeArgs &a, const PairTable &pt, int x0, int y0,
+                                              uint32_t *smem) {
   using L = WLayout<NW>;
-  extern __shared__ __align__(16) uint32_t smem[];
   const int halo = a.halo;
   const int tp = 32 + 2 * halo;
   const int th = kTY + 2 * halo;
@@ -80,7 +82,6 @@ __global__ void __launch_bounds__(kTY * 32) describe_kernel(const DescribeArgs a
   uint32_t *wbuf = tile + ((th * tp + 3) & ~3);
 
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int x0 = blockIdx.x * 32, y0 = blockIdx.y * kTY;
 
   // 0. colour tile with clamped coordinates
   for (int i = threadIdx.x; i < th * tp; i += blockDim.x) {
@@ -93,7 +94,7 @@ __global__ void __launch_bounds__(kTY * 32) describe_kernel(const DescribeArgs a
   __syncthreads();
 
   const int y = y0 + warp;
-  if (y >= a.h) return;  // whole warp; no CTA-wide barrier follows
+  if (y >= a.h) return;  // whole warp; no CTA-wide barrier follows in this tile
   uint32_t *wb = wbuf + warp * 32 * L::kStride;
   const int x = x0 + lane;
 
@@ -209,6 +210,68 @@ __global__ void __launch_bounds__(kTY * 32) describe_kernel(const DescribeArgs a
 }
 
 template <int NW>
+__global__ void __launch_bounds__(kTY * 32) describe_kernel(const DescribeArgs a, const __grid_constant__ PairTable pt) {
+  extern __shared__ __align__(16) uint32_t smem[];
+  describe_tile<NW>(a, pt, blockIdx.x * 32, blockIdx.y * kTY, smem);
+}
+
+// Binary search: the last pair whose first ticket of the stage is <= tk.
+template <typename F>
+__device__ __forceinline__ int find_pair(const BatchPair *pairs, int count, int tk, F base) {
+  int lo = 0, hi = count - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (base(pairs[mid]) <= tk) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+// Batched pre-pass: every row of every view of the batch (grid-stride). Also sets the pair's WTA
+// key buffers to all ones, ready for the batched cost kernel's atomicMin merge.
+__global__ void __launch_bounds__(256) color_plane_batch_kernel(const BatchHeader *hdr, const BatchPair *pairs,
+                                                                const uint32_t *__restrict__ table) {
+  const int total = hdr->total[0], count = hdr->count;
+  for (int tk = blockIdx.x; tk < total; tk += gridDim.x) {
+    const int i = find_pair(pairs, count, tk, [](const BatchPair &p) { return p.pre_base; });
+    const BatchPair &p = pairs[i];
+    const int r = tk - p.pre_base, view = r / p.h, y = r - view * p.h;
+    const uint8_t *row = p.rgb[view] + (size_t)y * p.pitch;
+    uint32_t *plane = p.plane[view] + (size_t)y * p.w;
+    int32_t *keys = p.disp[view] + (size_t)y * p.w;
+    for (int x = threadIdx.x; x < p.w; x += blockDim.x) {
+      const uint8_t *px = row + 3 * x;
+      plane[x] = __ldg(table + (((uint32_t)px[0] << 16) | ((uint32_t)px[1] << 8) | (uint32_t)px[2]));
+      keys[x] = -1;
+    }
+  }
+}
+
+// Batched describe: persistent CTAs take (pair, view, tile) tickets.
+template <int NW>
+__global__ void __launch_bounds__(kTY * 32) describe_batch_kernel(BatchHeader *hdr, const BatchPair *pairs, int k,
+                                                                  int halo, const __grid_constant__ PairTable pt) {
+  extern __shared__ __align__(16) uint32_t smem[];
+  __shared__ int s_ticket;
+  const int total = hdr->total[1], count = hdr->count;
+  for (;;) {
+    __syncthreads();  // the previous tile is done with shared memory
+    if (threadIdx.x == 0) s_ticket = (int)atomicAdd(&hdr->counters[1], 1u);
+    __syncthreads();
+    const int tk = s_ticket;
+    if (tk >= total) return;
+    const BatchPair &p = pairs[find_pair(pairs, count, tk, [](const BatchPair &q) { return q.desc_base; })];
+    int r = tk - p.desc_base;
+    const int per_view = p.desc_tx * p.desc_ty;
+    const int view = r / per_view;
+    r -= view * per_view;
+    const int ty = r / p.desc_tx, tx = r - ty * p.desc_tx;
+    const DescribeArgs a{p.plane[view], p.B[view], p.Phi[view], p.w, p.h, k, halo};
+    describe_tile<NW>(a, pt, tx * 32, ty * kTY, smem);
+  }
+}
+
+template <int NW>
 size_t describe_smem(int halo) {
   const int tp = 32 + 2 * halo, th = kTY + 2 * halo;
   return sizeof(uint32_t) * (size_t)(((th * tp + 3) & ~3) + kTY * 32 * WLayout<NW>::kStride);
@@ -224,7 +287,65 @@ cudaError_t launch_nw(const DescribeArgs &a, const PairTable &pt, cudaStream_t s
   return cudaGetLastError();
 }
 
+template <int NW>
+cudaError_t prepare_batch_nw(int halo, int sms, int *grid) {
+  const size_t smem = describe_smem<NW>(halo);
+  cudaError_t e =
+      cudaFuncSetAttribute(describe_batch_kernel<NW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, describe_batch_kernel<NW>, kTY * 32, smem);
+  *grid = max(1, per_sm) * sms;
+  return e;
+}
+
+template <int NW>
+cudaError_t launch_batch_nw(BatchHeader *hdr, const BatchPair *pairs, int k, int halo, const PairTable &pt, int grid,
+                            cudaStream_t s) {
+  describe_batch_kernel<NW><<<grid, kTY * 32, describe_smem<NW>(halo), s>>>(hdr, pairs, k, halo, pt);
+  return cudaGetLastError();
+}
+
+PairTable make_pair_table(const bsm_ctx *ctx) {
+  const int tp = 32 + 2 * ctx->halo;
+  PairTable pt{};
+  for (int i = 0; i < ctx->p.n_bits; ++i) {
+    const int8_t *q = ctx->pairs + 4 * i;
+    pt.off[i][0] = q[1] * tp + q[0];
+    pt.off[i][1] = q[3] * tp + q[2];
+  }
+  return pt;
+}
+
 }  // namespace
+
+cudaError_t launch_color_plane_batch(const bsm_ctx *ctx, const BatchHeader *hdr, const BatchPair *pairs, int grid,
+                                     cudaStream_t s) {
+  color_plane_batch_kernel<<<grid, 256, 0, s>>>(hdr, pairs, ctx->color_table);
+  return cudaGetLastError();
+}
+
+cudaError_t prepare_describe_batch(const bsm_ctx *ctx, int *grid) {
+  switch (ctx->nw) {
+    case 1: return prepare_batch_nw<1>(ctx->halo, ctx->sms, grid);
+    case 2: return prepare_batch_nw<2>(ctx->halo, ctx->sms, grid);
+    case 4: return prepare_batch_nw<4>(ctx->halo, ctx->sms, grid);
+    case 8: return prepare_batch_nw<8>(ctx->halo, ctx->sms, grid);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_describe_batch(const bsm_ctx *ctx, BatchHeader *hdr, const BatchPair *pairs, int grid,
+                                  cudaStream_t s) {
+  const PairTable pt = make_pair_table(ctx);
+  switch (ctx->nw) {
+    case 1: return launch_batch_nw<1>(hdr, pairs, ctx->mask_rank, ctx->halo, pt, grid, s);
+    case 2: return launch_batch_nw<2>(hdr, pairs, ctx->mask_rank, ctx->halo, pt, grid, s);
+    case 4: return launch_batch_nw<4>(hdr, pairs, ctx->mask_rank, ctx->halo, pt, grid, s);
+    case 8: return launch_batch_nw<8>(hdr, pairs, ctx->mask_rank, ctx->halo, pt, grid, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
 
 cudaError_t launch_color_plane(const bsm_ctx *ctx, const uint8_t *rgb, int w, int h, int pitch, uint32_t *plane,
                                cudaStream_t s) {
@@ -236,13 +357,7 @@ cudaError_t launch_color_plane(const bsm_ctx *ctx, const uint8_t *rgb, int w, in
 cudaError_t launch_describe_plane(const bsm_ctx *ctx, const uint32_t *plane, int w, int h, uint32_t *B,
                                   uint32_t *Phi, cudaStream_t s) {
   DescribeArgs a{plane, B, Phi, w, h, ctx->mask_rank, ctx->halo};
-  const int tp = 32 + 2 * ctx->halo;
-  PairTable pt{};
-  for (int i = 0; i < ctx->p.n_bits; ++i) {
-    const int8_t *q = ctx->pairs + 4 * i;
-    pt.off[i][0] = q[1] * tp + q[0];
-    pt.off[i][1] = q[3] * tp + q[2];
-  }
+  const PairTable pt = make_pair_table(ctx);
   switch (ctx->nw) {
     case 1: return launch_nw<1>(a, pt, s);
     case 2: return launch_nw<2>(a, pt, s);

@@ -27,6 +27,33 @@ struct PairTable {
   int32_t off[kMaxBits][2];
 };
 
+// ---------------------------------------------------------------- batched execution
+
+constexpr int kMaxBatch = 1024;   // pairs per bsm_batch_run call
+constexpr int kBatchDisp = 64;    // disparities per CTA of the batched cost kernel (8 warps)
+
+// One pair of a batch, as the batched kernels see it (built on the host, copied to the device).
+struct BatchPair {
+  const uint8_t *rgb[2];
+  uint32_t *B[2], *Phi[2];
+  int32_t *disp[2];
+  int32_t *out;
+  uint32_t *plane[2];  // colour planes in the batch scratch
+  int w, h, pitch, dmax;
+  int pre_base, desc_base, cost_base, ref_base;  // first ticket of this pair in each stage
+  int desc_tx, desc_ty;                          // describe tiles per view
+  int cost_cb, cost_bands, cost_dr;              // column blocks, row bands, disparity ranges
+  int ref_tx, ref_ty;                            // refine tiles
+};
+
+struct BatchHeader {
+  int count;
+  int total[4];        // tickets per stage: pre-pass rows, describe tiles, cost tasks, refine tiles
+  int band_rows;       // rows per cost task
+  unsigned counters[4];  // next ticket per stage; the host writes zeros with every batch
+  int pad[6];
+};
+
 }  // namespace bsm
 
 struct bsm_ctx {
@@ -46,6 +73,19 @@ struct bsm_ctx {
   // Scratch: packed colour plane of the describe pre-pass (grown on demand, or by bsm_reserve).
   uint32_t *plane = nullptr;
   size_t plane_px = 0;
+  int batch_rows = 0;       // rows per task of the batched cost kernel
+  // Batched execution (bsm_batch_run).
+  int sms = 0;
+  uint8_t *batch_table_host = nullptr;  // pinned ticket table
+  uint8_t *batch_table_dev = nullptr;
+  cudaEvent_t batch_copied = nullptr;   // the graph's table copy has finished
+  cudaStream_t batch_capture = nullptr; // stream the graph is captured on
+  cudaGraphExec_t batch_graph = nullptr;
+  int batch_graph_variant = -1;         // cost_plain_popc the graph was captured with
+  int batch_grid[4] = {0, 0, 0, 0};     // persistent grid sizes of the four batched kernels
+  uint32_t *batch_plane = nullptr;      // colour planes of every view of a batch
+  size_t batch_plane_words = 0;
+  cudaError_t last_cuda = cudaSuccess;  // last CUDA error behind a BSM_ERR_CUDA of this context
   // Workspace of bsm_match_host (grown on demand).
   void *ws = nullptr;
   size_t ws_bytes = 0;
@@ -64,6 +104,11 @@ cudaError_t launch_describe(const bsm_ctx *ctx, const uint8_t *rgb, int w, int h
 cudaError_t launch_cost_wta(const bsm_ctx *ctx, const uint32_t *BL, const uint32_t *PhiL, const uint32_t *BR,
                             const uint32_t *PhiR, int w, int h, int dmax, int32_t *dL, int32_t *dR, uint16_t *cost,
                             cudaStream_t s);
+// Batched kernels: prepare_* sets kernel attributes and returns the persistent grid (outside any
+// stream capture); launch_* only enqueues.
+cudaError_t prepare_describe_batch(const bsm_ctx *ctx, int *grid);
+cudaError_t prepare_cost_batch(const bsm_ctx *ctx, int *grid);
+cudaError_t prepare_refine_batch(const bsm_ctx *ctx, int *grid);
 cudaError_t launch_refine(const bsm_ctx *ctx, const uint8_t *rgb, int pitch, const int32_t *dL, const int32_t *dR,
                           int w, int h, int dmax, int32_t *out, cudaStream_t s);
 

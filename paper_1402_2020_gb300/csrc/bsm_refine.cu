@@ -1,16 +1,20 @@
 // Left/right check and voting refinement of the left disparity map (Sec. 3, Eq. 9-10).
 //
 // One CTA covers a 32 x 8 block of output pixels. It stages, for the block plus a halo of R pixels,
-// each pixel's CIELAB word (from the colour table) and its disparity if that pixel passes the
-// left/right check (-1 otherwise), together with the two integer vote tables. Valid pixels keep
-// their disparity. Invalid pixels are collected into a list that the CTA's warps share: a warp takes
-// one invalid pixel at a time; lane l owns window column l (and l + 32 when 2R+1 > 32) and walks
-// down its rows, summing each valid neighbour's vote floor(Ec[c] * Es[e2] / 2^15) in a register
-// while consecutive voters share a disparity and adding the run to a per-warp shared histogram over
-// d when the disparity changes (disparities are piecewise smooth, so runs are long and shared
-// atomics few). The warp then takes the smallest d with the largest weight (Eq. 9). When no vote
-// is positive the warp scans the row outward, 32 positions per step, for the nearest valid pixels
-// on each side.
+// each pixel's CIELAB word and its disparity if that pixel passes the left/right check (-1
+// otherwise), together with the two integer vote tables. Valid pixels keep their disparity. Invalid
+// pixels are collected into a list that the CTA's warps share: a warp takes one invalid pixel at a
+// time; lane l owns window column l (and l + 32 when 2R+1 > 32) and walks down its rows, summing each
+// valid neighbour's vote floor(Ec[c] * Es[e2] / 2^15) in a register while consecutive voters share a
+// disparity and adding the run to a per-warp shared histogram over d when the disparity changes
+// (disparities are piecewise smooth, so runs are long and shared atomics few). The warp then takes
+// the smallest d with the largest weight (Eq. 9). When no vote is positive the warp scans the row
+// outward, 32 positions per step, for the nearest valid pixels on each side.
+//
+// The batched form reads the colour words from the batch's colour planes, and its disparity inputs
+// are the batched cost kernel's keys (A << 10 | d): every read keeps the low 10 bits, and each CTA
+// writes its block's final disparities back over the keys. A key and its disparity agree in the low
+// 10 bits, so reads by other CTAs see the same disparity before and after that write.
 #include "bsm_internal.cuh"
 
 namespace bsm {
@@ -18,57 +22,72 @@ namespace {
 
 constexpr int kTX = 32, kTY = 8;
 constexpr int kWarps = kTX * kTY / 32;
+constexpr uint32_t kDispMask = 1023u;
 
 struct RefineArgs {
-  const uint8_t *rgb;
+  const uint8_t *rgb;      // RGB view (when plane == nullptr)
+  const uint32_t *plane;   // packed colour words, or nullptr
   const uint32_t *table;
-  const int32_t *dL;
-  const int32_t *dR;
-  const uint32_t *Ec;
-  const uint32_t *Es;
+  int32_t *dL;             // WTA maps (or keys, see above)
+  int32_t *dR;
   int32_t *out;
   int w, h, pitch, dmax, tol, R;
+  int hist_stride;         // shared histogram bins per warp (>= dmax)
+  bool finalize;           // write the masked disparities back into dL and dR
 };
 
 __device__ __forceinline__ uint32_t lab_sad(uint32_t a, uint32_t b) {
   return __dp4a(__vabsdiffu4(a, b), 0x00010101u, 0u);
 }
 
+__device__ __forceinline__ int disp_at(const int32_t *m, size_t i) {
+  return (int)((uint32_t)__ldcg(m + i) & kDispMask);
+}
+
 __device__ __forceinline__ bool lr_valid(const RefineArgs &a, int x, int y, int d) {
   const int xr = x - d;
   if (xr < 0 || xr >= a.w) return false;
-  const int dr = __ldg(a.dR + (size_t)y * a.w + xr);
-  return abs(d - dr) <= a.tol;
+  return abs(d - disp_at(a.dR, (size_t)y * a.w + xr)) <= a.tol;
 }
 
-__global__ void __launch_bounds__(kTX *kTY) refine_kernel(const RefineArgs a) {
-  extern __shared__ __align__(16) uint32_t smem[];
+__host__ __device__ size_t table_words(int R) { return (kMaxSad + 1) + (size_t)(2 * R * R + 1); }
+
+__device__ __forceinline__ void load_vote_tables(const uint32_t *Ec, const uint32_t *Es, int R, uint32_t *smem) {
+  const int ne = 2 * R * R + 1;
+  for (int i = threadIdx.x; i <= kMaxSad; i += blockDim.x) smem[i] = __ldg(Ec + i);
+  for (int i = threadIdx.x; i < ne; i += blockDim.x) smem[kMaxSad + 1 + i] = __ldg(Es + i);
+}
+
+// One 32 x 8 block with top-left corner (x0, y0); `tabs` holds the vote tables, `work` the tile.
+// Every thread of the CTA reaches its two CTA-wide barriers.
+__device__ __forceinline__ void refine_tile(const RefineArgs &a, int x0, int y0, const uint32_t *tabs,
+                                            uint32_t *work) {
   const int R = a.R, side = 2 * R + 1;
   const int tp = kTX + 2 * R, th = kTY + 2 * R;
-  const int ne = 2 * R * R + 1;
-  uint32_t *sEc = smem;                              // kMaxSad + 1
-  uint32_t *sEs = sEc + (kMaxSad + 1);               // ne
-  uint32_t *slab = sEs + ne;                         // th * tp
-  uint32_t *shist = slab + th * tp;                  // kWarps * dmax
-  int16_t *sd = reinterpret_cast<int16_t *>(shist + kWarps * a.dmax);  // th * tp
-  __shared__ int s_count;
-  __shared__ int16_t s_list[kTX * kTY];
+  const uint32_t *sEc = tabs;
+  const uint32_t *sEs = tabs + (kMaxSad + 1);
+  uint32_t *slab = work;                                                // th * tp
+  uint32_t *shist = slab + th * tp;                                     // kWarps * hist_stride
+  int16_t *sd = reinterpret_cast<int16_t *>(shist + kWarps * a.hist_stride);  // th * tp
+  int *s_count = reinterpret_cast<int *>(sd + ((th * tp + 1) & ~1));
+  int16_t *s_list = reinterpret_cast<int16_t *>(s_count + 1);           // kTX * kTY
 
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int x0 = blockIdx.x * kTX, y0 = blockIdx.y * kTY;
-  if (threadIdx.x == 0) s_count = 0;
-  for (int i = threadIdx.x; i <= kMaxSad; i += blockDim.x) sEc[i] = __ldg(a.Ec + i);
-  for (int i = threadIdx.x; i < ne; i += blockDim.x) sEs[i] = __ldg(a.Es + i);
+  if (threadIdx.x == 0) *s_count = 0;
   for (int i = threadIdx.x; i < th * tp; i += blockDim.x) {
     const int ty = i / tp, tx = i - ty * tp;
     const int gx = x0 + tx - R, gy = y0 + ty - R;
     int16_t dv = -1;
     uint32_t lab = 0;
     if (gx >= 0 && gx < a.w && gy >= 0 && gy < a.h) {
-      const uint8_t *px = a.rgb + (size_t)gy * a.pitch + 3 * gx;
-      lab = __ldg(a.table + (((uint32_t)px[0] << 16) | ((uint32_t)px[1] << 8) | (uint32_t)px[2])) & kLabMask;
-      const int d = __ldg(a.dL + (size_t)gy * a.w + gx);
-      if (d >= 0 && d < a.dmax && lr_valid(a, gx, gy, d)) dv = (int16_t)d;
+      if (a.plane != nullptr) {
+        lab = __ldg(a.plane + (size_t)gy * a.w + gx) & kLabMask;
+      } else {
+        const uint8_t *px = a.rgb + (size_t)gy * a.pitch + 3 * gx;
+        lab = __ldg(a.table + (((uint32_t)px[0] << 16) | ((uint32_t)px[1] << 8) | (uint32_t)px[2])) & kLabMask;
+      }
+      const int d = disp_at(a.dL, (size_t)gy * a.w + gx);
+      if (d < a.dmax && lr_valid(a, gx, gy, d)) dv = (int16_t)d;
     }
     slab[i] = lab;
     sd[i] = dv;
@@ -79,15 +98,16 @@ __global__ void __launch_bounds__(kTX *kTY) refine_kernel(const RefineArgs a) {
     const int tx = threadIdx.x & (kTX - 1), ty = threadIdx.x / kTX;
     const int x = x0 + tx, y = y0 + ty;
     if (x < a.w && y < a.h) {
+      const size_t i = (size_t)y * a.w + x;
       const int dv = sd[(ty + R) * tp + tx + R];
-      if (dv >= 0) a.out[(size_t)y * a.w + x] = dv;
-      else s_list[atomicAdd(&s_count, 1)] = (int16_t)threadIdx.x;
+      if (dv >= 0) a.out[i] = dv;
+      else s_list[atomicAdd(s_count, 1)] = (int16_t)threadIdx.x;
     }
   }
   __syncthreads();
 
-  const int count = s_count;
-  uint32_t *hist = shist + warp * a.dmax;
+  const int count = *s_count;
+  uint32_t *hist = shist + warp * a.hist_stride;
   for (int it = warp; it < count; it += kWarps) {
     const int t = s_list[it];
     const int tx = t & (kTX - 1), ty = t / kTX;
@@ -97,7 +117,7 @@ __global__ void __launch_bounds__(kTX *kTY) refine_kernel(const RefineArgs a) {
     const uint32_t labx = slab[(ty + R) * tp + tx + R];
     for (int wx = lane; wx < side; wx += 32) {
       const int dx2 = (wx - R) * (wx - R);
-      const int16_t *dcol = sd + ty * tp + tx + wx;     // window row 0 of this column
+      const int16_t *dcol = sd + ty * tp + tx + wx;  // window row 0 of this column
       const uint32_t *lcol = slab + ty * tp + tx + wx;
       int run_d = -1;
       uint32_t run = 0;
@@ -137,8 +157,8 @@ __global__ void __launch_bounds__(kTX *kTY) refine_kernel(const RefineArgs a) {
       for (int xs = x - 1; xs >= 0; xs -= 32) {
         const int xi = xs - lane;
         int d = -1;
-        if (xi >= 0) d = __ldg(a.dL + (size_t)y * a.w + xi);
-        const bool ok = xi >= 0 && d >= 0 && d < a.dmax && lr_valid(a, xi, y, d);
+        if (xi >= 0) d = disp_at(a.dL, (size_t)y * a.w + xi);
+        const bool ok = xi >= 0 && d < a.dmax && lr_valid(a, xi, y, d);
         const uint32_t m = __ballot_sync(0xFFFFFFFFu, ok);
         if (m) {
           left = __shfl_sync(0xFFFFFFFFu, d, __ffs(m) - 1);
@@ -148,8 +168,8 @@ __global__ void __launch_bounds__(kTX *kTY) refine_kernel(const RefineArgs a) {
       for (int xs = x + 1; xs < a.w; xs += 32) {
         const int xi = xs + lane;
         int d = -1;
-        if (xi < a.w) d = __ldg(a.dL + (size_t)y * a.w + xi);
-        const bool ok = xi < a.w && d >= 0 && d < a.dmax && lr_valid(a, xi, y, d);
+        if (xi < a.w) d = disp_at(a.dL, (size_t)y * a.w + xi);
+        const bool ok = xi < a.w && d < a.dmax && lr_valid(a, xi, y, d);
         const uint32_t m = __ballot_sync(0xFFFFFFFFu, ok);
         if (m) {
           right = __shfl_sync(0xFFFFFFFFu, d, __ffs(m) - 1);
@@ -164,25 +184,91 @@ __global__ void __launch_bounds__(kTX *kTY) refine_kernel(const RefineArgs a) {
     if (lane == 0) a.out[(size_t)y * a.w + x] = best;
     __syncwarp();
   }
+
+  if (a.finalize) {
+    const int tx = threadIdx.x & (kTX - 1), ty = threadIdx.x / kTX;
+    const int x = x0 + tx, y = y0 + ty;
+    if (x < a.w && y < a.h) {
+      const size_t i = (size_t)y * a.w + x;
+      a.dL[i] = disp_at(a.dL, i);
+      a.dR[i] = disp_at(a.dR, i);
+    }
+  }
+}
+
+size_t tile_bytes(int R, int hist_stride) {
+  const int tp = kTX + 2 * R, th = kTY + 2 * R;
+  return (size_t)th * tp * 4 + (size_t)kWarps * hist_stride * 4 + (size_t)((th * tp + 1) & ~1) * 2 + 4 +
+         (size_t)kTX * kTY * 2;
+}
+
+__global__ void __launch_bounds__(kTX *kTY) refine_kernel(const RefineArgs a, const uint32_t *Ec, const uint32_t *Es) {
+  extern __shared__ __align__(16) uint32_t smem[];
+  load_vote_tables(Ec, Es, a.R, smem);
+  refine_tile(a, blockIdx.x * kTX, blockIdx.y * kTY, smem, smem + table_words(a.R));
+}
+
+// Batched refinement: persistent CTAs take (pair, block) tickets.
+__global__ void __launch_bounds__(kTX *kTY) refine_batch_kernel(BatchHeader *hdr, const BatchPair *pairs,
+                                                               const uint32_t *Ec, const uint32_t *Es,
+                                                               const uint32_t *table, int tol, int R,
+                                                               int hist_stride) {
+  extern __shared__ __align__(16) uint32_t smem[];
+  __shared__ int s_ticket;
+  load_vote_tables(Ec, Es, R, smem);
+  const int total = hdr->total[3], count = hdr->count;
+  for (;;) {
+    __syncthreads();  // the previous block is done with shared memory
+    if (threadIdx.x == 0) s_ticket = (int)atomicAdd(&hdr->counters[3], 1u);
+    __syncthreads();
+    const int tk = s_ticket;
+    if (tk >= total) return;
+    int lo = 0, hi = count - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (pairs[mid].ref_base <= tk) lo = mid;
+      else hi = mid - 1;
+    }
+    const BatchPair &p = pairs[lo];
+    const int r = tk - p.ref_base, ty = r / p.ref_tx, tx = r - ty * p.ref_tx;
+    RefineArgs a{p.rgb[0], p.plane[0], table, p.disp[0], p.disp[1], p.out, p.w, p.h, p.pitch, p.dmax,
+                 tol, R, hist_stride, true};
+    refine_tile(a, tx * kTX, ty * kTY, smem, smem + table_words(R));
+  }
 }
 
 }  // namespace
 
-size_t refine_smem_bytes(int R, int dmax) {
-  const int tp = kTX + 2 * R, th = kTY + 2 * R;
-  const size_t words = (kMaxSad + 1) + (2 * R * R + 1) + (size_t)th * tp + (size_t)kWarps * dmax;
-  return words * 4 + (size_t)th * tp * 2;
-}
-
 cudaError_t launch_refine(const bsm_ctx *ctx, const uint8_t *rgb, int pitch, const int32_t *dL, const int32_t *dR,
                           int w, int h, int dmax, int32_t *out, cudaStream_t s) {
-  RefineArgs a{rgb, ctx->color_table, dL, dR, ctx->vote_ec, ctx->vote_es, out, w, h, pitch, dmax,
-               ctx->p.lr_tol, ctx->p.vote_radius};
-  const size_t smem = refine_smem_bytes(a.R, dmax);
+  // The plain form never writes dL or dR (finalize is off), so the const inputs stay untouched.
+  RefineArgs a{rgb, nullptr, ctx->color_table, const_cast<int32_t *>(dL), const_cast<int32_t *>(dR), out, w, h, pitch,
+               dmax, ctx->p.lr_tol, ctx->p.vote_radius, dmax, false};
+  const size_t smem = table_words(a.R) * 4 + tile_bytes(a.R, dmax);
   cudaError_t e = cudaFuncSetAttribute(refine_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   dim3 grid((w + kTX - 1) / kTX, (h + kTY - 1) / kTY);
-  refine_kernel<<<grid, kTX * kTY, smem, s>>>(a);
+  refine_kernel<<<grid, kTX * kTY, smem, s>>>(a, ctx->vote_ec, ctx->vote_es);
+  return cudaGetLastError();
+}
+
+cudaError_t prepare_refine_batch(const bsm_ctx *ctx, int *grid) {
+  const int R = ctx->p.vote_radius, hs = ctx->p.dmax;
+  const size_t smem = table_words(R) * 4 + tile_bytes(R, hs);
+  cudaError_t e = cudaFuncSetAttribute(refine_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, refine_batch_kernel, kTX * kTY, smem);
+  *grid = max(1, per_sm) * ctx->sms;
+  return e;
+}
+
+cudaError_t launch_refine_batch(const bsm_ctx *ctx, BatchHeader *hdr, const BatchPair *pairs, int grid,
+                                cudaStream_t s) {
+  const int R = ctx->p.vote_radius, hs = ctx->p.dmax;
+  const size_t smem = table_words(R) * 4 + tile_bytes(R, hs);
+  refine_batch_kernel<<<grid, kTX * kTY, smem, s>>>(hdr, pairs, ctx->vote_ec, ctx->vote_es, ctx->color_table,
+                                                    ctx->p.lr_tol, R, hs);
   return cudaGetLastError();
 }
 
