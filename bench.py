@@ -128,6 +128,9 @@ def profile_traffic(kernel_file, workload_key):
     return None
 
 
+_SAMPLE_CACHE = {}
+
+
 def oracle_sample(cfg, rows):
     """The oracle as it stands on a band of `rows` rows of the workload: returns (seconds, pix*disp)."""
     from oracle import oracle
@@ -136,7 +139,10 @@ def oracle_sample(cfg, rows):
     if "count" in cfg:  # batch workload: sample the first pair of the batch
         w, h, dmax, seed = synth.batch_shapes(cfg["count"], seed=cfg["seed"])[0]
         cfg = dict(w=w, h=h, dmax=dmax, seed=seed, radiometric=False)
-    left, right, _ = synth.stereo_pair(cfg["w"], cfg["h"], cfg["dmax"], cfg["seed"], cfg["radiometric"])
+    key = (cfg["w"], cfg["h"], cfg["dmax"], cfg["seed"], cfg["radiometric"])
+    if key not in _SAMPLE_CACHE:
+        _SAMPLE_CACHE[key] = synth.stereo_pair(*key)
+    left, right, _ = _SAMPLE_CACHE[key]
     pairs = synth.pair_table(N_BITS, WINDOW_S, seed=PAIR_SEED)
     y0 = cfg["h"] // 2 - rows // 2
     l = np.ascontiguousarray(left[y0:y0 + rows])
