@@ -35,6 +35,8 @@ CONFIGS = {
     "c4": dict(w=3840, h=2160, dmax=256, radiometric=False, seed=4,
                name="3840x2160 RGB8 pair, dmax 256"),
     "c3": dict(count=64, seed=3, name="batch of 64 uneven pairs: w U[320,1920], h U[240,1080], dmax {64,128,192,256}"),
+    "c5": dict(seed=5, name="serving stream: Poisson arrivals, sizes {640x480,1280x720,1920x1080,3840x2160} x dmax "
+                            "{64,128,256}, continuous batching vs one-at-a-time"),
 }
 N_BITS, WINDOW_S, AGG, VOTE_R = 256, 31, 5, 15
 PAIR_SEED = 11
@@ -55,6 +57,10 @@ def parse():
     ap.add_argument("--cost-rows", type=int, default=0, help="rows per CTA of the cost kernel (0: heuristic)")
     ap.add_argument("--cost-popc-plain", type=int, default=0, help="1: plain popcount in the cost kernel")
     ap.add_argument("--batch-rows", type=int, default=0, help="rows per task of the batched cost kernel (0: 64)")
+    ap.add_argument("--requests", type=int, default=2000, help="serving stream length (c5)")
+    ap.add_argument("--rho", type=float, default=0.7, help="arrival rate as a fraction of measured capacity (c5)")
+    ap.add_argument("--lanes", type=int, default=2, help="serving lanes (c5)")
+    ap.add_argument("--max-batch", type=int, default=16, help="serving batch limit (c5)")
     return ap.parse_args()
 
 
@@ -139,6 +145,8 @@ def oracle_sample(cfg, rows):
     if "count" in cfg:  # batch workload: sample the first pair of the batch
         w, h, dmax, seed = synth.batch_shapes(cfg["count"], seed=cfg["seed"])[0]
         cfg = dict(w=w, h=h, dmax=dmax, seed=seed, radiometric=False)
+    elif "w" not in cfg:  # request stream: sample its 1280x720, dmax 128 class
+        cfg = dict(w=1280, h=720, dmax=128, seed=cfg["seed"], radiometric=False)
     key = (cfg["w"], cfg["h"], cfg["dmax"], cfg["seed"], cfg["radiometric"])
     if key not in _SAMPLE_CACHE:
         _SAMPLE_CACHE[key] = synth.stereo_pair(*key)
@@ -173,6 +181,8 @@ def run_reference(args, cfg, world, rank):
 
         w0 = synth.batch_shapes(cfg["count"], seed=cfg["seed"])[0][0]
         cfg = dict(cfg, w=w0)
+    elif "w" not in cfg:
+        cfg = dict(cfg, w=1280)
     times = []
     for i in range(args.warmup + args.steps):
         dt, units = oracle_sample(cfg, rows)
@@ -282,6 +292,115 @@ def run_batch(args, cfg, world, rank, local):
     bsm.bsm_destroy(ctx)
 
 
+def run_serving(args, cfg, world, rank, local):
+    """Config 5: a Poisson request stream through the continuous-batching engine, against the same trace
+    processed one request at a time through the host-buffer C-ABI call."""
+    import torch
+
+    from paper_1402_2020_gb300 import bsm, synth
+
+    torch.cuda.set_device(local)
+    pairs = synth.pair_table(N_BITS, WINDOW_S, seed=PAIR_SEED)
+    params = bsm.make_params(pairs, window_S=WINDOW_S, agg_window=AGG, dmax=256, vote_radius=VOTE_R)
+    classes = [(w, h, d) for (w, h) in synth.SERVE_SIZES for d in synth.SERVE_DMAX]
+    data = {}
+    for i, (w, h, d) in enumerate(classes):
+        l, r, _ = synth.stereo_pair(w, h, d, cfg["seed"] * 100 + i + 1000 * rank)
+        data[(w, h, d)] = (torch.from_numpy(l).pin_memory(), torch.from_numpy(r).pin_memory(),
+                           torch.empty((h, w), dtype=torch.int32).pin_memory())
+    srv = bsm.bsm_server_create(params, lanes=args.lanes, max_batch=args.max_batch)
+    ctx = bsm.bsm_create(params)
+    rng = np.random.default_rng(cfg["seed"] + rank)
+
+    def submit(i, c):
+        l, r, o = data[c]
+        st = bsm.bsm_server_submit(srv, i, l, r, c[0], c[1], 3 * c[0], c[2], o)
+        assert st == bsm.BSM_OK, st
+
+    # warm-up (graph capture, pools) and capacity: a flat-out burst
+    for i in range(2 * len(classes)):
+        submit(i, classes[i % len(classes)])
+    bsm.bsm_server_drain(srv)
+    while bsm.bsm_server_poll(srv, 256, 0):
+        pass
+    n_cap = 240
+    burst = [classes[int(k)] for k in rng.integers(0, len(classes), size=n_cap)]
+    t0 = time.perf_counter()
+    for i, c in enumerate(burst):
+        submit(10 ** 6 + i, c)
+    bsm.bsm_server_drain(srv)
+    capacity = n_cap / (time.perf_counter() - t0)
+    while bsm.bsm_server_poll(srv, 256, 0):
+        pass
+
+    trace = synth.request_trace(args.requests, args.rho * capacity, seed=cfg["seed"] + rank)
+    units = sum(w * h * d for (_, w, h, d) in trace)
+
+    def served():
+        done = {}
+        start = time.perf_counter() + 0.05
+
+        def producer():
+            for i, (ta, w, h, d) in enumerate(trace):
+                delay = start + ta - time.perf_counter()
+                if delay > 0:
+                    time.sleep(delay)
+                submit(i, (w, h, d))
+
+        th = threading.Thread(target=producer)
+        th.start()
+        while len(done) < len(trace):
+            for cid, st, _ in bsm.bsm_server_poll(srv, 512, 2000):
+                assert st == bsm.BSM_OK, st
+                done[cid] = time.perf_counter()
+        th.join()
+        lat = np.array([done[i] - (start + trace[i][0]) for i in range(len(trace))])
+        return lat, max(done.values()) - start
+
+    def plain():
+        done = []
+        start = time.perf_counter() + 0.05
+        for ta, w, h, d in trace:
+            delay = start + ta - time.perf_counter()
+            if delay > 0:
+                time.sleep(delay)
+            l, r, o = data[(w, h, d)]
+            bsm.bsm_match_host(ctx, l.data_ptr(), r.data_ptr(), w, h, 3 * w, d, o.data_ptr())
+            done.append(time.perf_counter())
+        lat = np.array([done[i] - (start + trace[i][0]) for i in range(len(trace))])
+        return lat, done[-1] - start
+
+    clk = Clocks(local)
+    clk.start()
+    lat_s, wall_s = served()
+    clocks = clk.stop()
+    stats = bsm.bsm_server_get_stats(srv)
+    lat_p, wall_p = plain()
+    bsm.bsm_server_destroy(srv)
+    bsm.bsm_destroy(ctx)
+
+    def summary(lat, wall):
+        return {"pairs_per_s": len(trace) / wall, "gpix_disp_per_s": units / wall / 1e9,
+                "p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
+                "max_ms": float(lat.max() * 1e3), "wall_s": wall}
+
+    s_sum, p_sum = summary(lat_s, wall_s), summary(lat_p, wall_p)
+    line = {
+        "metric": METRIC, "value": s_sum["gpix_disp_per_s"] * world, "unit": METRIC, "n_gpus": world,
+        "steps": len(trace), "warmup": 2 * len(classes), "ms_per_step": wall_s * 1e3 / len(trace),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": cfg["name"], "requests": len(trace), "rho": args.rho, "lanes": args.lanes,
+                   "max_batch": args.max_batch, "arrival_rate_per_s": args.rho * capacity,
+                   "n_bits": N_BITS, "agg_window": AGG, "parallelism": f"replicas x{world}"},
+        "capacity_pairs_per_s": capacity,
+        "served": s_sum, "one_at_a_time": p_sum,
+        "p99_speedup": p_sum["p99_ms"] / s_sum["p99_ms"],
+        "engine": stats, "clocks": clocks,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def torch_dist_done():
     import torch.distributed as dist
 
@@ -295,8 +414,8 @@ def main():
     if args.impl == "reference":
         run_reference(args, cfg, world, rank)
         return
-    if args.config == "c3":
-        run_batch(args, cfg, world, rank, local)
+    if args.config in ("c3", "c5"):
+        (run_batch if args.config == "c3" else run_serving)(args, cfg, world, rank, local)
         if world > 1:
             torch_dist_done()
         return

@@ -143,6 +143,62 @@ bsm_status bsm_batch_run(bsm_ctx *ctx, const bsm_pair_desc *pairs, int32_t count
 /* Size the batch scratch for batches of up to `total_pixels` pixels per view summed over the pairs. */
 bsm_status bsm_reserve_batch(bsm_ctx *ctx, int64_t total_pixels);
 
+/*
+ * Serving engine: continuous batching of requests on the current device.
+ *
+ * A scheduler thread owns `lanes` lanes (each a context with the engine's parameters and its own
+ * stream). Whenever a lane is free it admits queued requests in arrival order while the engine's
+ * device-memory budget allows, and runs them as one bsm_batch_run with the copies of their views in
+ * and their refined maps out, so batches of different lanes overlap on the device and requests that
+ * arrive while others run are admitted as soon as a lane and memory free up. Request buffers are
+ * allocated from the engine's own stream-ordered pool; each lane's context also keeps batch scratch
+ * (grown to the largest batch it has seen) outside the budget. Results are bit-identical to the
+ * per-pair calls.
+ */
+typedef struct bsm_server bsm_server;
+
+typedef struct {
+  int32_t lanes;          /* batches in flight at once, 1..8 */
+  int32_t max_batch;      /* requests per batch, 1..BSM_MAX_BATCH */
+  int64_t device_budget;  /* bytes of request buffers the engine may hold; 0 selects half the free memory */
+} bsm_server_config;
+
+typedef struct {
+  uint64_t id;                 /* caller's identifier, returned with the completion */
+  const uint8_t *rgbL, *rgbR;  /* HOST views, h rows of pitch_bytes; pinned memory lets copies overlap */
+  int32_t w, h, pitch_bytes, dmax;
+  int32_t *out;                /* HOST int32 [h][w]: the refined left map (pinned memory recommended) */
+} bsm_request;                 /* the buffers must stay valid until the request completes */
+
+typedef struct {
+  uint64_t id;
+  bsm_status status;           /* BSM_OK, or why the request failed */
+  double latency_us;           /* from bsm_server_submit to the scheduler seeing the result */
+} bsm_completion;
+
+typedef struct {
+  int64_t submitted, completed, failed, batches, max_batch_seen, queued, bytes_in_use, budget;
+} bsm_server_stats;
+
+/* Start an engine (creates `lanes` contexts: synchronous, allocates). */
+bsm_status bsm_server_create(const bsm_params *params, const bsm_server_config *cfg, bsm_server **out);
+
+/* Queue a request (any thread, non-blocking). A malformed request, or one larger than the whole
+ * budget, completes at once with BSM_ERR_INVALID_ARG, which is also returned here. */
+bsm_status bsm_server_submit(bsm_server *s, const bsm_request *req);
+
+/* Up to max_out completions; waits up to timeout_us for the first (0: none, < 0: forever).
+ * Returns how many were written (-1 on a bad argument). */
+int32_t bsm_server_poll(bsm_server *s, bsm_completion *out, int32_t max_out, int32_t timeout_us);
+
+/* Wait until every submitted request has completed (timeout_ms < 0: forever); BSM_ERR_TIMEOUT if not. */
+bsm_status bsm_server_drain(bsm_server *s, int32_t timeout_ms);
+
+bsm_status bsm_server_get_stats(bsm_server *s, bsm_server_stats *out);
+
+/* Finish every queued request, then stop the scheduler and release everything. */
+void bsm_server_destroy(bsm_server *s);
+
 /* Largest image, in pixels (width * height), that bsm_describe_noalloc accepts: 2^22. */
 #define BSM_NOALLOC_MAX_PIXELS 4194304
 

@@ -27,7 +27,8 @@ EXPORTED = (
     "bsm_create", "bsm_destroy", "bsm_describe", "bsm_cost_aggregate_wta", "bsm_refine", "bsm_match_host",
     "bsm_last_error", "bsm_status_string", "bsm_copy_color_table", "bsm_vote_tables", "bsm_validate_params",
     "bsm_abi_version", "bsm_set_tuning", "bsm_get_tuning", "bsm_reserve", "bsm_describe_noalloc",
-    "bsm_batch_run", "bsm_reserve_batch", "bsm_last_cuda_error",
+    "bsm_batch_run", "bsm_reserve_batch", "bsm_last_cuda_error", "bsm_server_create", "bsm_server_submit",
+    "bsm_server_poll", "bsm_server_drain", "bsm_server_get_stats", "bsm_server_destroy",
 )
 BSM_MAX_BATCH = 1024
 
@@ -65,6 +66,25 @@ class bsm_pair_desc(ctypes.Structure):
                 ("pitch_bytes", ctypes.c_int32), ("dmax", ctypes.c_int32), ("BL", ctypes.c_void_p),
                 ("PhiL", ctypes.c_void_p), ("BR", ctypes.c_void_p), ("PhiR", ctypes.c_void_p),
                 ("dispL", ctypes.c_void_p), ("dispR", ctypes.c_void_p), ("out", ctypes.c_void_p)]
+
+
+class bsm_server_config(ctypes.Structure):
+    _fields_ = [("lanes", ctypes.c_int32), ("max_batch", ctypes.c_int32), ("device_budget", ctypes.c_int64)]
+
+
+class bsm_request(ctypes.Structure):
+    _fields_ = [("id", ctypes.c_uint64), ("rgbL", ctypes.c_void_p), ("rgbR", ctypes.c_void_p), ("w", ctypes.c_int32),
+                ("h", ctypes.c_int32), ("pitch_bytes", ctypes.c_int32), ("dmax", ctypes.c_int32),
+                ("out", ctypes.c_void_p)]
+
+
+class bsm_completion(ctypes.Structure):
+    _fields_ = [("id", ctypes.c_uint64), ("status", ctypes.c_int), ("latency_us", ctypes.c_double)]
+
+
+class bsm_server_stats(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_int64) for k in ("submitted", "completed", "failed", "batches", "max_batch_seen",
+                                              "queued", "bytes_in_use", "budget")]
 
 
 _lib = None
@@ -105,6 +125,19 @@ def lib():
         L.bsm_get_tuning.restype = S
         L.bsm_describe_noalloc.argtypes = [P, P, I, I, I, P, P, P]
         L.bsm_describe_noalloc.restype = S
+        L.bsm_server_create.argtypes = [ctypes.POINTER(bsm_params), ctypes.POINTER(bsm_server_config),
+                                        ctypes.POINTER(P)]
+        L.bsm_server_create.restype = S
+        L.bsm_server_submit.argtypes = [P, ctypes.POINTER(bsm_request)]
+        L.bsm_server_submit.restype = S
+        L.bsm_server_poll.argtypes = [P, ctypes.POINTER(bsm_completion), I, I]
+        L.bsm_server_poll.restype = I
+        L.bsm_server_drain.argtypes = [P, I]
+        L.bsm_server_drain.restype = S
+        L.bsm_server_get_stats.argtypes = [P, ctypes.POINTER(bsm_server_stats)]
+        L.bsm_server_get_stats.restype = S
+        L.bsm_server_destroy.argtypes = [P]
+        L.bsm_server_destroy.restype = None
         L.bsm_last_cuda_error.argtypes = [P]
         L.bsm_last_cuda_error.restype = ctypes.c_char_p
         L.bsm_batch_run.argtypes = [P, ctypes.POINTER(bsm_pair_desc), I, P]
@@ -323,3 +356,39 @@ class Matcher:
         BR, PhiR = self.describe(rgbR, stream)
         dL, dR, _ = self.cost_wta(BL, PhiL, BR, PhiR, dmax, stream=stream)
         return self.refine(rgbL, dL, dR, dmax, stream)
+
+
+def bsm_server_create(params: bsm_params, lanes: int = 2, max_batch: int = 64, device_budget: int = 0) -> int:
+    cfg = bsm_server_config(lanes, max_batch, device_budget)
+    h = ctypes.c_void_p()
+    _check(lib().bsm_server_create(ctypes.byref(params), ctypes.byref(cfg), ctypes.byref(h)), "bsm_server_create")
+    return h.value
+
+
+def bsm_server_submit(srv: int, req_id: int, rgbL, rgbR, w: int, h: int, pitch: int, dmax: int, out) -> int:
+    """Queue one request (host buffers). Returns the status (a rejected request also completes)."""
+    r = bsm_request(req_id, _ptr(rgbL), _ptr(rgbR), w, h, pitch, dmax, _ptr(out))
+    return lib().bsm_server_submit(srv, ctypes.byref(r))
+
+
+def bsm_server_poll(srv: int, max_out: int = 256, timeout_us: int = 1000):
+    """List of (id, status, latency_us) completions."""
+    arr = (bsm_completion * max_out)()
+    n = lib().bsm_server_poll(srv, arr, max_out, timeout_us)
+    if n < 0:
+        raise BsmError(BSM_ERR_INVALID_ARG, "bsm_server_poll")
+    return [(arr[i].id, arr[i].status, arr[i].latency_us) for i in range(n)]
+
+
+def bsm_server_drain(srv: int, timeout_ms: int = -1) -> None:
+    _check(lib().bsm_server_drain(srv, timeout_ms), "bsm_server_drain")
+
+
+def bsm_server_get_stats(srv: int) -> dict:
+    st = bsm_server_stats()
+    _check(lib().bsm_server_get_stats(srv, ctypes.byref(st)), "bsm_server_get_stats")
+    return {k: getattr(st, k) for k, _ in bsm_server_stats._fields_}
+
+
+def bsm_server_destroy(srv: int) -> None:
+    lib().bsm_server_destroy(srv)
