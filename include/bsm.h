@@ -161,6 +161,8 @@ typedef struct {
   int32_t lanes;          /* batches in flight at once, 1..8 */
   int32_t max_batch;      /* requests per batch, 1..BSM_MAX_BATCH */
   int64_t device_budget;  /* bytes of request buffers the engine may hold; 0 selects half the free memory */
+  int64_t max_batch_work; /* cap on a batch's sum of w * h * dmax (a larger request still runs alone);
+                             0 = no cap. Keeps large requests from holding small ones in one batch. */
 } bsm_server_config;
 
 typedef struct {
@@ -252,6 +254,15 @@ bsm_status bsm_match_host(bsm_ctx *ctx, const uint8_t *rgbL_host, const uint8_t 
  * Synchronises the context's device.
  */
 bsm_status bsm_last_error(bsm_ctx *ctx);
+
+/*
+ * Test hooks for failure detection (off by default; every hook only withholds work, it never faults).
+ *   BSM_DEBUG_WITHHOLD_ARRIVALS (1): value 1 makes the cost kernels' staging thread skip its mbarrier
+ *     arrivals, so every bounded wait of the next cost launch runs out (about a second per wave of
+ *     CTAs); the kernel then latches BSM_ERR_TIMEOUT and returns, and the context stays usable.
+ */
+#define BSM_DEBUG_WITHHOLD_ARRIVALS 1
+bsm_status bsm_debug_set(bsm_ctx *ctx, int32_t key, int32_t value);
 
 /* Name of the CUDA runtime error behind the context's most recent BSM_ERR_CUDA ("" if none). */
 const char *bsm_last_cuda_error(bsm_ctx *ctx);

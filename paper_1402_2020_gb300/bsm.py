@@ -28,8 +28,9 @@ EXPORTED = (
     "bsm_last_error", "bsm_status_string", "bsm_copy_color_table", "bsm_vote_tables", "bsm_validate_params",
     "bsm_abi_version", "bsm_set_tuning", "bsm_get_tuning", "bsm_reserve", "bsm_describe_noalloc",
     "bsm_batch_run", "bsm_reserve_batch", "bsm_last_cuda_error", "bsm_server_create", "bsm_server_submit",
-    "bsm_server_poll", "bsm_server_drain", "bsm_server_get_stats", "bsm_server_destroy",
+    "bsm_server_poll", "bsm_server_drain", "bsm_server_get_stats", "bsm_server_destroy", "bsm_debug_set",
 )
+BSM_DEBUG_WITHHOLD_ARRIVALS = 1
 BSM_MAX_BATCH = 1024
 
 BSM_NOALLOC_MAX_PIXELS = 4194304
@@ -69,7 +70,8 @@ class bsm_pair_desc(ctypes.Structure):
 
 
 class bsm_server_config(ctypes.Structure):
-    _fields_ = [("lanes", ctypes.c_int32), ("max_batch", ctypes.c_int32), ("device_budget", ctypes.c_int64)]
+    _fields_ = [("lanes", ctypes.c_int32), ("max_batch", ctypes.c_int32), ("device_budget", ctypes.c_int64),
+                ("max_batch_work", ctypes.c_int64)]
 
 
 class bsm_request(ctypes.Structure):
@@ -138,6 +140,8 @@ def lib():
         L.bsm_server_get_stats.restype = S
         L.bsm_server_destroy.argtypes = [P]
         L.bsm_server_destroy.restype = None
+        L.bsm_debug_set.argtypes = [P, I, I]
+        L.bsm_debug_set.restype = S
         L.bsm_last_cuda_error.argtypes = [P]
         L.bsm_last_cuda_error.restype = ctypes.c_char_p
         L.bsm_batch_run.argtypes = [P, ctypes.POINTER(bsm_pair_desc), I, P]
@@ -160,6 +164,10 @@ def _check(s: int, where: str, ctx: int = 0):
     if s != BSM_OK:
         detail = lib().bsm_last_cuda_error(ctx).decode() if ctx and s == BSM_ERR_CUDA else ""
         raise BsmError(s, where + (f" [{detail}]" if detail else ""))
+
+
+def bsm_debug_set(ctx: int, key: int, value: int) -> None:
+    _check(lib().bsm_debug_set(ctx, key, value), "bsm_debug_set")
 
 
 def bsm_last_cuda_error(ctx: int) -> str:
@@ -358,8 +366,9 @@ class Matcher:
         return self.refine(rgbL, dL, dR, dmax, stream)
 
 
-def bsm_server_create(params: bsm_params, lanes: int = 2, max_batch: int = 64, device_budget: int = 0) -> int:
-    cfg = bsm_server_config(lanes, max_batch, device_budget)
+def bsm_server_create(params: bsm_params, lanes: int = 2, max_batch: int = 64, device_budget: int = 0,
+                      max_batch_work: int = 0) -> int:
+    cfg = bsm_server_config(lanes, max_batch, device_budget, max_batch_work)
     h = ctypes.c_void_p()
     _check(lib().bsm_server_create(ctypes.byref(params), ctypes.byref(cfg), ctypes.byref(h)), "bsm_server_create")
     return h.value

@@ -277,6 +277,15 @@ bsm_status bsm_last_error(bsm_ctx *ctx) {
   return (bsm_status)v;
 }
 
+bsm_status bsm_debug_set(bsm_ctx *ctx, int32_t key, int32_t value) {
+  if (ctx == nullptr) return BSM_ERR_INVALID_ARG;
+  if (key == BSM_DEBUG_WITHHOLD_ARRIVALS && (value == 0 || value == 1)) {
+    ctx->withhold_arrivals = value;
+    return BSM_OK;
+  }
+  return BSM_ERR_INVALID_ARG;
+}
+
 const char *bsm_last_cuda_error(bsm_ctx *ctx) {
   if (ctx == nullptr || ctx->last_cuda == cudaSuccess) return "";
   return cudaGetErrorName(ctx->last_cuda);

@@ -38,6 +38,7 @@ struct CostArgs {
   uint16_t *cost;          // optional, direction 0 only
   uint32_t *status;
   int w, h, dmax, rows;
+  int withhold;            // test hook: skip the mbarrier arrivals so the bounded waits run out
 };
 
 // ---------------------------------------------------------------- TMA bulk copies and mbarriers
@@ -175,7 +176,8 @@ struct CostTask {
 // mbarrier phase, and carries over between the tasks of a persistent CTA). Returns false, in every
 // thread, if a bounded wait gave up.
 template <int NW, int WIN, int DIR, bool CSA, bool ATOMIC>
-__device__ __forceinline__ bool cost_task(const CostTask &t, uint8_t *smem_raw, uint32_t &g, uint32_t *status) {
+__device__ __forceinline__ bool cost_task(const CostTask &t, uint8_t *smem_raw, uint32_t &g, uint32_t *status,
+                                          int withhold = 0) {
   constexpr int R = WIN / 2;
   constexpr int NBITS = 32 * NW;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
@@ -206,6 +208,7 @@ __device__ __forceinline__ bool cost_task(const CostTask &t, uint8_t *smem_raw, 
 
   auto issue = [&](int y, int s) {  // one thread: stage row y into buffer s
     uint32_t *st = stages + s * L.stage_words;
+    if (withhold) return;  // test hook: no arrival, so the phase never completes
     if (y >= 0 && y < h) {
       const int c0 = max(x0, 0), c1 = min(x0 + 32, w);
       const int o0 = max(ox0, 0), o1 = min(ox0 + nocols, w);
@@ -397,8 +400,8 @@ __global__ void __launch_bounds__(1024, 1) cost_wta_kernel(const CostArgs a) {
   t.ye = min(a.h, t.yb + a.rows);
   t.dbase = 0;
   uint32_t g = 0;
-  if (dir == 0) cost_task<NW, WIN, 0, CSA, false>(t, smem_raw, g, a.status);
-  else cost_task<NW, WIN, 1, CSA, false>(t, smem_raw, g, a.status);
+  if (dir == 0) cost_task<NW, WIN, 0, CSA, false>(t, smem_raw, g, a.status, a.withhold);
+  else cost_task<NW, WIN, 1, CSA, false>(t, smem_raw, g, a.status, a.withhold);
 }
 
 // Persistent batch kernel: 8 warps (64 disparities) per CTA; every CTA takes tasks
@@ -538,6 +541,7 @@ cudaError_t launch_cost_wta(const bsm_ctx *ctx, const uint32_t *BL, const uint32
   a.status = ctx->status;
   a.w = w; a.h = h; a.dmax = dmax;
   a.rows = ctx->cost_rows > 0 ? ctx->cost_rows : pick_rows(w, h, ctx->p.agg_window, dmax);
+  a.withhold = ctx->withhold_arrivals;
   switch (ctx->nw) {
     case 1: return launch_win<1, false>(ctx->p.agg_window, a, s);
     case 2: return launch_win<2, false>(ctx->p.agg_window, a, s);

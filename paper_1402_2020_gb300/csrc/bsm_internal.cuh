@@ -74,6 +74,7 @@ struct bsm_ctx {
   uint32_t *plane = nullptr;
   size_t plane_px = 0;
   int batch_rows = 0;       // rows per task of the batched cost kernel
+  int withhold_arrivals = 0;  // test hook: cost kernels skip their mbarrier arrivals
   // Batched execution (bsm_batch_run).
   int sms = 0;
   uint8_t *batch_table_host = nullptr;  // pinned ticket table

@@ -170,9 +170,13 @@ void worker_main(bsm_server *s) {
     // 2. fill free lanes from the queue (arrival order) within the memory budget
     for (Lane &lane : s->lanes) {
       if (!lane.batch.empty() || s->queue.empty()) continue;
+      int64_t work = 0;
       while (!s->queue.empty() && (int)lane.batch.size() < s->cfg.max_batch) {
         Pending &p = s->queue.front();
         if (s->in_use + p.bytes > s->budget) break;  // waits for memory to free up
+        const int64_t wk = (int64_t)p.req.w * p.req.h * p.req.dmax;
+        if (!lane.batch.empty() && s->cfg.max_batch_work > 0 && work + wk > s->cfg.max_batch_work) break;
+        work += wk;
         s->in_use += p.bytes;
         lane.batch.push_back(InFlight{p, nullptr});
         s->queue.pop_front();
@@ -210,7 +214,7 @@ extern "C" {
 bsm_status bsm_server_create(const bsm_params *params, const bsm_server_config *cfg, bsm_server **out) {
   if (params == nullptr || cfg == nullptr || out == nullptr) return BSM_ERR_INVALID_ARG;
   if (cfg->lanes < 1 || cfg->lanes > 8 || cfg->max_batch < 1 || cfg->max_batch > bsm::kMaxBatch ||
-      cfg->device_budget < 0)
+      cfg->device_budget < 0 || cfg->max_batch_work < 0)
     return BSM_ERR_INVALID_ARG;
   const bsm_status v = bsm_validate_params(params);
   if (v != BSM_OK) return v;
