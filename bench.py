@@ -163,6 +163,19 @@ def oracle_sample(cfg, rows):
     return dt, cfg["w"] * rows * cfg["dmax"]
 
 
+def max_over_ranks(values, world, device=None):
+    """Element-wise maximum of per-rank floats over all ranks (identity on one rank). Replicas share no
+    data, so this reduction of their timings is the only collective the benchmark makes."""
+    if world <= 1:
+        return [float(v) for v in values]
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t.cpu()]
+
+
 def dist_init(args):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -269,10 +282,7 @@ def run_batch(args, cfg, world, rank, local):
     clocks = clk.stop()
     t_plain = timed(plain)
     assert bsm.bsm_last_error(ctx) == bsm.BSM_OK
-    if world > 1:
-        tt = torch.tensor([t_batch, t_plain], device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        t_batch, t_plain = float(tt[0]), float(tt[1])
+    t_batch, t_plain = max_over_ranks([t_batch, t_plain], world, dev)
     value = world * units / (t_batch * 1e-3) / 1e9
     line = {
         "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
@@ -490,10 +500,7 @@ def main():
     per = np.array([[ev[i][j].elapsed_time(ev[i][j + 1]) for j in range(4)] for i in range(args.steps)])
     step_ms = per.sum(axis=1)
     t_step = float(step_ms.mean())
-    if world > 1:
-        tt = torch.tensor([t_step], device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        t_step = float(tt.item())
+    t_step = max_over_ranks([t_step], world, dev)[0]
     units = w * h * dmax
     value = world * units / (t_step * 1e-3) / 1e9
 
@@ -511,10 +518,7 @@ def main():
         bsm.bsm_match_host(ctx, hl.data_ptr(), hr.data_ptr(), w, h, pitch, dmax, ho.data_ptr(), s)
         e2e_t.append(time.perf_counter() - t0)
     e2e_s = float(np.mean(e2e_t))
-    if world > 1:
-        tt = torch.tensor([e2e_s], device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        e2e_s = float(tt.item())
+    e2e_s = max_over_ranks([e2e_s], world, dev)[0]
     e2e_value = world * units / e2e_s / 1e9
 
     # roofline of the dominant kernel: fused cost/aggregation/WTA, both reference views per launch

@@ -18,8 +18,13 @@ _lib = None
 def lib():
     global _lib
     if _lib is None:
-        path = _build.build()
-        L = ctypes.CDLL(path)
+        _lib = bind(ctypes.CDLL(_build.build()))
+    return _lib
+
+
+def bind(L):
+    """Declare the C signatures of an oracle library handle (the built one, or a test's variant)."""
+    if True:
         P = ctypes.c_void_p
         I = ctypes.c_int
         D = ctypes.c_double
@@ -45,8 +50,7 @@ def lib():
         L.oracle_refine.restype = I
         L.oracle_refine_region.argtypes = [P, I, P, P, I, I, I, I, D, D, I, I, I, I, P]
         L.oracle_refine_region.restype = I
-        _lib = L
-    return _lib
+    return L
 
 
 def _p(a):

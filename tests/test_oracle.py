@@ -5,6 +5,7 @@ forms, invariants, special cases that reduce to a library routine (numpy bit cou
 sums, numpy argmin) and hand-built cases whose answer follows from the equation by hand.
 """
 import math
+import sys
 import os
 
 import numpy as np
@@ -143,6 +144,38 @@ def test_mask_keeps_exactly_the_k_nearest_colours(orc):
     got = [(int(Phi[1, x, 0]) >> i) & 1 for i in range(32)]
     assert got == [int(wv <= T) for wv in w_i]
     assert sum(got) >= k
+
+
+def test_mask_weight_uses_both_pair_points(orc):
+    # p_i is the centre and q_i walks the ramp: w_i = max(SAD(x, x), SAD(x, q_i)) = SAD(x, q_i) (Eq. 5),
+    # so the mask keeps the k pairs whose q lies nearest in lightness.
+    ramp = np.arange(0, 31 * 8, 8)
+    img = gray_image(np.tile(ramp, (3, 1)))
+    x = 15
+    offsets = list(range(1, 16)) + list(range(-15, 0)) + [0, 0]
+    pairs = np.array([(0, 0, o, 0) for o in offsets], np.int8)
+    Ls = [orc.lab(int(v), int(v), int(v))[0] for v in ramp]
+    w_i = [abs(Ls[x + o] - Ls[x]) for o in offsets]
+    k = 11
+    T = sorted(w_i)[k - 1]
+    _, Phi = orc.describe(img, pairs, k=k)
+    assert [(int(Phi[1, x, 0]) >> i) & 1 for i in range(32)] == [int(wv <= T) for wv in w_i]
+
+
+def test_mask_exactly_k_bits_when_weights_are_distinct(orc):
+    # weights strictly increase with the offset (one-sided ramp, q at the centre): T is the k-th
+    # smallest of distinct values, so exactly k bits are set and they are the first k pairs.
+    ramp = np.arange(0, 64 * 4, 4)[:64]
+    img = gray_image(np.tile(ramp, (3, 1)))
+    x = 1
+    pairs = np.array([(min(1 + i, 31), 0, 0, 0) for i in range(32)], np.int8)
+    w_i = [orc.lab(*(3 * [int(ramp[x + 1 + i])]))[0] - orc.lab(*(3 * [int(ramp[x])]))[0] for i in range(31)]
+    assert all(b > a for a, b in zip(w_i, w_i[1:]))
+    for k in (1, 8, 20):
+        _, Phi = orc.describe(img, pairs, k=k)
+        word = int(Phi[1, x, 0])
+        assert bin(word).count("1") == k
+        assert word == (1 << k) - 1
 
 
 def test_mask_popcount_at_least_k(orc):
@@ -341,6 +374,36 @@ def test_refine_weighted_vote_hand_case(orc):
     out = orc.refine(img, dL, valid, 8, R=15)
     assert out[2, 2] == (3 if w3 > w5 else 5)
     assert w3 != w5
+
+
+def test_refine_distance_term_decides(orc):
+    # Eq. 10's spatial term: a voter one pixel away with a slightly different colour (disparity 3)
+    # against a voter ten pixels away with the same colour (disparity 5). Only the bilateral weight
+    # with both terms makes the near voter win.
+    img = np.full((1, 21, 3), 100, np.uint8)
+    img[0, 11] = (110, 110, 110)
+    dL = np.zeros((1, 21), np.int32)
+    valid = np.zeros((1, 21), np.uint8)
+    valid[0, 11], dL[0, 11] = 1, 3
+    valid[0, 20], dL[0, 20] = 1, 5
+    Ec, Es = orc.vote_tables(9.0, 16.0, 15)
+    c = abs(orc.lab(110, 110, 110)[0] - orc.lab(100, 100, 100)[0])
+    near = (int(Ec[c]) * int(Es[1])) >> 15
+    far = (int(Ec[0]) * int(Es[100])) >> 15
+    assert near > far and int(Ec[c]) < int(Ec[0])  # the case separates the two readings
+    out = orc.refine(img, dL, valid, 8, R=15)
+    assert out[0, 10] == 3
+
+
+def test_refine_tie_goes_to_smallest_disparity(orc):
+    # two voters with identical colour and distance vote for disparities 6 and 2 with equal weight
+    img = np.full((1, 11, 3), 80, np.uint8)
+    dL = np.zeros((1, 11), np.int32)
+    valid = np.zeros((1, 11), np.uint8)
+    valid[0, 3], dL[0, 3] = 1, 6
+    valid[0, 7], dL[0, 7] = 1, 2
+    out = orc.refine(img, dL, valid, 8, R=5)
+    assert out[0, 5] == 2
 
 
 def test_refine_fallback_on_the_row(orc):
