@@ -57,6 +57,7 @@ def parse():
     ap.add_argument("--cost-rows", type=int, default=0, help="rows per CTA of the cost kernel (0: heuristic)")
     ap.add_argument("--cost-popc-plain", type=int, default=0, help="1: plain popcount in the cost kernel")
     ap.add_argument("--batch-rows", type=int, default=0, help="rows per task of the batched cost kernel (0: 64)")
+    ap.add_argument("--no-autotune", action="store_true", help="skip the launch-shape autotuner")
     ap.add_argument("--requests", type=int, default=2000, help="serving stream length (c5)")
     ap.add_argument("--rho", type=float, default=0.7, help="arrival rate as a fraction of measured capacity (c5)")
     ap.add_argument("--lanes", type=int, default=2, help="serving lanes (c5)")
@@ -247,6 +248,11 @@ def run_batch(args, cfg, world, rank, local):
     s = stream.cuda_stream
     bsm.bsm_reserve(ctx, max(t["w"] for t in ts), max(t["h"] for t in ts))
     bsm.bsm_reserve_batch(ctx, sum(t["w"] * t["h"] for t in ts))
+    if not args.no_autotune and args.batch_rows == 0:
+        from paper_1402_2020_gb300 import autotune
+
+        with torch.cuda.stream(stream):
+            autotune.tune_batch(ctx, descs, N_BITS, AGG)
 
     def batched():
         bsm.bsm_batch_run(ctx, descs, s)
@@ -453,6 +459,10 @@ def main():
     params = bsm.make_params(pairs, window_S=WINDOW_S, agg_window=AGG, dmax=dmax, vote_radius=VOTE_R)
     ctx = bsm.bsm_create(params)
     bsm.bsm_set_tuning(ctx, args.cost_rows, args.cost_popc_plain, args.batch_rows)
+    if not args.no_autotune and args.cost_rows == 0:
+        from paper_1402_2020_gb300 import autotune
+
+        autotune.tune_cost(ctx, N_BITS, AGG, w, h, dmax)
     stream = torch.cuda.Stream(device=dev)
     s = stream.cuda_stream
     nw = N_BITS // 32

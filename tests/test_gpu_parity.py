@@ -245,3 +245,22 @@ def test_argument_errors_are_synchronous(B):
         B.bsm_describe(c.ctx, x, 4, 4, 12, x.data_ptr() + 4, x)  # misaligned plane
     assert B.bsm_last_error(c.ctx) == B.BSM_OK
     c.close()
+
+
+def test_autotuner_applies_a_candidate_and_bits_stay(B, orc):
+    from paper_1402_2020_gb300 import autotune
+
+    w, h, dmax = 150, 70, 48
+    pairs = synth.pair_table(256, 31, seed=260)
+    c = Ctx(B, pairs, agg_window=5, dmax=dmax)
+    t = autotune.tune_cost(c.ctx, 256, 5, w, h, dmax, reps=1, use_cache=False)
+    assert t["cost_rows"] in autotune.COST_ROWS and t["cost_popc_plain"] in (0, 1)
+    assert B.bsm_get_tuning(c.ctx)["cost_rows"] == t["cost_rows"]
+    l, r, _ = synth.stereo_pair(w, h, dmax, seed=261)
+    BL, PL, _, _ = c.describe(l)
+    BR, PR, _, _ = c.describe(r)
+    dL, _, _ = c.cost_wta(BL, PL, BR, PR, dmax)
+    oBL, oPL = orc.describe(l, pairs)
+    oBR, _ = orc.describe(r, pairs)
+    assert (dL.cpu().numpy() == orc.wta(oBL, oPL, oBR, dmax, 5, 0)).all()
+    c.close()
