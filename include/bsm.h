@@ -293,7 +293,9 @@ typedef struct {
   int32_t cost_popc_plain; /* 1: plain POPC per word in the cost kernel; 0: carry-save adder tree
                               (n_bits = 256 only) */
   int32_t batch_rows;      /* rows per task of bsm_batch_run's cost stage: 0 (64) or 8..512 */
-  int32_t reserved[5];     /* must be zero */
+  int32_t cost_variant;    /* 0: automatic (two columns per lane for n_bits 128 and 256, else one);
+                              1: one column per lane; 2: two columns per lane (n_bits 128 or 256) */
+  int32_t reserved[4];     /* must be zero */
 } bsm_tuning;
 
 /* Set / read the context's launch shapes. Synchronous, host only. */

@@ -17,6 +17,7 @@ from . import bsm
 
 COST_ROWS = (16, 32, 64, 128, 256)
 POPC_FORMS = (0, 1)
+VARIANTS = (1, 2)  # one or two columns per lane
 BATCH_ROWS = (32, 64, 128)
 
 
@@ -34,7 +35,7 @@ def bucket(v: int) -> int:
 
 
 def key(gpu: str, n_bits: int, win: int, w: int, h: int, dmax: int) -> str:
-    return f"{gpu}|n{n_bits}|win{win}|d{bucket(dmax)}|px{bucket(w * h)}"
+    return f"{gpu}|n{n_bits}|win{win}|d{bucket(dmax)}|px{bucket(w * h)}|v2"
 
 
 def load() -> dict:
@@ -66,10 +67,10 @@ def choose(candidates, measure):
     return best, timings
 
 
-def _time_cost(ctx, planes, w, h, dmax, rows, popc, reps, torch):
+def _time_cost(ctx, planes, w, h, dmax, rows, popc, variant, reps, torch):
     dL = torch.empty((h, w), dtype=torch.int32, device="cuda")
     dR = torch.empty_like(dL)
-    bsm.bsm_set_tuning(ctx, rows, popc, 0)
+    bsm.bsm_set_tuning(ctx, rows, popc, 0, variant)
     s = torch.cuda.current_stream()
     for _ in range(2):
         bsm.bsm_cost_aggregate_wta(ctx, *planes, w, h, dmax, dL, dR)
@@ -83,7 +84,7 @@ def _time_cost(ctx, planes, w, h, dmax, rows, popc, reps, torch):
 
 
 def tune_cost(ctx, n_bits: int, win: int, w: int, h: int, dmax: int, reps: int = 3, use_cache: bool = True) -> dict:
-    """Best (cost_rows, cost_popc_plain) for this workload shape; applied to ctx and cached."""
+    """Best (cost_rows, cost_popc_plain, cost_variant) for this workload shape; applied to ctx and cached."""
     import torch
 
     gpu = torch.cuda.get_device_name()
@@ -95,16 +96,17 @@ def tune_cost(ctx, n_bits: int, win: int, w: int, h: int, dmax: int, reps: int =
         planes = [torch.randint(-2 ** 31, 2 ** 31 - 1, (h, w, nw), dtype=torch.int32, device="cuda", generator=gen)
                   for _ in range(4)]
         forms = POPC_FORMS if nw == 8 else (0,)
-        cands = [(r, p) for r in COST_ROWS if r <= max(16, 2 * h) for p in forms]
-        best, timings = choose(cands, lambda c: _time_cost(ctx, planes, w, h, dmax, c[0], c[1], reps, torch))
-        cache[k] = {"cost_rows": best[0], "cost_popc_plain": best[1], "timings_ms": timings}
+        variants = VARIANTS if nw in (4, 8) else (1,)
+        cands = [(r, p, v) for v in variants for r in COST_ROWS if r <= max(16, 2 * h) for p in forms]
+        best, timings = choose(cands, lambda c: _time_cost(ctx, planes, w, h, dmax, c[0], c[1], c[2], reps, torch))
+        cache[k] = {"cost_rows": best[0], "cost_popc_plain": best[1], "cost_variant": best[2], "timings_ms": timings}
         if use_cache:
             merged = load()
             merged[k] = cache[k]
             store(merged)
     t = cache[k]
     cur = bsm.bsm_get_tuning(ctx)
-    bsm.bsm_set_tuning(ctx, t["cost_rows"], t["cost_popc_plain"], cur["batch_rows"])
+    bsm.bsm_set_tuning(ctx, t["cost_rows"], t["cost_popc_plain"], cur["batch_rows"], t.get("cost_variant", 0))
     return t
 
 
@@ -120,7 +122,7 @@ def tune_batch(ctx, descs, n_bits: int, win: int, reps: int = 2, use_cache: bool
         cur = bsm.bsm_get_tuning(ctx)
 
         def measure(rows):
-            bsm.bsm_set_tuning(ctx, cur["cost_rows"], cur["cost_popc_plain"], rows)
+            bsm.bsm_set_tuning(ctx, cur["cost_rows"], cur["cost_popc_plain"], rows, cur["cost_variant"])
             s = torch.cuda.current_stream()
             bsm.bsm_batch_run(ctx, descs)
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -139,5 +141,5 @@ def tune_batch(ctx, descs, n_bits: int, win: int, reps: int = 2, use_cache: bool
             store(merged)
     t = cache[k]
     cur = bsm.bsm_get_tuning(ctx)
-    bsm.bsm_set_tuning(ctx, cur["cost_rows"], cur["cost_popc_plain"], t["batch_rows"])
+    bsm.bsm_set_tuning(ctx, cur["cost_rows"], cur["cost_popc_plain"], t["batch_rows"], cur["cost_variant"])
     return t

@@ -247,14 +247,17 @@ bsm_status bsm_reserve(bsm_ctx *ctx, int32_t max_w, int32_t max_h) {
 
 bsm_status bsm_set_tuning(bsm_ctx *ctx, const bsm_tuning *t) {
   if (ctx == nullptr || t == nullptr) return BSM_ERR_INVALID_ARG;
-  for (int i = 0; i < 5; ++i)
+  for (int i = 0; i < 4; ++i)
     if (t->reserved[i] != 0) return BSM_ERR_INVALID_ARG;
+  if (t->cost_variant < 0 || t->cost_variant > 2) return BSM_ERR_INVALID_ARG;
+  if (t->cost_variant == 2 && ctx->nw != 4 && ctx->nw != 8) return BSM_ERR_UNSUPPORTED;
   if (t->cost_rows != 0 && (t->cost_rows < 8 || t->cost_rows > 512)) return BSM_ERR_INVALID_ARG;
   if (t->batch_rows != 0 && (t->batch_rows < 8 || t->batch_rows > 512)) return BSM_ERR_INVALID_ARG;
   if (t->cost_popc_plain != 0 && t->cost_popc_plain != 1) return BSM_ERR_INVALID_ARG;
   ctx->cost_rows = t->cost_rows;
   ctx->cost_plain_popc = t->cost_popc_plain;
   ctx->batch_rows = t->batch_rows;
+  ctx->cost_variant = t->cost_variant;
   return BSM_OK;
 }
 
@@ -264,6 +267,7 @@ bsm_status bsm_get_tuning(bsm_ctx *ctx, bsm_tuning *t) {
   t->cost_rows = ctx->cost_rows;
   t->cost_popc_plain = ctx->cost_plain_popc;
   t->batch_rows = ctx->batch_rows;
+  t->cost_variant = ctx->cost_variant;
   return BSM_OK;
 }
 

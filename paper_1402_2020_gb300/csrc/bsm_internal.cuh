@@ -74,6 +74,7 @@ struct bsm_ctx {
   uint32_t *plane = nullptr;
   size_t plane_px = 0;
   int batch_rows = 0;       // rows per task of the batched cost kernel
+  int cost_variant = 0;     // 0 automatic, 1 one column per lane, 2 two columns per lane
   int withhold_arrivals = 0;  // test hook: cost kernels skip their mbarrier arrivals
   // Batched execution (bsm_batch_run).
   int sms = 0;
@@ -110,6 +111,10 @@ cudaError_t launch_cost_wta(const bsm_ctx *ctx, const uint32_t *BL, const uint32
 cudaError_t prepare_describe_batch(const bsm_ctx *ctx, int *grid);
 cudaError_t prepare_cost_batch(const bsm_ctx *ctx, int *grid);
 cudaError_t prepare_refine_batch(const bsm_ctx *ctx, int *grid);
+bool cost2_supported(const bsm_ctx *ctx);
+cudaError_t launch_cost2(const bsm_ctx *ctx, const uint32_t *BL, const uint32_t *PhiL, const uint32_t *BR,
+                         const uint32_t *PhiR, int w, int h, int dmax, int32_t *dL, int32_t *dR, uint16_t *cost,
+                         cudaStream_t s);
 cudaError_t launch_refine(const bsm_ctx *ctx, const uint8_t *rgb, int pitch, const int32_t *dL, const int32_t *dR,
                           int w, int h, int dmax, int32_t *out, cudaStream_t s);
 

@@ -99,9 +99,10 @@ def test_describe_bit_exact(B, orc, w, h, n, k, pad):
     c.close()
 
 
-@pytest.mark.parametrize("win,n", [(1, 256), (3, 64), (5, 256), (7, 128), (5, 32)])
-def test_cost_volume_bit_exact(B, orc, win, n):
-    w, h, dmax = 61, 29, 24
+@pytest.mark.parametrize("win,n,dmax", [(1, 256, 24), (3, 64, 24), (5, 256, 24), (7, 128, 24), (5, 32, 24),
+                                        (3, 256, 150), (7, 256, 137), (1, 128, 140)])
+def test_cost_volume_bit_exact(B, orc, win, n, dmax):
+    w, h = 61, 29
     l, r, _ = synth.stereo_pair(w, h, dmax, seed=200 + win)
     pairs = synth.pair_table(n, 31, seed=201)
     c = Ctx(B, pairs, agg_window=win, dmax=dmax)
@@ -120,14 +121,17 @@ def test_cost_volume_bit_exact(B, orc, win, n):
     c.close()
 
 
-@pytest.mark.parametrize("rows,plain", [(8, 0), (8, 1), (16, 1), (128, 0), (512, 1)])
-def test_tuning_does_not_change_bits(B, orc, rows, plain):
-    w, h, dmax = 77, 41, 40
+@pytest.mark.parametrize("rows,plain,variant,dmax", [(8, 0, 1, 40), (8, 1, 1, 40), (16, 1, 2, 40), (128, 0, 2, 40),
+                                                    (512, 1, 1, 40), (8, 0, 2, 200), (32, 1, 2, 129),
+                                                    (16, 0, 1, 200)])
+def test_tuning_does_not_change_bits(B, orc, rows, plain, variant, dmax):
+    w, h = 77, 41
     l, r, _ = synth.stereo_pair(w, h, dmax, seed=250)
     pairs = synth.pair_table(256, 31, seed=251)
     c = Ctx(B, pairs, agg_window=5, dmax=dmax)
-    B.bsm_set_tuning(c.ctx, rows, plain)
-    assert B.bsm_get_tuning(c.ctx) == {"cost_rows": rows, "cost_popc_plain": plain, "batch_rows": 0}
+    B.bsm_set_tuning(c.ctx, rows, plain, 0, variant)
+    assert B.bsm_get_tuning(c.ctx) == {"cost_rows": rows, "cost_popc_plain": plain, "batch_rows": 0,
+                                       "cost_variant": variant}
     BL, PL, _, _ = c.describe(l)
     BR, PR, _, _ = c.describe(r)
     dL, dR, cost = c.cost_wta(BL, PL, BR, PR, dmax, want_cost=True)
@@ -165,16 +169,18 @@ def test_wta_and_refine_teddy_shape(B, orc, win):
     c.close()
 
 
+@pytest.mark.parametrize("n", [64, 256])
 @pytest.mark.parametrize("w,h,dmax,win", [
     (20, 9, 40, 5),    # dmax > width: most matches fall outside the image
     (3, 3, 1, 1),      # dmax = 1
     (1, 12, 8, 3),
     (130, 17, 256, 5), # the largest dmax on a narrow image
     (95, 33, 13, 7),   # dmax not a multiple of 8
+    (70, 9, 64, 3),    # 64 columns plus a ragged tail
 ])
-def test_edge_shapes_full_chain(B, orc, w, h, dmax, win):
+def test_edge_shapes_full_chain(B, orc, w, h, dmax, win, n):
     l, r, _ = synth.stereo_pair(w, h, dmax, seed=300 + w)
-    pairs = synth.pair_table(64, 31, seed=301)
+    pairs = synth.pair_table(n, 31, seed=301)
     c = Ctx(B, pairs, agg_window=win, dmax=dmax, vote_radius=4)
     BL, PL, dl, pitch = c.describe(l, 1)
     BR, PR, _, _ = c.describe(r, 1)
