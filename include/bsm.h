@@ -290,8 +290,9 @@ bsm_status bsm_vote_tables(int32_t lambda_c, int32_t lambda_e, int32_t nc, int32
  */
 typedef struct {
   int32_t cost_rows;       /* rows per CTA band of the cost/aggregation/WTA kernel: 0 or 8..512 */
-  int32_t cost_popc_plain; /* 1: plain POPC per word in the cost kernel; 0: carry-save adder tree
-                              (n_bits = 256 only) */
+  int32_t cost_popc_plain; /* popcount form of the cost kernel (n_bits = 256; results identical):
+                              0 carry-save tree over 8 words, 1 plain POPC per word, 2 two 3-word
+                              carry-save adders plus 2 plain words (two-column kernel only) */
   int32_t batch_rows;      /* rows per task of bsm_batch_run's cost stage: 0 (64) or 8..512 */
   int32_t cost_variant;    /* 0: automatic (two columns per lane for n_bits 128 and 256, else one);
                               1: one column per lane; 2: two columns per lane (n_bits 128 or 256) */

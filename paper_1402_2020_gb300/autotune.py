@@ -16,7 +16,7 @@ import os
 from . import bsm
 
 COST_ROWS = (16, 32, 64, 128, 256)
-POPC_FORMS = (0, 1)
+POPC_FORMS = (0, 1, 2)
 VARIANTS = (1, 2)  # one or two columns per lane
 BATCH_ROWS = (32, 64, 128)
 
@@ -35,7 +35,7 @@ def bucket(v: int) -> int:
 
 
 def key(gpu: str, n_bits: int, win: int, w: int, h: int, dmax: int) -> str:
-    return f"{gpu}|n{n_bits}|win{win}|d{bucket(dmax)}|px{bucket(w * h)}|v2"
+    return f"{gpu}|n{n_bits}|win{win}|d{bucket(dmax)}|px{bucket(w * h)}|v3"
 
 
 def load() -> dict:
@@ -97,7 +97,8 @@ def tune_cost(ctx, n_bits: int, win: int, w: int, h: int, dmax: int, reps: int =
                   for _ in range(4)]
         forms = POPC_FORMS if nw == 8 else (0,)
         variants = VARIANTS if nw in (4, 8) else (1,)
-        cands = [(r, p, v) for v in variants for r in COST_ROWS if r <= max(16, 2 * h) for p in forms]
+        cands = [(r, p, v) for v in variants for r in COST_ROWS if r <= max(16, 2 * h) for p in forms
+                 if not (v == 1 and p == 2)]
         best, timings = choose(cands, lambda c: _time_cost(ctx, planes, w, h, dmax, c[0], c[1], c[2], reps, torch))
         cache[k] = {"cost_rows": best[0], "cost_popc_plain": best[1], "cost_variant": best[2], "timings_ms": timings}
         if use_cache:

@@ -253,7 +253,7 @@ bsm_status bsm_set_tuning(bsm_ctx *ctx, const bsm_tuning *t) {
   if (t->cost_variant == 2 && ctx->nw != 4 && ctx->nw != 8) return BSM_ERR_UNSUPPORTED;
   if (t->cost_rows != 0 && (t->cost_rows < 8 || t->cost_rows > 512)) return BSM_ERR_INVALID_ARG;
   if (t->batch_rows != 0 && (t->batch_rows < 8 || t->batch_rows > 512)) return BSM_ERR_INVALID_ARG;
-  if (t->cost_popc_plain != 0 && t->cost_popc_plain != 1) return BSM_ERR_INVALID_ARG;
+  if (t->cost_popc_plain < 0 || t->cost_popc_plain > 2) return BSM_ERR_INVALID_ARG;
   ctx->cost_rows = t->cost_rows;
   ctx->cost_plain_popc = t->cost_popc_plain;
   ctx->batch_rows = t->batch_rows;

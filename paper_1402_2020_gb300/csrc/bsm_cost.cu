@@ -510,7 +510,7 @@ cudaError_t cost_batch_dispatch(const bsm_ctx *ctx, BatchHeader *hdr, const Batc
     case 2: return launch_batch_win<2, false>(win, hdr, pairs, ctx->status, grid, prepare, grid_out, s);
     case 4: return launch_batch_win<4, false>(win, hdr, pairs, ctx->status, grid, prepare, grid_out, s);
     case 8:
-      return ctx->cost_plain_popc
+      return ctx->cost_plain_popc == 1
                  ? launch_batch_win<8, false>(win, hdr, pairs, ctx->status, grid, prepare, grid_out, s)
                  : launch_batch_win<8, true>(win, hdr, pairs, ctx->status, grid, prepare, grid_out, s);
     default: return cudaErrorInvalidValue;
@@ -551,7 +551,7 @@ cudaError_t launch_cost_wta(const bsm_ctx *ctx, const uint32_t *BL, const uint32
     case 2: return launch_win<2, false>(ctx->p.agg_window, a, s);
     case 4: return launch_win<4, false>(ctx->p.agg_window, a, s);
     case 8:
-      return ctx->cost_plain_popc ? launch_win<8, false>(ctx->p.agg_window, a, s)
+      return ctx->cost_plain_popc == 1 ? launch_win<8, false>(ctx->p.agg_window, a, s)
                                   : launch_win<8, true>(ctx->p.agg_window, a, s);
     default: return cudaErrorInvalidValue;
   }

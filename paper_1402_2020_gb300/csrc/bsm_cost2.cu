@@ -45,24 +45,36 @@ __device__ __forceinline__ uint32_t lop3_maj(uint32_t a, uint32_t b, uint32_t c)
   asm("lop3.b32 %0, %1, %2, %3, 0xE8;" : "=r"(r) : "r"(a), "r"(b), "r"(c));
   return r;
 }
+__device__ __forceinline__ uint32_t vmin_u16x2(uint32_t a, uint32_t b) {
+  uint32_t r;
+  asm("min.u16x2 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(b));
+  return r;
+}
 __device__ __forceinline__ uint32_t lop3_xor_and(uint32_t a, uint32_t b, uint32_t m) {
   uint32_t r;
   asm("lop3.b32 %0, %1, %2, %3, 0x28;" : "=r"(r) : "r"(a), "r"(b), "r"(m));
   return r;
 }
 
-template <int NW, bool CSA>
+// Popcount forms of the masked words (results identical): 0 = carry-save tree over all 8 words
+// (4 POPC), 1 = one POPC per word, 2 = two 3-word carry-save adders and 2 plain words (6 POPC).
+template <int NW, int PM>
 __device__ __forceinline__ uint32_t masked_hamming(const uint32_t (&b)[NW], const uint32_t (&o)[NW],
                                                    const uint32_t (&m)[NW]) {
   uint32_t v[NW];
 #pragma unroll
   for (int j = 0; j < NW; ++j) v[j] = lop3_xor_and(b[j], o[j], m[j]);
-  if constexpr (CSA && NW == 8) {
+  if constexpr (PM == 0 && NW == 8) {
     const uint32_t s1 = lop3_xor3(v[0], v[1], v[2]), c1 = lop3_maj(v[0], v[1], v[2]);
     const uint32_t s2 = lop3_xor3(v[3], v[4], v[5]), c2 = lop3_maj(v[3], v[4], v[5]);
     const uint32_t s3 = lop3_xor3(s1, s2, v[6]), c3 = lop3_maj(s1, s2, v[6]);
     const uint32_t s4 = lop3_xor3(c1, c2, c3), c4 = lop3_maj(c1, c2, c3);
     return (uint32_t)__popc(s3) + (uint32_t)__popc(v[7]) + 2u * (uint32_t)__popc(s4) + 4u * (uint32_t)__popc(c4);
+  } else if constexpr (PM == 2 && NW == 8) {
+    const uint32_t s1 = lop3_xor3(v[0], v[1], v[2]), c1 = lop3_maj(v[0], v[1], v[2]);
+    const uint32_t s2 = lop3_xor3(v[3], v[4], v[5]), c2 = lop3_maj(v[3], v[4], v[5]);
+    return (uint32_t)__popc(s1) + (uint32_t)__popc(s2) + (uint32_t)__popc(v[6]) + (uint32_t)__popc(v[7]) +
+           2u * ((uint32_t)__popc(c1) + (uint32_t)__popc(c2));
   } else {
     uint32_t c = 0;
 #pragma unroll
@@ -114,7 +126,7 @@ size_t cost2_smem_bytes(int nd, int win, int nthreads) {
   return b;
 }
 
-template <int NW, int WIN, int DIR, bool CSA, bool SPLIT>
+template <int NW, int WIN, int DIR, int PM, bool SPLIT, bool PK>
 __device__ __forceinline__ void cost2_body(const Cost2Args &a, uint8_t *smem_raw) {
   constexpr int R = WIN / 2;
   constexpr int OUTC = 64 - 2 * R;
@@ -127,13 +139,13 @@ __device__ __forceinline__ void cost2_body(const Cost2Args &a, uint8_t *smem_raw
   uint32_t *keys = stages + 2 * S.words;  // [2][nwarps][64]
   uint4 *ring = reinterpret_cast<uint4 *>(keys + 2 * nwarps * 64);
 
-  const int dr = (int)blockIdx.z % a.ndr;
+  const int dr = (int)blockIdx.x % a.ndr;  // sibling disparity ranges run side by side and share L2
   const uint32_t *__restrict__ Bref = a.B[DIR];
   const uint32_t *__restrict__ Phiref = a.Phi[DIR];
   const uint32_t *__restrict__ Both = a.O[DIR];
   int32_t *__restrict__ disp = a.disp[DIR];
   const int w = a.w, h = a.h, dmax = a.dmax;
-  const int x0 = (int)blockIdx.x * OUTC - R;       // column of lane 0's first column
+  const int x0 = (int)(blockIdx.x / a.ndr) * OUTC - R;  // column of lane 0's first column
   const int xa = x0 + 2 * lane, xb = xa + 1;       // this lane's two columns
   const int yb = (int)blockIdx.y * a.rows, ye = min(h, yb + a.rows);
   const int dbase = dr * nd;
@@ -215,12 +227,12 @@ __device__ __forceinline__ void cost2_body(const Cost2Args &a, uint8_t *smem_raw
         uint32_t ca, cb;
         if constexpr (DIR == 0) {
           load_desc<NW>(S.oth(st, pbase - dd), q, o_new);  // first column at d; second reuses d - 1's
-          ca = masked_hamming<NW, CSA>(ba, o_new, ma);
-          cb = masked_hamming<NW, CSA>(bb, o_keep, mb);
+          ca = masked_hamming<NW, PM>(ba, o_new, ma);
+          cb = masked_hamming<NW, PM>(bb, o_keep, mb);
         } else {
           load_desc<NW>(S.oth(st, pbase + dd + 1), q, o_new);  // second column at d; first reuses it
-          ca = masked_hamming<NW, CSA>(ba, o_keep, ma);
-          cb = masked_hamming<NW, CSA>(bb, o_new, mb);
+          ca = masked_hamming<NW, PM>(ba, o_keep, ma);
+          cb = masked_hamming<NW, PM>(bb, o_new, mb);
         }
 #pragma unroll
         for (int j = 0; j < NW; ++j) o_keep[j] = o_new[j];
@@ -254,6 +266,7 @@ __device__ __forceinline__ void cost2_body(const Cost2Args &a, uint8_t *smem_raw
     const int yo = y - R;
     if (yo >= yb) {
       uint32_t ka = 0xFFFFFFFFu, kb = 0xFFFFFFFFu;
+      uint32_t pa = 0xFFFFFFFFu, pb = 0xFFFFFFFFu;  // packed 16-bit keys (A << 3 | dd) when PK
 #pragma unroll
       for (int j = 0; j < kDP; ++j) {
         // Column 2l sums offsets -R..R of 2l, column 2l+1 those of 2l+1. Lane l-t holds columns
@@ -279,13 +292,23 @@ __device__ __forceinline__ void cost2_body(const Cost2Args &a, uint8_t *smem_raw
         }
         const int de = d0 + 2 * j;
         const uint32_t a_lo = Aa & 0xFFFFu, a_hi = Aa >> 16, b_lo = Ab & 0xFFFFu, b_hi = Ab >> 16;
-        if (de < dmax) {
-          ka = min(ka, (a_lo << 10) | (uint32_t)de);
-          kb = min(kb, (b_lo << 10) | (uint32_t)de);
-        }
-        if (de + 1 < dmax) {
-          ka = min(ka, (a_hi << 10) | (uint32_t)(de + 1));
-          kb = min(kb, (b_hi << 10) | (uint32_t)(de + 1));
+        if constexpr (PK) {
+          // A < 2^13, so A << 3 | dd fits a 16-bit half; one multiply-add forms both halves' keys
+          const uint32_t dd2 = (uint32_t)(2 * j) | ((uint32_t)(2 * j + 1) << 16);
+          uint32_t ea = Aa * 8u + dd2, eb = Ab * 8u + dd2;
+          if (de >= dmax) { ea |= 0xFFFFu; eb |= 0xFFFFu; }
+          if (de + 1 >= dmax) { ea |= 0xFFFF0000u; eb |= 0xFFFF0000u; }
+          pa = vmin_u16x2(pa, ea);
+          pb = vmin_u16x2(pb, eb);
+        } else {
+          if (de < dmax) {
+            ka = min(ka, (a_lo << 10) | (uint32_t)de);
+            kb = min(kb, (b_lo << 10) | (uint32_t)de);
+          }
+          if (de + 1 < dmax) {
+            ka = min(ka, (a_hi << 10) | (uint32_t)(de + 1));
+            kb = min(kb, (b_hi << 10) | (uint32_t)(de + 1));
+          }
         }
         if (DIR == 0 && a.cost != nullptr) {
           if (2 * lane >= R && 2 * lane < 64 - R && ina) {
@@ -300,6 +323,11 @@ __device__ __forceinline__ void cost2_body(const Cost2Args &a, uint8_t *smem_raw
           }
         }
       }
+      if constexpr (PK) {
+        const uint32_t a16 = min(pa & 0xFFFFu, pa >> 16), b16 = min(pb & 0xFFFFu, pb >> 16);
+        ka = a16 == 0xFFFFu ? 0xFFFFFFFFu : ((a16 >> 3) << 10) | (uint32_t)(d0 + (a16 & 7u));
+        kb = b16 == 0xFFFFu ? 0xFFFFFFFFu : ((b16 >> 3) << 10) | (uint32_t)(d0 + (b16 & 7u));
+      }
       keys[(it & 1) * nwarps * 64 + warp * 64 + 2 * lane] = ka;
       keys[(it & 1) * nwarps * 64 + warp * 64 + 2 * lane + 1] = kb;
     }
@@ -309,11 +337,11 @@ __device__ __forceinline__ void cost2_body(const Cost2Args &a, uint8_t *smem_raw
   if (warp == 0 && y_first + n_it - 1 - R >= yb) reduce_keys(n_it - 1);
 }
 
-template <int NW, int WIN, bool CSA, bool SPLIT>
+template <int NW, int WIN, int PM, bool SPLIT, bool PK>
 __global__ void __launch_bounds__(512, 1) cost2_kernel(const Cost2Args a) {
   extern __shared__ __align__(16) uint8_t smem_raw[];
-  if ((int)blockIdx.z < a.ndr) cost2_body<NW, WIN, 0, CSA, SPLIT>(a, smem_raw);
-  else cost2_body<NW, WIN, 1, CSA, SPLIT>(a, smem_raw);
+  if (blockIdx.z == 0) cost2_body<NW, WIN, 0, PM, SPLIT, PK>(a, smem_raw);
+  else cost2_body<NW, WIN, 1, PM, SPLIT, PK>(a, smem_raw);
 }
 
 __global__ void __launch_bounds__(256) keep_disparity_bits(int32_t *a, int32_t *b, size_t n) {
@@ -323,32 +351,33 @@ __global__ void __launch_bounds__(256) keep_disparity_bits(int32_t *a, int32_t *
   }
 }
 
-template <int NW, int WIN, bool CSA, bool SPLIT>
+template <int NW, int WIN, int PM, bool SPLIT>
 cudaError_t launch_t(const Cost2Args &a, int nwarps, cudaStream_t s) {
   constexpr int OUTC = 64 - 2 * (WIN / 2);
+  constexpr bool PK = 32 * NW * WIN * WIN < 8192;  // aggregated costs fit 13 bits: packed argmin
   const size_t smem = cost2_smem_bytes<NW>(nwarps * kDC, WIN, nwarps * 32);
-  cudaError_t e = cudaFuncSetAttribute(cost2_kernel<NW, WIN, CSA, SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem);
+  cudaError_t e = cudaFuncSetAttribute(cost2_kernel<NW, WIN, PM, SPLIT, PK>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  dim3 grid((a.w + OUTC - 1) / OUTC, (a.h + a.rows - 1) / a.rows, 2 * a.ndr);
-  cost2_kernel<NW, WIN, CSA, SPLIT><<<grid, nwarps * 32, smem, s>>>(a);
+  dim3 grid(((a.w + OUTC - 1) / OUTC) * a.ndr, (a.h + a.rows - 1) / a.rows, 2);
+  cost2_kernel<NW, WIN, PM, SPLIT, PK><<<grid, nwarps * 32, smem, s>>>(a);
   return cudaGetLastError();
 }
 
-template <int NW, bool CSA, bool SPLIT>
+template <int NW, int PM, bool SPLIT>
 cudaError_t launch_win(int win, const Cost2Args &a, int nwarps, cudaStream_t s) {
   switch (win) {
-    case 1: return launch_t<NW, 1, CSA, SPLIT>(a, nwarps, s);
-    case 3: return launch_t<NW, 3, CSA, SPLIT>(a, nwarps, s);
-    case 5: return launch_t<NW, 5, CSA, SPLIT>(a, nwarps, s);
-    case 7: return launch_t<NW, 7, CSA, SPLIT>(a, nwarps, s);
+    case 1: return launch_t<NW, 1, PM, SPLIT>(a, nwarps, s);
+    case 3: return launch_t<NW, 3, PM, SPLIT>(a, nwarps, s);
+    case 5: return launch_t<NW, 5, PM, SPLIT>(a, nwarps, s);
+    case 7: return launch_t<NW, 7, PM, SPLIT>(a, nwarps, s);
     default: return cudaErrorInvalidValue;
   }
 }
 
-template <int NW, bool CSA>
+template <int NW, int PM>
 cudaError_t launch_split(bool split, int win, const Cost2Args &a, int nwarps, cudaStream_t s) {
-  return split ? launch_win<NW, CSA, true>(win, a, nwarps, s) : launch_win<NW, CSA, false>(win, a, nwarps, s);
+  return split ? launch_win<NW, PM, true>(win, a, nwarps, s) : launch_win<NW, PM, false>(win, a, nwarps, s);
 }
 
 int pick_rows2(int w, int h, int win, int ctas_z) {
@@ -385,10 +414,13 @@ cudaError_t launch_cost2(const bsm_ctx *ctx, const uint32_t *BL, const uint32_t 
   }
   const int win = ctx->p.agg_window;
   if (ctx->nw == 8) {
-    e = ctx->cost_plain_popc ? launch_split<8, false>(split, win, a, nwarps, s)
-                             : launch_split<8, true>(split, win, a, nwarps, s);
+    switch (ctx->cost_plain_popc) {
+      case 1: e = launch_split<8, 1>(split, win, a, nwarps, s); break;
+      case 2: e = launch_split<8, 2>(split, win, a, nwarps, s); break;
+      default: e = launch_split<8, 0>(split, win, a, nwarps, s); break;
+    }
   } else if (ctx->nw == 4) {
-    e = launch_split<4, false>(split, win, a, nwarps, s);
+    e = launch_split<4, 1>(split, win, a, nwarps, s);
   } else {
     return cudaErrorInvalidValue;
   }

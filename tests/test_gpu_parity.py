@@ -123,7 +123,7 @@ def test_cost_volume_bit_exact(B, orc, win, n, dmax):
 
 @pytest.mark.parametrize("rows,plain,variant,dmax", [(8, 0, 1, 40), (8, 1, 1, 40), (16, 1, 2, 40), (128, 0, 2, 40),
                                                     (512, 1, 1, 40), (8, 0, 2, 200), (32, 1, 2, 129),
-                                                    (16, 0, 1, 200)])
+                                                    (16, 0, 1, 200), (32, 2, 2, 200), (64, 2, 2, 40)])
 def test_tuning_does_not_change_bits(B, orc, rows, plain, variant, dmax):
     w, h = 77, 41
     l, r, _ = synth.stereo_pair(w, h, dmax, seed=250)
