@@ -58,6 +58,9 @@ def parse():
     ap.add_argument("--cost-popc-plain", type=int, default=0, help="1: plain popcount in the cost kernel")
     ap.add_argument("--batch-rows", type=int, default=0, help="rows per task of the batched cost kernel (0: 64)")
     ap.add_argument("--no-autotune", action="store_true", help="skip the launch-shape autotuner")
+    ap.add_argument("--n-bits", type=int, default=N_BITS, help="descriptor length n (32 ... 4096)")
+    ap.add_argument("--sweep-n", action="store_true",
+                    help="speed for every descriptor length 32 ... 4096 on the chosen pair config (Fig. 3b)")
     ap.add_argument("--requests", type=int, default=2000, help="serving stream length (c5)")
     ap.add_argument("--rho", type=float, default=0.7, help="arrival rate as a fraction of measured capacity (c5)")
     ap.add_argument("--lanes", type=int, default=2, help="serving lanes (c5)")
@@ -435,18 +438,22 @@ def torch_dist_done():
     dist.destroy_process_group()
 
 
-def main():
-    args = parse()
-    cfg = CONFIGS[args.config]
-    world, rank, local = dist_init(args)
-    if args.impl == "reference":
-        run_reference(args, cfg, world, rank)
-        return
-    if args.config in ("c3", "c5"):
-        (run_batch if args.config == "c3" else run_serving)(args, cfg, world, rank, local)
-        if world > 1:
-            torch_dist_done()
-        return
+def cost_kernel(tuning, nw, dmax):
+    """(kernel name, source file, launches per call) of the cost/aggregation/WTA stage the library runs
+    for this tuning, descriptor length and disparity range (the dispatch of bsm_cost_aggregate_wta)."""
+    if nw > 8:
+        return "cost_long_kernel", "bsm_long.cu", 1
+    v = tuning["cost_variant"]
+    if v == 2 or (v == 0 and nw in (4, 8)):
+        need = (dmax + 7) // 8
+        split = (need + min(16, need) - 1) // min(16, need) > 1
+        return "cost2_kernel", "bsm_cost2.cu", 2 if split else 1  # + keep_disparity_bits after a split
+    return "cost_wta_kernel", "bsm_cost.cu", 1
+
+
+def run_pair(args, cfg, world, rank, local, n_bits=N_BITS, window_S=WINDOW_S, sigma=None, agg=AGG, e2e=True,
+             cpu_baseline=True):
+    """One pair per step through the per-pair C-ABI calls; returns the JSON line (dict)."""
     import torch
 
     from paper_1402_2020_gb300 import bsm, synth
@@ -455,17 +462,18 @@ def main():
     dev = torch.device("cuda", local)
     w, h, dmax = cfg["w"], cfg["h"], cfg["dmax"]
     left, right, _ = synth.stereo_pair(w, h, dmax, cfg["seed"] + rank * 1000, cfg["radiometric"])
-    pairs = synth.pair_table(N_BITS, WINDOW_S, seed=PAIR_SEED)
-    params = bsm.make_params(pairs, window_S=WINDOW_S, agg_window=AGG, dmax=dmax, vote_radius=VOTE_R)
+    pairs = synth.pair_table(n_bits, window_S, sigma=sigma, seed=PAIR_SEED)
+    params = bsm.make_params(pairs, window_S=window_S + (window_S % 2 == 0), agg_window=agg, dmax=dmax,
+                             vote_radius=VOTE_R)
     ctx = bsm.bsm_create(params)
+    nw = n_bits // 32
     bsm.bsm_set_tuning(ctx, args.cost_rows, args.cost_popc_plain, args.batch_rows)
     if not args.no_autotune and args.cost_rows == 0:
         from paper_1402_2020_gb300 import autotune
 
-        autotune.tune_cost(ctx, N_BITS, AGG, w, h, dmax)
+        autotune.tune_cost(ctx, n_bits, agg, w, h, dmax)
     stream = torch.cuda.Stream(device=dev)
     s = stream.cuda_stream
-    nw = N_BITS // 32
     dl = torch.from_numpy(left).to(dev)
     dr = torch.from_numpy(right).to(dev)
     pitch = 3 * w
@@ -514,58 +522,93 @@ def main():
     units = w * h * dmax
     value = world * units / (t_step * 1e-3) / 1e9
 
-    # end to end through the host-buffer C-ABI call (H2D of both views and D2H of the map inside)
-    hl = torch.from_numpy(left).pin_memory()
-    hr = torch.from_numpy(right).pin_memory()
-    ho = torch.empty((h, w), dtype=torch.int32).pin_memory()
-    for _ in range(2):
-        bsm.bsm_match_host(ctx, hl.data_ptr(), hr.data_ptr(), w, h, pitch, dmax, ho.data_ptr(), s)
-    e2e_t = []
-    for _ in range(max(3, args.steps // 2)):
-        flush.zero_()
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        bsm.bsm_match_host(ctx, hl.data_ptr(), hr.data_ptr(), w, h, pitch, dmax, ho.data_ptr(), s)
-        e2e_t.append(time.perf_counter() - t0)
-    e2e_s = float(np.mean(e2e_t))
-    e2e_s = max_over_ranks([e2e_s], world, dev)[0]
-    e2e_value = world * units / e2e_s / 1e9
-
+    tuning = bsm.bsm_get_tuning(ctx)
+    kname, kfile, klaunch = cost_kernel(tuning, nw, dmax)
     # roofline of the dominant kernel: fused cost/aggregation/WTA, both reference views per launch
     t_k2 = float(per[:, 2].mean()) * 1e-3
-    word_ops = 2 * units * (N_BITS // 32)
+    word_ops = 2 * units * nw
     achieved = word_ops / t_k2 / 1e9
     peak = SMS * POPC_PER_CLK_SM * MAX_SM_MHZ * 1e6 / 1e9
-    traffic = profile_traffic("bsm_cost.cu", args.config)
+    workload_key = args.config if n_bits == N_BITS else f"{args.config}_n{n_bits}"
+    traffic = profile_traffic(kfile, workload_key)
     line = {
         "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-        "config": {"workload": cfg["name"], "n_bits": N_BITS, "window_S": WINDOW_S, "agg_window": AGG,
-                   "mask_rank": N_BITS // 4, "vote_radius": VOTE_R, "parallelism": f"replicas x{world}",
+        "config": {"workload": cfg["name"], "n_bits": n_bits, "window_S": window_S, "pair_sigma": sigma,
+                   "agg_window": agg, "mask_rank": n_bits // 4, "vote_radius": VOTE_R,
+                   "parallelism": f"replicas x{world}",
                    "l2": f"flushed between timed steps ({L2_FLUSH_BYTES >> 20} MiB write)"},
         "stage_ms": {"describe_left": float(per[:, 0].mean()), "describe_right": float(per[:, 1].mean()),
                      "cost_aggregate_wta": float(per[:, 2].mean()), "refine": float(per[:, 3].mean())},
         "pairs_per_s": world / (t_step * 1e-3),
-        "e2e": {"value": e2e_value, "unit": METRIC, "h2d_bytes_per_step": 2 * h * pitch,
-                "d2h_bytes_per_step": 4 * w * h, "ms_per_step": e2e_s * 1e3},
-        "gpu_launches": 6 * args.steps,  # colour pre-pass + describe per view, cost, refine
-        "roofline": {"bound": "alu", "kernel": "cost_wta_kernel", "achieved": achieved, "peak": peak,
+        # colour pre-pass + describe per view, the cost stage's kernels, refine
+        "gpu_launches": (4 + klaunch + 1) * args.steps,
+        "roofline": {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": peak,
                      "unit": "Gpopc/s", "frac": achieved / peak, "traffic": traffic,
                      "work_per_launch": word_ops,
                      "peak_basis": f"{SMS} SMs x {POPC_PER_CLK_SM} POPC/clk x {MAX_SM_MHZ} MHz"},
         "clocks": clocks,
-        "tuning": bsm.bsm_get_tuning(ctx),
+        "tuning": tuning,
     }
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if e2e:
+        # end to end through the host-buffer C-ABI call (H2D of both views and D2H of the map inside)
+        hl = torch.from_numpy(left).pin_memory()
+        hr = torch.from_numpy(right).pin_memory()
+        ho = torch.empty((h, w), dtype=torch.int32).pin_memory()
+        for _ in range(2):
+            bsm.bsm_match_host(ctx, hl.data_ptr(), hr.data_ptr(), w, h, pitch, dmax, ho.data_ptr(), s)
+        e2e_t = []
+        for _ in range(max(3, args.steps // 2)):
+            flush.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            bsm.bsm_match_host(ctx, hl.data_ptr(), hr.data_ptr(), w, h, pitch, dmax, ho.data_ptr(), s)
+            e2e_t.append(time.perf_counter() - t0)
+        e2e_s = float(np.mean(e2e_t))
+        e2e_s = max_over_ranks([e2e_s], world, dev)[0]
+        line["e2e"] = {"value": world * units / e2e_s / 1e9, "unit": METRIC, "h2d_bytes_per_step": 2 * h * pitch,
+                       "d2h_bytes_per_step": 4 * w * h, "ms_per_step": e2e_s * 1e3}
+    if cpu_baseline and rank == 0 and world == 1 and not args.no_cpu_baseline:
         dt, u = oracle_sample(cfg, 32)
         line["cpu_baseline"] = {"value": u / dt / 1e9, "unit": METRIC, "cores": 1, "kind": "oracle",
                                 "sample": f"{w}x32 row band of the workload, whole oracle pipeline, single thread"}
-    if rank == 0:
-        print(json.dumps(line), flush=True)
     bsm.bsm_destroy(ctx)
+    return line
+
+
+SWEEP_N = (32, 64, 128, 256, 512, 1024, 2048, 4096)
+
+
+def run_sweep_n(args, cfg, world, rank, local):
+    """Speed against descriptor length (the speed half of Fig. 3b): the paper's pair distribution
+    (S = 26, sigma = 4), a 3x3 box (n * 3^2 fits the 16-bit cost for every n), one line per n."""
+    agg = 3
+    for n in SWEEP_N:
+        line = run_pair(args, cfg, world, rank, local, n_bits=n, window_S=26, sigma=4.0, agg=agg, e2e=False,
+                        cpu_baseline=False)
+        line["sweep"] = "descriptor length n (Fig. 3b speed)"
+        if rank == 0:
+            print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    cfg = CONFIGS[args.config]
+    world, rank, local = dist_init(args)
+    if args.impl == "reference":
+        run_reference(args, cfg, world, rank)
+        return
+    if args.config in ("c3", "c5"):
+        (run_batch if args.config == "c3" else run_serving)(args, cfg, world, rank, local)
+    elif args.sweep_n:
+        run_sweep_n(args, cfg, world, rank, local)
+    else:
+        line = run_pair(args, cfg, world, rank, local, n_bits=args.n_bits)
+        if rank == 0:
+            print(json.dumps(line), flush=True)
     if world > 1:
-        torch.distributed.destroy_process_group()
+        torch_dist_done()
 
 
 if __name__ == "__main__":

@@ -50,8 +50,9 @@ typedef enum {
 
 /* Parameters of the method, fixed at bsm_create. */
 typedef struct {
-  int32_t n_bits;        /* descriptor length n (Eq. 2): a multiple of 32; this version builds
-                            32, 64, 128 and 256 (the paper uses 4096, Sec. 4.1) */
+  int32_t n_bits;        /* descriptor length n (Eq. 2): a multiple of 32; this version builds the
+                            powers of two 32 ... 4096 (the paper uses 4096, Sec. 4.1). Batching and
+                            serving take n_bits <= 256. */
   int32_t window_S;      /* sampling window S (Sec. 3): every offset satisfies |off| <= S / 2;
                             3..63 */
   const int8_t *pairs;   /* HOST pointer to n_bits entries of 4 int8 (px, py, qx, qy): the offsets of
@@ -136,7 +137,8 @@ typedef struct {
  * read before the call returns. Work is asynchronous on `stream`. The context's batch scratch (the
  * colour planes of all 2 * count views) grows here if too small (bsm_reserve_batch sizes it up
  * front); the call waits until the previous batch's ticket table has been copied to the device.
- * Errors: BSM_ERR_INVALID_ARG for a bad descriptor or count outside 1..BSM_MAX_BATCH.
+ * Errors: BSM_ERR_INVALID_ARG for a bad descriptor or count outside 1..BSM_MAX_BATCH;
+ * BSM_ERR_UNSUPPORTED when the context's n_bits exceeds 256 (long descriptors run per pair).
  */
 bsm_status bsm_batch_run(bsm_ctx *ctx, const bsm_pair_desc *pairs, int32_t count, void *stream);
 
@@ -182,7 +184,8 @@ typedef struct {
   int64_t submitted, completed, failed, batches, max_batch_seen, queued, bytes_in_use, budget;
 } bsm_server_stats;
 
-/* Start an engine (creates `lanes` contexts: synchronous, allocates). */
+/* Start an engine (creates `lanes` contexts: synchronous, allocates). BSM_ERR_UNSUPPORTED for
+ * n_bits > 256, which the batched kernels do not serve. */
 bsm_status bsm_server_create(const bsm_params *params, const bsm_server_config *cfg, bsm_server **out);
 
 /* Queue a request (any thread, non-blocking). A malformed request, or one larger than the whole
@@ -289,7 +292,8 @@ bsm_status bsm_vote_tables(int32_t lambda_c, int32_t lambda_e, int32_t nc, int32
  * A zero field selects the library's heuristic.
  */
 typedef struct {
-  int32_t cost_rows;       /* rows per CTA band of the cost/aggregation/WTA kernel: 0 or 8..512 */
+  int32_t cost_rows;       /* rows per CTA band of the cost/aggregation/WTA kernel: 0 or 8..512
+                              (n_bits > 256: the chunked long-descriptor kernel's band) */
   int32_t cost_popc_plain; /* popcount form of the cost kernel (n_bits = 256; results identical):
                               0 carry-save tree over 8 words, 1 plain POPC per word, 2 two 3-word
                               carry-save adders plus 2 plain words (two-column kernel only) */

@@ -80,7 +80,7 @@ bsm_status bsm_validate_params(const bsm_params *p) {
   for (int i = 0; i < 4 * p->n_bits; ++i)
     if (std::abs((int)p->pairs[i]) > half) return BSM_ERR_INVALID_ARG;
   // Valid per the method, not built in this version.
-  if (p->n_bits != 32 && p->n_bits != 64 && p->n_bits != 128 && p->n_bits != 256) return BSM_ERR_UNSUPPORTED;
+  if (p->n_bits & (p->n_bits - 1)) return BSM_ERR_UNSUPPORTED;  // 32, 64, ..., 4096
   if (p->agg_window > 7) return BSM_ERR_UNSUPPORTED;
   if (p->dmax > bsm::kMaxDmax) return BSM_ERR_UNSUPPORTED;
   return BSM_OK;
@@ -106,6 +106,7 @@ void bsm_destroy(bsm_ctx *ctx) {
   cudaFree(ctx->vote_ec);
   cudaFree(ctx->vote_es);
   cudaFree(ctx->status);
+  cudaFree(ctx->wide_offs);
   cudaFree(ctx->ws);
   cudaFree(ctx->plane);
   if (ctx->batch_graph) cudaGraphExecDestroy(ctx->batch_graph);
@@ -154,6 +155,17 @@ bsm_status bsm_create(const bsm_params *p, bsm_ctx **out) {
       if (e == cudaSuccess) e = cudaMemcpy(ctx->vote_ec, Ec, sizeof(Ec), cudaMemcpyHostToDevice);
       if (e == cudaSuccess) e = cudaMemcpy(ctx->vote_es, Es, sizeof(uint32_t) * ne, cudaMemcpyHostToDevice);
       delete[] Es;
+    }
+  }
+  if (e == cudaSuccess && ctx->nw > 8) {
+    int32_t *offs = new (std::nothrow) int32_t[p->n_bits];
+    if (offs == nullptr) {
+      e = cudaErrorMemoryAllocation;
+    } else {
+      bsm::wide_offsets(ctx, offs);
+      e = cudaMalloc(&ctx->wide_offs, sizeof(int32_t) * p->n_bits);
+      if (e == cudaSuccess) e = cudaMemcpy(ctx->wide_offs, offs, sizeof(int32_t) * p->n_bits, cudaMemcpyHostToDevice);
+      delete[] offs;
     }
   }
   if (e == cudaSuccess) e = cudaMemset(ctx->status, 0, sizeof(uint32_t));

@@ -309,7 +309,7 @@ cudaError_t launch_batch_nw(BatchHeader *hdr, const BatchPair *pairs, int k, int
 PairTable make_pair_table(const bsm_ctx *ctx) {
   const int tp = 32 + 2 * ctx->halo;
   PairTable pt{};
-  for (int i = 0; i < ctx->p.n_bits; ++i) {
+  for (int i = 0; i < ctx->p.n_bits && i < kMaxShortBits; ++i) {
     const int8_t *q = ctx->pairs + 4 * i;
     pt.off[i][0] = q[1] * tp + q[0];
     pt.off[i][1] = q[3] * tp + q[2];
@@ -356,6 +356,7 @@ cudaError_t launch_color_plane(const bsm_ctx *ctx, const uint8_t *rgb, int w, in
 
 cudaError_t launch_describe_plane(const bsm_ctx *ctx, const uint32_t *plane, int w, int h, uint32_t *B,
                                   uint32_t *Phi, cudaStream_t s) {
+  if (ctx->nw > 8) return launch_describe_wide(ctx, plane, w, h, B, Phi, s);
   DescribeArgs a{plane, B, Phi, w, h, ctx->mask_rank, ctx->halo};
   const PairTable pt = make_pair_table(ctx);
   switch (ctx->nw) {

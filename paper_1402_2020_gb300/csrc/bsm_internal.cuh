@@ -10,8 +10,8 @@
 
 namespace bsm {
 
-constexpr int kMaxBits = 256;      // descriptor length supported by the kernels of this version
-constexpr int kMaxWords = kMaxBits / 32;
+constexpr int kMaxBits = 4096;     // longest descriptor (the paper's n, Sec. 4.1)
+constexpr int kMaxShortBits = 256; // longest descriptor of the short-descriptor kernels
 constexpr int kMaxDmax = 256;
 constexpr int kMaxHalo = 31;       // largest |offset| of a sampling pair
 constexpr int kMaxVoteRadius = 31;
@@ -24,7 +24,7 @@ constexpr uint32_t kLabMask = 0x00FFFFFFu;
 // Pair offsets in the shared-memory tile of the describe kernel: element i is
 // (dy_p * pitch + dx_p, dy_q * pitch + dx_q) for the tile pitch chosen at launch.
 struct PairTable {
-  int32_t off[kMaxBits][2];
+  int32_t off[kMaxShortBits][2];
 };
 
 // ---------------------------------------------------------------- batched execution
@@ -67,6 +67,7 @@ struct bsm_ctx {
   uint32_t *vote_ec = nullptr;      // device, kMaxSad + 1 entries
   uint32_t *vote_es = nullptr;      // device, 2 R^2 + 1 entries
   uint32_t *status = nullptr;       // device status word (bsm_status latched by kernels)
+  int32_t *wide_offs = nullptr;     // device pair offsets of the long-descriptor describe kernel
   // Launch shapes (bsm_set_tuning); 0 selects the library's heuristic.
   int cost_rows = 0;        // rows per CTA band of the cost kernel
   int cost_plain_popc = 0;  // 1: plain popcount in the cost kernel instead of the carry-save tree
@@ -111,6 +112,12 @@ cudaError_t launch_cost_wta(const bsm_ctx *ctx, const uint32_t *BL, const uint32
 cudaError_t prepare_describe_batch(const bsm_ctx *ctx, int *grid);
 cudaError_t prepare_cost_batch(const bsm_ctx *ctx, int *grid);
 cudaError_t prepare_refine_batch(const bsm_ctx *ctx, int *grid);
+void wide_offsets(const bsm_ctx *ctx, int32_t *out);
+cudaError_t launch_describe_wide(const bsm_ctx *ctx, const uint32_t *plane, int w, int h, uint32_t *B, uint32_t *Phi,
+                                 cudaStream_t s);
+cudaError_t launch_cost_long(const bsm_ctx *ctx, const uint32_t *BL, const uint32_t *PhiL, const uint32_t *BR,
+                             const uint32_t *PhiR, int w, int h, int dmax, int32_t *dL, int32_t *dR, uint16_t *cost,
+                             cudaStream_t s);
 bool cost2_supported(const bsm_ctx *ctx);
 cudaError_t launch_cost2(const bsm_ctx *ctx, const uint32_t *BL, const uint32_t *PhiL, const uint32_t *BR,
                          const uint32_t *PhiR, int w, int h, int dmax, int32_t *dL, int32_t *dR, uint16_t *cost,

@@ -68,10 +68,21 @@ def test_validate_params(lib):
     ]
     for kw in bad:
         assert bsm.bsm_validate_params(_params(**kw)) == bsm.BSM_ERR_INVALID_ARG, kw
-    unsupported = [dict(pairs=synth.pair_table(512, 31, seed=4)), dict(agg_window=9, pairs=synth.pair_table(64, 31)),
+    unsupported = [dict(pairs=synth.pair_table(768, 31, seed=4)), dict(agg_window=9, pairs=synth.pair_table(64, 31)),
                    dict(dmax=300), dict(pairs=synth.pair_table(96, 31, seed=5))]
     for kw in unsupported:
         assert bsm.bsm_validate_params(_params(**kw)) == bsm.BSM_ERR_UNSUPPORTED, kw
+    # long descriptors: every power of two up to the paper's 4096, with n * W^2 <= 65535
+    for n, win in ((512, 5), (1024, 7), (2048, 5), (4096, 3), (4096, 1)):
+        assert bsm.bsm_validate_params(_params(pairs=synth.pair_table(n, 31, seed=n), agg_window=win)) == bsm.BSM_OK
+    assert bsm.bsm_validate_params(_params(pairs=synth.pair_table(4096, 31, seed=6), agg_window=5)) == \
+        bsm.BSM_ERR_INVALID_ARG
+    assert bsm.bsm_validate_params(_params(pairs=synth.pair_table(8192, 31, seed=6), agg_window=1)) == \
+        bsm.BSM_ERR_INVALID_ARG
+    # the server batches descriptors of up to 256 bits; it refuses longer ones before touching a device
+    with pytest.raises(bsm.BsmError) as e:
+        bsm.bsm_server_create(_params(pairs=synth.pair_table(512, 31, seed=7)))
+    assert e.value.status == bsm.BSM_ERR_UNSUPPORTED
     # a NULL pair table
     p = _params()
     p.pairs = ctypes.POINTER(ctypes.c_int8)()
