@@ -59,6 +59,8 @@ def parse():
     ap.add_argument("--batch-rows", type=int, default=0, help="rows per task of the batched cost kernel (0: 64)")
     ap.add_argument("--no-autotune", action="store_true", help="skip the launch-shape autotuner")
     ap.add_argument("--n-bits", type=int, default=N_BITS, help="descriptor length n (32 ... 4096)")
+    ap.add_argument("--quality", action="store_true",
+                    help="bad-pixel rates against the generator's ground truth: mask ablation, radiometric 3x3")
     ap.add_argument("--sweep-n", action="store_true",
                     help="speed for every descriptor length 32 ... 4096 on the chosen pair config (Fig. 3b)")
     ap.add_argument("--requests", type=int, default=2000, help="serving stream length (c5)")
@@ -461,7 +463,7 @@ def run_pair(args, cfg, world, rank, local, n_bits=N_BITS, window_S=WINDOW_S, si
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     w, h, dmax = cfg["w"], cfg["h"], cfg["dmax"]
-    left, right, _ = synth.stereo_pair(w, h, dmax, cfg["seed"] + rank * 1000, cfg["radiometric"])
+    left, right, gt = synth.stereo_pair(w, h, dmax, cfg["seed"] + rank * 1000, cfg["radiometric"])
     pairs = synth.pair_table(n_bits, window_S, sigma=sigma, seed=PAIR_SEED)
     params = bsm.make_params(pairs, window_S=window_S + (window_S % 2 == 0), agg_window=agg, dmax=dmax,
                              vote_radius=VOTE_R)
@@ -524,6 +526,7 @@ def run_pair(args, cfg, world, rank, local, n_bits=N_BITS, window_S=WINDOW_S, si
 
     tuning = bsm.bsm_get_tuning(ctx)
     kname, kfile, klaunch = cost_kernel(tuning, nw, dmax)
+    bad = bad_pixel_rate(out.cpu().numpy(), gt)
     # roofline of the dominant kernel: fused cost/aggregation/WTA, both reference views per launch
     t_k2 = float(per[:, 2].mean()) * 1e-3
     word_ops = 2 * units * nw
@@ -542,6 +545,7 @@ def run_pair(args, cfg, world, rank, local, n_bits=N_BITS, window_S=WINDOW_S, si
         "stage_ms": {"describe_left": float(per[:, 0].mean()), "describe_right": float(per[:, 1].mean()),
                      "cost_aggregate_wta": float(per[:, 2].mean()), "refine": float(per[:, 3].mean())},
         "pairs_per_s": world / (t_step * 1e-3),
+        "bad_pixel_rate": bad,  # |d - d_gt| > 1 against the generator's ground truth, rank 0's pair
         # colour pre-pass + describe per view, the cost stage's kernels, refine
         "gpu_launches": (4 + klaunch + 1) * args.steps,
         "roofline": {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": peak,
@@ -580,6 +584,68 @@ def run_pair(args, cfg, world, rank, local, n_bits=N_BITS, window_S=WINDOW_S, si
 SWEEP_N = (32, 64, 128, 256, 512, 1024, 2048, 4096)
 
 
+def bad_pixel_rate(disp, gt, tol=1):
+    """Share of pixels whose disparity is off the generator's ground truth by more than tol, over the
+    pixels whose true match lies inside the right view."""
+    disp = np.asarray(disp)
+    x = np.arange(gt.shape[1])[None, :]
+    m = x - gt >= 0
+    return float((np.abs(disp.astype(np.int64) - gt)[m] > tol).mean())
+
+
+MASK_NAMES = {0: "BSM mask (Eq. 8)", 1: "no mask (Eq. 4)", 2: "both views' masks"}
+EXPOSURE = ((0.5, 0.7), (0.5, 1.0), (0.5, 1.4), (1.0, 0.7), (1.0, 1.0), (1.0, 1.4), (2.0, 0.7), (2.0, 1.0),
+            (2.0, 1.4))  # (gain, gamma) of the right view: a 3 x 3 exposure / illumination design
+
+
+def run_quality(args, cfg, world, rank, local):
+    """Disparity error against the generator's ground truth (synthetic stand-ins for the paper's
+    Middlebury evaluation): the mask ablation (Eq. 8's mask, no mask as in Eq. 4, both views' masks) for
+    window 1 and 5, and the same three under a 3 x 3 radiometric design applied to the right view."""
+    import torch
+
+    from paper_1402_2020_gb300 import bsm, synth
+
+    if rank != 0:
+        return
+    torch.cuda.set_device(local)
+    w, h, dmax = cfg["w"], cfg["h"], cfg["dmax"]
+    seeds = range(cfg["seed"], cfg["seed"] + 3)
+    views = {s: synth.stereo_pair(w, h, dmax, s) for s in seeds}
+    # this library's default descriptor, and the paper's (n = 4096, S = 26, sigma = 4) with a 3 x 3 box
+    settings = {"n=256, S=31": (256, 31, None, AGG), "n=4096, S=26, sigma=4": (4096, 26, 4.0, 3)}
+
+    def evaluate(setting, mode, agg, transform=None):
+        n, S, sigma, _ = settings[setting]
+        pairs = synth.pair_table(n, S, sigma=sigma, seed=PAIR_SEED)
+        m = bsm.Matcher(pairs, window_S=S + (S % 2 == 0), agg_window=agg, dmax=dmax, vote_radius=VOTE_R,
+                        mask_mode=mode)
+        rates = []
+        for s in seeds:
+            left, right, gt = views[s]
+            if transform is not None:
+                right = transform(right)
+            out = m.match(torch.from_numpy(left).cuda(), torch.from_numpy(np.ascontiguousarray(right)).cuda(), dmax)
+            rates.append(bad_pixel_rate(out.cpu().numpy(), gt))
+        m.close()
+        return float(np.mean(rates))
+
+    table, radio = {}, {}
+    for setting, (_, _, _, agg_box) in settings.items():
+        for mode in (0, 1, 2):
+            for agg in (1, agg_box):
+                table[f"{setting}: {MASK_NAMES[mode]}, window {agg}"] = evaluate(setting, mode, agg)
+            radio[f"{setting}: {MASK_NAMES[mode]}, window {agg_box}"] = {
+                f"gain {g} gamma {gm}": evaluate(setting, mode, agg_box,
+                                                 lambda r, g=g, gm=gm: synth.radiometric_fixed(r, g, gm))
+                for g, gm in EXPOSURE}
+    line = {"metric": "bad-pixel rate (|d - d_gt| > 1)", "unit": "fraction", "higher_is_better": False,
+            "data": "synthetic", "config": {"workload": cfg["name"], "settings": list(settings),
+                                            "seeds": list(seeds), "vote_radius": VOTE_R},
+            "mask_ablation": table, "radiometric_3x3": radio}
+    print(json.dumps(line), flush=True)
+
+
 def run_sweep_n(args, cfg, world, rank, local):
     """Speed against descriptor length (the speed half of Fig. 3b): the paper's pair distribution
     (S = 26, sigma = 4), a 3x3 box (n * 3^2 fits the 16-bit cost for every n), one line per n."""
@@ -587,7 +653,7 @@ def run_sweep_n(args, cfg, world, rank, local):
     for n in SWEEP_N:
         line = run_pair(args, cfg, world, rank, local, n_bits=n, window_S=26, sigma=4.0, agg=agg, e2e=False,
                         cpu_baseline=False)
-        line["sweep"] = "descriptor length n (Fig. 3b speed)"
+        line["sweep"] = "descriptor length n (Fig. 3b)"
         if rank == 0:
             print(json.dumps(line), flush=True)
 
@@ -603,8 +669,11 @@ def main():
         (run_batch if args.config == "c3" else run_serving)(args, cfg, world, rank, local)
     elif args.sweep_n:
         run_sweep_n(args, cfg, world, rank, local)
+    elif args.quality:
+        run_quality(args, cfg, world, rank, local)
     else:
-        line = run_pair(args, cfg, world, rank, local, n_bits=args.n_bits)
+        agg = AGG if args.n_bits * AGG * AGG <= 65535 else 3  # the 16-bit aggregated cost bounds n * W^2
+        line = run_pair(args, cfg, world, rank, local, n_bits=args.n_bits, agg=agg)
         if rank == 0:
             print(json.dumps(line), flush=True)
     if world > 1:

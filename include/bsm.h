@@ -69,7 +69,17 @@ typedef struct {
   int32_t vote_radius;   /* R: the refinement votes over a (2R+1)^2 window (0..31; default 15) */
   int32_t lambda_c;      /* lambda_c of Eq. 10 (paper: 9), > 0 */
   int32_t lambda_e;      /* lambda_e of Eq. 10 (paper: 16), > 0 */
+  int32_t mask_mode;     /* which mask weights Eq. 8's Hamming distance (BSM_MASK_*):
+                            BSM_MASK_REFERENCE (0): the reference pixel's Phi, the paper's method;
+                            BSM_MASK_NONE (1): no mask, the plain descriptor distance of Eq. 4
+                            (Phi is written as all ones; mask_rank must be 0 or n_bits);
+                            BSM_MASK_BOTH (2): Phi of the reference pixel AND Phi of its match, an
+                            ablation of the paper's choice (n_bits >= 256; per-pair calls only) */
 } bsm_params;
+
+#define BSM_MASK_REFERENCE 0
+#define BSM_MASK_NONE 1
+#define BSM_MASK_BOTH 2
 
 /*
  * Create a context on the current CUDA device: validates the parameters, uploads the sampling
@@ -138,7 +148,8 @@ typedef struct {
  * colour planes of all 2 * count views) grows here if too small (bsm_reserve_batch sizes it up
  * front); the call waits until the previous batch's ticket table has been copied to the device.
  * Errors: BSM_ERR_INVALID_ARG for a bad descriptor or count outside 1..BSM_MAX_BATCH;
- * BSM_ERR_UNSUPPORTED when the context's n_bits exceeds 256 (long descriptors run per pair).
+ * BSM_ERR_UNSUPPORTED when the context's n_bits exceeds 256 (long descriptors run per pair) or its
+ * mask_mode is BSM_MASK_BOTH.
  */
 bsm_status bsm_batch_run(bsm_ctx *ctx, const bsm_pair_desc *pairs, int32_t count, void *stream);
 
@@ -185,7 +196,7 @@ typedef struct {
 } bsm_server_stats;
 
 /* Start an engine (creates `lanes` contexts: synchronous, allocates). BSM_ERR_UNSUPPORTED for
- * n_bits > 256, which the batched kernels do not serve. */
+ * n_bits > 256 or mask_mode BSM_MASK_BOTH, which the batched kernels do not serve. */
 bsm_status bsm_server_create(const bsm_params *params, const bsm_server_config *cfg, bsm_server **out);
 
 /* Queue a request (any thread, non-blocking). A malformed request, or one larger than the whole

@@ -87,28 +87,35 @@ inline int popcount32(uint32_t v) { return __builtin_popcount(v); }
 
 // Eq. 8 for one (x, y, d): popcount((B_ref(x) XOR B_oth(x_d)) AND Phi_ref(x)); reading R5.
 // dir 0: left view is the reference and x_d = x - d; dir 1: right view is the reference, x_d = x + d.
+// Phioth, when given, is the other view's mask plane: the ablation that also weights by the matched
+// pixel's mask, popcount((B_ref XOR B_oth) AND Phi_ref(x) AND Phi_oth(x_d)) (not the paper's Eq. 8).
 uint32_t cost_at(const uint32_t *Bref, const uint32_t *Phiref, const uint32_t *Both, int w, int nw,
-                 int x, int y, int d, int dir) {
+                 int x, int y, int d, int dir, const uint32_t *Phioth = nullptr) {
   const int xd = dir == 0 ? x - d : x + d;
   if (xd < 0 || xd >= w) return (uint32_t)(32 * nw);
   const uint32_t *b = Bref + ((size_t)y * w + x) * nw;
   const uint32_t *m = Phiref + ((size_t)y * w + x) * nw;
   const uint32_t *o = Both + ((size_t)y * w + xd) * nw;
   uint32_t c = 0;
-  for (int j = 0; j < nw; ++j) c += (uint32_t)popcount32((b[j] ^ o[j]) & m[j]);
+  if (Phioth == nullptr) {
+    for (int j = 0; j < nw; ++j) c += (uint32_t)popcount32((b[j] ^ o[j]) & m[j]);
+  } else {
+    const uint32_t *mo = Phioth + ((size_t)y * w + xd) * nw;
+    for (int j = 0; j < nw; ++j) c += (uint32_t)popcount32((b[j] ^ o[j]) & m[j] & mo[j]);
+  }
   return c;
 }
 
 // Window aggregation of Eq. 8's cost at (x, y, d); reading R6.
 uint32_t aggregated_at(const uint32_t *Bref, const uint32_t *Phiref, const uint32_t *Both, int w, int h,
-                       int nw, int win, int x, int y, int d, int dir) {
+                       int nw, int win, int x, int y, int d, int dir, const uint32_t *Phioth = nullptr) {
   const int r = win / 2;
   uint32_t s = 0;
   for (int dy = -r; dy <= r; ++dy)
     for (int dx = -r; dx <= r; ++dx) {
       const int xx = x + dx, yy = y + dy;
       if (xx < 0 || xx >= w || yy < 0 || yy >= h) continue;
-      s += cost_at(Bref, Phiref, Both, w, nw, xx, yy, d, dir);
+      s += cost_at(Bref, Phiref, Both, w, nw, xx, yy, d, dir, Phioth);
     }
   return s;
 }
@@ -206,29 +213,30 @@ int oracle_describe(const uint8_t *rgb, int w, int h, int pitch, const int8_t *p
 
 // Eq. 8 (with reading R5) for one (x, y, d).
 uint32_t oracle_cost_at(const uint32_t *Bref, const uint32_t *Phiref, const uint32_t *Both, int w, int h, int n,
-                        int x, int y, int d, int dir) {
+                        int x, int y, int d, int dir, const uint32_t *Phioth) {
   (void)h;
-  return cost_at(Bref, Phiref, Both, w, n / 32, x, y, d, dir);
+  return cost_at(Bref, Phiref, Both, w, n / 32, x, y, d, dir, Phioth);
 }
 
 // Aggregated cost A(x, y, d) for every pixel of the region [x0, x1) x [y0, y1) and d in [0, dmax):
 // A is written as [y1-y0][x1-x0][dmax] (d fastest). With win = 1 this is Eq. 8's cost itself.
 int oracle_aggregate(const uint32_t *Bref, const uint32_t *Phiref, const uint32_t *Both, int w, int h, int n,
-                     int dmax, int win, int dir, int x0, int x1, int y0, int y1, uint32_t *A) {
+                     int dmax, int win, int dir, int x0, int x1, int y0, int y1, uint32_t *A,
+                     const uint32_t *Phioth) {
   if (n % 32 != 0 || win < 1 || win % 2 == 0 || dmax < 1 || x0 < 0 || x1 > w || y0 < 0 || y1 > h) return -1;
   const int nw = n / 32;
   for (int y = y0; y < y1; ++y)
     for (int x = x0; x < x1; ++x)
       for (int d = 0; d < dmax; ++d)
         A[(((size_t)(y - y0)) * (x1 - x0) + (x - x0)) * dmax + d] =
-            aggregated_at(Bref, Phiref, Both, w, h, nw, win, x, y, d, dir);
+            aggregated_at(Bref, Phiref, Both, w, h, nw, win, x, y, d, dir, Phioth);
   return 0;
 }
 
 // Eq. 1 (winner-take-all, reading R7) on the aggregated cost, for the region [x0, x1) x [y0, y1).
 // disp is [y1-y0][x1-x0].
 int oracle_wta(const uint32_t *Bref, const uint32_t *Phiref, const uint32_t *Both, int w, int h, int n, int dmax,
-               int win, int dir, int x0, int x1, int y0, int y1, int32_t *disp) {
+               int win, int dir, int x0, int x1, int y0, int y1, int32_t *disp, const uint32_t *Phioth) {
   if (n % 32 != 0 || win < 1 || win % 2 == 0 || dmax < 1 || x0 < 0 || x1 > w || y0 < 0 || y1 > h) return -1;
   const int nw = n / 32;
   for (int y = y0; y < y1; ++y)
@@ -236,7 +244,7 @@ int oracle_wta(const uint32_t *Bref, const uint32_t *Phiref, const uint32_t *Bot
       uint32_t best = 0xffffffffu;
       int arg = 0;
       for (int d = 0; d < dmax; ++d) {
-        const uint32_t a = aggregated_at(Bref, Phiref, Both, w, h, nw, win, x, y, d, dir);
+        const uint32_t a = aggregated_at(Bref, Phiref, Both, w, h, nw, win, x, y, d, dir, Phioth);
         if (a < best) {
           best = a;
           arg = d;

@@ -36,11 +36,11 @@ def bind(L):
         L.oracle_lab_all.restype = None
         L.oracle_describe.argtypes = [P, I, I, I, P, I, I, I, I, P, P]
         L.oracle_describe.restype = I
-        L.oracle_cost_at.argtypes = [P, P, P, I, I, I, I, I, I, I]
+        L.oracle_cost_at.argtypes = [P, P, P, I, I, I, I, I, I, I, P]
         L.oracle_cost_at.restype = ctypes.c_uint32
-        L.oracle_aggregate.argtypes = [P, P, P, I, I, I, I, I, I, I, I, I, I, P]
+        L.oracle_aggregate.argtypes = [P, P, P, I, I, I, I, I, I, I, I, I, I, P, P]
         L.oracle_aggregate.restype = I
-        L.oracle_wta.argtypes = [P, P, P, I, I, I, I, I, I, I, I, I, I, P]
+        L.oracle_wta.argtypes = [P, P, P, I, I, I, I, I, I, I, I, I, I, P, P]
         L.oracle_wta.restype = I
         L.oracle_lr_check.argtypes = [P, P, I, I, I, P]
         L.oracle_lr_check.restype = I
@@ -108,40 +108,50 @@ def describe(img, pairs, k=None, y0=0, y1=None, out=None):
     return B, Phi
 
 
-def cost_at(Bref, Phiref, Both, x, y, d, direction):
-    """C(x, d) of Eq. 8 at one pixel (direction 0: left reference, 1: right reference)."""
+def _opt(p):
+    """The optional other-view mask plane as a C pointer (None: Eq. 8's reference mask only)."""
+    return None if p is None else _p(p)
+
+
+def cost_at(Bref, Phiref, Both, x, y, d, direction, Phioth=None):
+    """C(x, d) of Eq. 8 at one pixel (direction 0: left reference, 1: right reference).
+
+    With Phioth (the other view's mask plane) the matched pixel's mask is ANDed as well: the mask
+    ablation, not the paper's Eq. 8."""
     h, w, nw = Bref.shape
+    if Phioth is not None:
+        Phioth = np.ascontiguousarray(Phioth, dtype=np.uint32)
     return int(lib().oracle_cost_at(_p(Bref), _p(Phiref), _p(Both), w, h, 32 * nw, int(x), int(y), int(d),
-                                    int(direction)))
+                                    int(direction), _opt(Phioth)))
 
 
 def _planes(*ps):
-    return [np.ascontiguousarray(p, dtype=np.uint32) for p in ps]
+    return [None if p is None else np.ascontiguousarray(p, dtype=np.uint32) for p in ps]
 
 
-def aggregate(Bref, Phiref, Both, dmax, win, direction, x0=0, x1=None, y0=0, y1=None):
+def aggregate(Bref, Phiref, Both, dmax, win, direction, x0=0, x1=None, y0=0, y1=None, Phioth=None):
     """Window-aggregated cost A[y][x][d] (uint32) over the region; win = 1 gives Eq. 8 itself."""
-    Bref, Phiref, Both = _planes(Bref, Phiref, Both)
+    Bref, Phiref, Both, Phioth = _planes(Bref, Phiref, Both, Phioth)
     h, w, nw = Bref.shape
     x1 = w if x1 is None else x1
     y1 = h if y1 is None else y1
     A = np.zeros((y1 - y0, x1 - x0, dmax), np.uint32)
     rc = lib().oracle_aggregate(_p(Bref), _p(Phiref), _p(Both), w, h, 32 * nw, dmax, win, direction,
-                                x0, x1, y0, y1, _p(A))
+                                x0, x1, y0, y1, _p(A), _opt(Phioth))
     if rc != 0:
         raise ValueError("oracle_aggregate rejected its arguments")
     return A
 
 
-def wta(Bref, Phiref, Both, dmax, win, direction, x0=0, x1=None, y0=0, y1=None):
+def wta(Bref, Phiref, Both, dmax, win, direction, x0=0, x1=None, y0=0, y1=None, Phioth=None):
     """Eq. 1 on the aggregated cost: int32 disparities [y1-y0][x1-x0]."""
-    Bref, Phiref, Both = _planes(Bref, Phiref, Both)
+    Bref, Phiref, Both, Phioth = _planes(Bref, Phiref, Both, Phioth)
     h, w, nw = Bref.shape
     x1 = w if x1 is None else x1
     y1 = h if y1 is None else y1
     disp = np.zeros((y1 - y0, x1 - x0), np.int32)
     rc = lib().oracle_wta(_p(Bref), _p(Phiref), _p(Both), w, h, 32 * nw, dmax, win, direction,
-                          x0, x1, y0, y1, _p(disp))
+                          x0, x1, y0, y1, _p(disp), _opt(Phioth))
     if rc != 0:
         raise ValueError("oracle_wta rejected its arguments")
     return disp
@@ -195,12 +205,23 @@ def refine_region(imgL, dL, valid, dmax, x0, x1, y0, y1, R=15, lambda_c=9.0, lam
     return out
 
 
-def pipeline(imgL, imgR, pairs, dmax, win=5, k=None, tol=1, R=15, lambda_c=9.0, lambda_e=16.0):
-    """The whole method of Sec. 3 on one pair: returns dict of every intermediate and the final map."""
+MASK_REFERENCE, MASK_NONE, MASK_BOTH = 0, 1, 2
+
+
+def pipeline(imgL, imgR, pairs, dmax, win=5, k=None, tol=1, R=15, lambda_c=9.0, lambda_e=16.0,
+             mask_mode=MASK_REFERENCE):
+    """The whole method of Sec. 3 on one pair: returns dict of every intermediate and the final map.
+
+    mask_mode: MASK_REFERENCE is Eq. 8 as printed; MASK_NONE drops the mask (Eq. 4, every Phi bit set);
+    MASK_BOTH also ANDs the matched pixel's Phi (the mask ablation)."""
     BL, PhiL = describe(imgL, pairs, k)
     BR, PhiR = describe(imgR, pairs, k)
-    dL = wta(BL, PhiL, BR, dmax, win, 0)
-    dR = wta(BR, PhiR, BL, dmax, win, 1)
+    if mask_mode == MASK_NONE:
+        PhiL = np.full_like(PhiL, 0xFFFFFFFF)
+        PhiR = np.full_like(PhiR, 0xFFFFFFFF)
+    both = mask_mode == MASK_BOTH
+    dL = wta(BL, PhiL, BR, dmax, win, 0, Phioth=PhiR if both else None)
+    dR = wta(BR, PhiR, BL, dmax, win, 1, Phioth=PhiL if both else None)
     valid = lr_check(dL, dR, tol)
     out = refine(imgL, dL, valid, dmax, R, lambda_c, lambda_e)
     return {"BL": BL, "PhiL": PhiL, "BR": BR, "PhiR": PhiR, "dL": dL, "dR": dR, "valid": valid, "disp": out}

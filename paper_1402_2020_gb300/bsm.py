@@ -54,7 +54,11 @@ class bsm_params(ctypes.Structure):
         ("vote_radius", ctypes.c_int32),
         ("lambda_c", ctypes.c_int32),
         ("lambda_e", ctypes.c_int32),
+        ("mask_mode", ctypes.c_int32),
     ]
+
+
+BSM_MASK_REFERENCE, BSM_MASK_NONE, BSM_MASK_BOTH = 0, 1, 2
 
 
 class bsm_tuning(ctypes.Structure):
@@ -196,7 +200,8 @@ def _stream(stream) -> int:
 
 
 def make_params(pairs: np.ndarray, window_S: int = 31, agg_window: int = 5, mask_rank: int = 0, dmax: int = 256,
-                lr_tol: int = 1, vote_radius: int = 15, lambda_c: int = 9, lambda_e: int = 16):
+                lr_tol: int = 1, vote_radius: int = 15, lambda_c: int = 9, lambda_e: int = 16,
+                mask_mode: int = BSM_MASK_REFERENCE):
     """bsm_params for a pair table (int8 [n][4]); keeps the table alive on the returned object."""
     pairs = np.ascontiguousarray(pairs, dtype=np.int8)
     p = bsm_params()
@@ -210,6 +215,7 @@ def make_params(pairs: np.ndarray, window_S: int = 31, agg_window: int = 5, mask
     p.vote_radius = vote_radius
     p.lambda_c = lambda_c
     p.lambda_e = lambda_e
+    p.mask_mode = mask_mode
     p._keep = pairs
     return p
 

@@ -51,7 +51,7 @@ cudaError_t ensure_plane(bsm_ctx *ctx, size_t pixels) {
 
 extern "C" {
 
-int32_t bsm_abi_version(void) { return 1; }
+int32_t bsm_abi_version(void) { return 2; }
 
 const char *bsm_status_string(bsm_status s) {
   switch (s) {
@@ -79,8 +79,11 @@ bsm_status bsm_validate_params(const bsm_params *p) {
   const int half = p->window_S / 2;
   for (int i = 0; i < 4 * p->n_bits; ++i)
     if (std::abs((int)p->pairs[i]) > half) return BSM_ERR_INVALID_ARG;
+  if (p->mask_mode < BSM_MASK_REFERENCE || p->mask_mode > BSM_MASK_BOTH) return BSM_ERR_INVALID_ARG;
+  if (p->mask_mode == BSM_MASK_NONE && p->mask_rank != 0 && p->mask_rank != p->n_bits) return BSM_ERR_INVALID_ARG;
   // Valid per the method, not built in this version.
   if (p->n_bits & (p->n_bits - 1)) return BSM_ERR_UNSUPPORTED;  // 32, 64, ..., 4096
+  if (p->mask_mode == BSM_MASK_BOTH && p->n_bits < 256) return BSM_ERR_UNSUPPORTED;
   if (p->agg_window > 7) return BSM_ERR_UNSUPPORTED;
   if (p->dmax > bsm::kMaxDmax) return BSM_ERR_UNSUPPORTED;
   return BSM_OK;
@@ -129,6 +132,8 @@ bsm_status bsm_create(const bsm_params *p, bsm_ctx **out) {
   ctx->p.pairs = nullptr;  // the copy below is the context's own
   ctx->nw = p->n_bits / 32;
   ctx->mask_rank = p->mask_rank == 0 ? p->n_bits / 4 : p->mask_rank;
+  // No mask (Eq. 4): T of rank n is the largest weight, so every bit of Phi is set.
+  if (p->mask_mode == BSM_MASK_NONE) ctx->mask_rank = p->n_bits;
   std::memcpy(ctx->pairs, p->pairs, (size_t)4 * p->n_bits);
   int halo = 0;
   for (int i = 0; i < 4 * p->n_bits; ++i) halo = std::max(halo, std::abs((int)p->pairs[i]));
@@ -262,7 +267,8 @@ bsm_status bsm_set_tuning(bsm_ctx *ctx, const bsm_tuning *t) {
   for (int i = 0; i < 4; ++i)
     if (t->reserved[i] != 0) return BSM_ERR_INVALID_ARG;
   if (t->cost_variant < 0 || t->cost_variant > 2) return BSM_ERR_INVALID_ARG;
-  if (t->cost_variant == 2 && ctx->nw != 4 && ctx->nw != 8) return BSM_ERR_UNSUPPORTED;
+  if (t->cost_variant == 2 && ((ctx->nw != 4 && ctx->nw != 8) || ctx->p.mask_mode == BSM_MASK_BOTH))
+    return BSM_ERR_UNSUPPORTED;
   if (t->cost_rows != 0 && (t->cost_rows < 8 || t->cost_rows > 512)) return BSM_ERR_INVALID_ARG;
   if (t->batch_rows != 0 && (t->batch_rows < 8 || t->batch_rows > 512)) return BSM_ERR_INVALID_ARG;
   if (t->cost_popc_plain < 0 || t->cost_popc_plain > 2) return BSM_ERR_INVALID_ARG;

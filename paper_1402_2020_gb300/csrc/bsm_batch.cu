@@ -95,7 +95,8 @@ using namespace bsm;
 
 extern "C" bsm_status bsm_batch_run(bsm_ctx *ctx, const bsm_pair_desc *descs, int32_t count, void *stream) {
   if (ctx == nullptr || descs == nullptr || count < 1 || count > kMaxBatch) return BSM_ERR_INVALID_ARG;
-  if (ctx->nw > 8) return BSM_ERR_UNSUPPORTED;  // the batched kernels serve descriptors of up to 256 bits
+  // the batched kernels serve descriptors of up to 256 bits weighted by the reference pixel's mask
+  if (ctx->nw > 8 || ctx->p.mask_mode == BSM_MASK_BOTH) return BSM_ERR_UNSUPPORTED;
   const int outc = 32 - 2 * (ctx->p.agg_window / 2);
   const int band = ctx->batch_rows > 0 ? ctx->batch_rows : 64;
   size_t plane_words = 0;

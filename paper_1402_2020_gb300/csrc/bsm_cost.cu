@@ -534,7 +534,8 @@ int pick_rows(int w, int h, int win, int dmax) {
 cudaError_t launch_cost_wta(const bsm_ctx *ctx, const uint32_t *BL, const uint32_t *PhiL, const uint32_t *BR,
                             const uint32_t *PhiR, int w, int h, int dmax, int32_t *dL, int32_t *dR, uint16_t *cost,
                             cudaStream_t s) {
-  if (ctx->nw > 8) return launch_cost_long(ctx, BL, PhiL, BR, PhiR, w, h, dmax, dL, dR, cost, s);
+  if (ctx->nw > 8 || ctx->p.mask_mode == BSM_MASK_BOTH)
+    return launch_cost_long(ctx, BL, PhiL, BR, PhiR, w, h, dmax, dL, dR, cost, s);
   // The two-column kernel has no staging wait to withhold, so the failure-detection hook keeps the
   // one-column kernel.
   if (ctx->cost_variant != 1 && cost2_supported(ctx) && !ctx->withhold_arrivals)

@@ -11,6 +11,8 @@
 // (32 bytes per pixel) with 16-byte cp.async copies, double-buffered over the sequence of (row, chunk);
 // the masked popcounts accumulate over the chunks, and the out-of-image cost, the box sums and the
 // argmin follow a row's last chunk. n * window^2 <= 65535 keeps two costs per 32-bit register.
+// The same kernel serves the mask ablation that also ANDs the matched pixel's Phi (template MM), for
+// any n that is a multiple of 256 bits: the other view's Phi is then staged beside its B.
 #include <cuda_fp16.h>
 
 #include "bsm_internal.cuh"
@@ -142,7 +144,7 @@ cudaError_t launch_wide_nw(const WideArgs &a, cudaStream_t s) {
 constexpr int kDC = 8, kDP = 4, kChunkWords = 8;
 
 struct LongArgs {
-  const uint32_t *B[2], *Phi[2], *O[2];
+  const uint32_t *B[2], *Phi[2], *O[2], *OPhi[2];
   int32_t *disp[2];
   uint16_t *cost;
   int w, h, dmax, rows, nw;
@@ -184,12 +186,21 @@ __device__ __forceinline__ uint32_t masked_hamming8(const uint32_t (&b)[8], cons
   return (uint32_t)__popc(s3) + (uint32_t)__popc(v[7]) + 2u * (uint32_t)__popc(s4) + 4u * (uint32_t)__popc(c4);
 }
 
-template <int WIN, int DIR>
+// the same with both views' masks: popcount((b ^ o) & m & mo)
+__device__ __forceinline__ uint32_t masked2_hamming8(const uint32_t (&b)[8], const uint32_t (&o)[8],
+                                                     const uint32_t (&m)[8], const uint32_t (&mo)[8]) {
+  uint32_t mm[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) mm[j] = m[j] & mo[j];
+  return masked_hamming8(b, o, mm);
+}
+
+template <int WIN, int DIR, int MM>
 __device__ __forceinline__ void cost_long_body(const LongArgs &a, uint8_t *smem_raw) {
   constexpr int R = WIN / 2, OUTC = 32 - 2 * R;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
   const int nd = nwarps * kDC, ocols = 32 + nd - 1;
-  const int stage_words = 64 * kChunkWords + ocols * kChunkWords;
+  const int stage_words = 64 * kChunkWords + (MM + 1) * ocols * kChunkWords;
   uint32_t *stages = reinterpret_cast<uint32_t *>(smem_raw);
   uint32_t *keys = stages + 2 * stage_words;  // [2][nwarps][32]
   uint4 *ring = reinterpret_cast<uint4 *>(keys + 2 * nwarps * 32);
@@ -197,6 +208,7 @@ __device__ __forceinline__ void cost_long_body(const LongArgs &a, uint8_t *smem_
   const uint32_t *__restrict__ Bref = a.B[DIR];
   const uint32_t *__restrict__ Phiref = a.Phi[DIR];
   const uint32_t *__restrict__ Both = a.O[DIR];
+  const uint32_t *__restrict__ Phioth = a.OPhi[DIR];
   int32_t *__restrict__ disp = a.disp[DIR];
   const int w = a.w, h = a.h, dmax = a.dmax, nw = a.nw, nch = nw / kChunkWords;
   const uint32_t nbits = 32u * (uint32_t)nw;
@@ -214,7 +226,7 @@ __device__ __forceinline__ void cost_long_body(const LongArgs &a, uint8_t *smem_
     if (y < 0 || y >= h) return;
     uint32_t *st = stages + s * stage_words;
     const int nref = 2 * 32 * 2, noth = ocols * 2;  // 16-byte halves of each pixel's chunk
-    for (int i = tid; i < nref + noth; i += blockDim.x) {
+    for (int i = tid; i < nref + (MM + 1) * noth; i += blockDim.x) {
       if (i < nref) {
         const int plane = i >> 6, j = (i >> 1) & 31, half = i & 1;
         const int gx = x0 + j;
@@ -222,11 +234,11 @@ __device__ __forceinline__ void cost_long_body(const LongArgs &a, uint8_t *smem_
           cp_async16(st + plane * 32 * kChunkWords + j * kChunkWords + 4 * half,
                      (plane ? Phiref : Bref) + ((size_t)y * w + gx) * nw + ch * kChunkWords + 4 * half);
       } else {
-        const int r = i - nref, p = r >> 1, half = r & 1;
+        const int r0 = i - nref, plane = r0 >= noth ? 1 : 0, r = r0 - plane * noth, p = r >> 1, half = r & 1;
         const int gx = ox0 + p;
         if (gx >= 0 && gx < w)
-          cp_async16(st + 64 * kChunkWords + p * kChunkWords + 4 * half,
-                     Both + ((size_t)y * w + gx) * nw + ch * kChunkWords + 4 * half);
+          cp_async16(st + 64 * kChunkWords + (plane * ocols + p) * kChunkWords + 4 * half,
+                     (plane ? Phioth : Both) + ((size_t)y * w + gx) * nw + ch * kChunkWords + 4 * half);
       }
     }
   };
@@ -267,7 +279,13 @@ __device__ __forceinline__ void cost_long_body(const LongArgs &a, uint8_t *smem_
       for (int dd = 0; dd < kDC; ++dd) {
         uint32_t o[8];
         load8(ob + (DIR == 0 ? -dd : dd) * kChunkWords, q, o);
-        C[dd >> 1] += masked_hamming8(b, o, m) << (16 * (dd & 1));
+        if constexpr (MM) {
+          uint32_t mo[8];
+          load8(ob + (ocols + (DIR == 0 ? -dd : dd)) * kChunkWords, q, mo);
+          C[dd >> 1] += masked2_hamming8(b, o, m, mo) << (16 * (dd & 1));
+        } else {
+          C[dd >> 1] += masked_hamming8(b, o, m) << (16 * (dd & 1));
+        }
       }
     }
     if (ch != nch - 1) continue;
@@ -320,25 +338,37 @@ __device__ __forceinline__ void cost_long_body(const LongArgs &a, uint8_t *smem_
   if (warp == 0 && y_first + n_it - 1 - R >= yb) reduce_keys(n_it - 1);
 }
 
-template <int WIN>
+template <int WIN, int MM>
 __global__ void __launch_bounds__(1024, 1) cost_long_kernel(const LongArgs a) {
   extern __shared__ __align__(16) uint8_t smem_raw[];
-  if (blockIdx.z == 0) cost_long_body<WIN, 0>(a, smem_raw);
-  else cost_long_body<WIN, 1>(a, smem_raw);
+  if (blockIdx.z == 0) cost_long_body<WIN, 0, MM>(a, smem_raw);
+  else cost_long_body<WIN, 1, MM>(a, smem_raw);
 }
 
-template <int WIN>
+template <int WIN, int MM>
 cudaError_t launch_long_t(const LongArgs &a, cudaStream_t s) {
   constexpr int OUTC = 32 - 2 * (WIN / 2);
   const int nwarps = (a.dmax + kDC - 1) / kDC, nd = nwarps * kDC, nt = nwarps * 32;
-  const size_t stage_words = 64 * kChunkWords + (size_t)(32 + nd - 1) * kChunkWords;
+  const size_t stage_words = 64 * kChunkWords + (size_t)(MM + 1) * (32 + nd - 1) * kChunkWords;
   size_t smem = 4 * (2 * stage_words + 2 * (size_t)nwarps * 32);
   if (WIN > 1) smem += (size_t)WIN * nt * 16;
-  cudaError_t e = cudaFuncSetAttribute(cost_long_kernel<WIN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e =
+      cudaFuncSetAttribute(cost_long_kernel<WIN, MM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   dim3 grid((a.w + OUTC - 1) / OUTC, (a.h + a.rows - 1) / a.rows, 2);
-  cost_long_kernel<WIN><<<grid, nt, smem, s>>>(a);
+  cost_long_kernel<WIN, MM><<<grid, nt, smem, s>>>(a);
   return cudaGetLastError();
+}
+
+template <int MM>
+cudaError_t launch_long_win(int win, const LongArgs &a, cudaStream_t s) {
+  switch (win) {
+    case 1: return launch_long_t<1, MM>(a, s);
+    case 3: return launch_long_t<3, MM>(a, s);
+    case 5: return launch_long_t<5, MM>(a, s);
+    case 7: return launch_long_t<7, MM>(a, s);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 }  // namespace
@@ -369,18 +399,14 @@ cudaError_t launch_cost_long(const bsm_ctx *ctx, const uint32_t *BL, const uint3
                              const uint32_t *PhiR, int w, int h, int dmax, int32_t *dL, int32_t *dR, uint16_t *cost,
                              cudaStream_t s) {
   LongArgs a{};
-  a.B[0] = BL; a.Phi[0] = PhiL; a.O[0] = BR; a.disp[0] = dL;
-  a.B[1] = BR; a.Phi[1] = PhiR; a.O[1] = BL; a.disp[1] = dR;
+  a.B[0] = BL; a.Phi[0] = PhiL; a.O[0] = BR; a.OPhi[0] = PhiR; a.disp[0] = dL;
+  a.B[1] = BR; a.Phi[1] = PhiR; a.O[1] = BL; a.OPhi[1] = PhiL; a.disp[1] = dR;
   a.cost = cost;
   a.w = w; a.h = h; a.dmax = dmax; a.nw = ctx->nw;
   a.rows = ctx->cost_rows > 0 ? ctx->cost_rows : (h >= 256 ? 64 : 16);
-  switch (ctx->p.agg_window) {
-    case 1: return launch_long_t<1>(a, s);
-    case 3: return launch_long_t<3>(a, s);
-    case 5: return launch_long_t<5>(a, s);
-    case 7: return launch_long_t<7>(a, s);
-    default: return cudaErrorInvalidValue;
-  }
+  if (a.nw % kChunkWords != 0) return cudaErrorInvalidValue;
+  return ctx->p.mask_mode == BSM_MASK_BOTH ? launch_long_win<1>(ctx->p.agg_window, a, s)
+                                           : launch_long_win<0>(ctx->p.agg_window, a, s);
 }
 
 }  // namespace bsm

@@ -218,7 +218,8 @@ bsm_status bsm_server_create(const bsm_params *params, const bsm_server_config *
     return BSM_ERR_INVALID_ARG;
   const bsm_status v = bsm_validate_params(params);
   if (v != BSM_OK) return v;
-  if (params->n_bits > bsm::kMaxShortBits) return BSM_ERR_UNSUPPORTED;  // served through bsm_batch_run
+  // served through bsm_batch_run
+  if (params->n_bits > bsm::kMaxShortBits || params->mask_mode == BSM_MASK_BOTH) return BSM_ERR_UNSUPPORTED;
   bsm_server *s = new (std::nothrow) bsm_server();
   if (s == nullptr) return BSM_ERR_OUT_OF_MEMORY;
   s->params = *params;

@@ -116,12 +116,17 @@ def forward_warp(left: np.ndarray, disp: np.ndarray, rng: np.random.Generator) -
     return right.reshape(h, w, 3)
 
 
+def radiometric_fixed(img: np.ndarray, gain: float, gamma: float, off=(0.0, 0.0, 0.0)) -> np.ndarray:
+    """v' = clamp(round(255 (gain v / 255)^gamma + off_c)): one exposure/illumination setting."""
+    v = 255.0 * np.power(gain * img.astype(np.float64) / 255.0, gamma) + np.asarray(off, np.float64)
+    return np.clip(np.rint(v), 0, 255).astype(np.uint8)
+
+
 def radiometric(img: np.ndarray, rng: np.random.Generator) -> np.ndarray:
     gain = rng.uniform(0.5, 2.0)
     gamma = rng.uniform(0.7, 1.5)
     off = rng.uniform(-20.0, 20.0, size=3)
-    v = 255.0 * np.power(gain * img.astype(np.float64) / 255.0, gamma) + off
-    return np.clip(np.rint(v), 0, 255).astype(np.uint8)
+    return radiometric_fixed(img, gain, gamma, off)
 
 
 def stereo_pair(w: int, h: int, dmax: int, seed: int, radiometric_change: bool = False):

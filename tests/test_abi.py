@@ -41,7 +41,7 @@ def test_every_declared_symbol_is_exported(lib):
 def test_status_strings(lib):
     assert bsm.bsm_status_string(0) == "ok"
     assert "timed out" in bsm.bsm_status_string(bsm.BSM_ERR_TIMEOUT)
-    assert bsm.bsm_abi_version() == 1
+    assert bsm.bsm_abi_version() == 2
 
 
 def _params(**kw):
@@ -79,6 +79,17 @@ def test_validate_params(lib):
         bsm.BSM_ERR_INVALID_ARG
     assert bsm.bsm_validate_params(_params(pairs=synth.pair_table(8192, 31, seed=6), agg_window=1)) == \
         bsm.BSM_ERR_INVALID_ARG
+    # mask modes: 0 (Eq. 8), 1 (no mask, Eq. 4), 2 (both views' masks, n >= 256)
+    assert bsm.bsm_validate_params(_params(mask_mode=3)) == bsm.BSM_ERR_INVALID_ARG
+    assert bsm.bsm_validate_params(_params(mask_mode=-1)) == bsm.BSM_ERR_INVALID_ARG
+    assert bsm.bsm_validate_params(_params(mask_mode=1, mask_rank=5)) == bsm.BSM_ERR_INVALID_ARG
+    assert bsm.bsm_validate_params(_params(mask_mode=1)) == bsm.BSM_OK
+    assert bsm.bsm_validate_params(_params(mask_mode=2)) == bsm.BSM_OK
+    assert bsm.bsm_validate_params(_params(mask_mode=2, pairs=synth.pair_table(128, 31, seed=8))) == \
+        bsm.BSM_ERR_UNSUPPORTED
+    with pytest.raises(bsm.BsmError) as e:
+        bsm.bsm_server_create(_params(mask_mode=2))
+    assert e.value.status == bsm.BSM_ERR_UNSUPPORTED
     # the server batches descriptors of up to 256 bits; it refuses longer ones before touching a device
     with pytest.raises(bsm.BsmError) as e:
         bsm.bsm_server_create(_params(pairs=synth.pair_table(512, 31, seed=7)))

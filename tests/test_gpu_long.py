@@ -163,3 +163,48 @@ def test_long_descriptors_refused_where_not_built(B):
         B.bsm_batch_run(ctx, [d])
     assert e.value.status == B.BSM_ERR_UNSUPPORTED
     B.bsm_destroy(ctx)
+
+
+# ---------------------------------------------------------------- mask ablations
+
+@pytest.mark.parametrize("mode,n,win,dmax", [(1, 256, 5, 40), (1, 64, 1, 24), (2, 256, 5, 40), (2, 256, 1, 137),
+                                             (2, 512, 3, 24)])
+def test_mask_modes_full_chain(B, orc, mode, n, win, dmax):
+    w, h = 83, 31
+    l, r, _ = synth.stereo_pair(w, h, dmax, seed=800 + n + mode)
+    pairs = synth.pair_table(n, 31, seed=801)
+    ctx = B.bsm_create(B.make_params(pairs, agg_window=win, dmax=dmax, vote_radius=5, mask_mode=mode))
+    nw = n // 32
+    BL, PL, dl, pitch = _describe(B, ctx, l, nw)
+    BR, PR, _, _ = _describe(B, ctx, r, nw)
+    dL = torch.empty((h, w), dtype=torch.int32, device="cuda")
+    dR = torch.empty_like(dL)
+    cost = torch.zeros((h, w, dmax), dtype=torch.int16, device="cuda")
+    B.bsm_cost_aggregate_wta(ctx, BL, PL, BR, PR, w, h, dmax, dL, dR, cost)
+    out = torch.empty_like(dL)
+    B.bsm_refine(ctx, dl, pitch, dL, dR, w, h, dmax, out)
+    torch.cuda.synchronize()
+    ref = orc.pipeline(l, r, pairs, dmax, win=win, R=5, mask_mode=mode)
+    assert (u32(PL) == ref["PhiL"]).all() and (u32(PR) == ref["PhiR"]).all()
+    A = orc.aggregate(ref["BL"], ref["PhiL"], ref["BR"], dmax, win, 0, Phioth=ref["PhiR"] if mode == 2 else None)
+    assert (cost.cpu().numpy().view(np.uint16).astype(np.uint32) == A).all()
+    assert (dL.cpu().numpy() == ref["dL"]).all()
+    assert (dR.cpu().numpy() == ref["dR"]).all()
+    assert (out.cpu().numpy() == ref["disp"]).all()
+    B.bsm_destroy(ctx)
+
+
+def test_both_masks_refused_where_not_built(B):
+    ctx = B.bsm_create(B.make_params(synth.pair_table(256, 31, seed=810), dmax=16, mask_mode=2))
+    with pytest.raises(B.BsmError) as e:
+        B.bsm_set_tuning(ctx, 0, 0, 0, 2)
+    assert e.value.status == B.BSM_ERR_UNSUPPORTED
+    w, h = 32, 8
+    t = lambda *s: torch.zeros(s, dtype=torch.int32, device="cuda")
+    img = torch.zeros((h, 3 * w), dtype=torch.uint8, device="cuda")
+    d = B.pair_desc(img, img, w, h, 3 * w, 16, t(h, w, 8), t(h, w, 8), t(h, w, 8), t(h, w, 8), t(h, w), t(h, w),
+                    t(h, w))
+    with pytest.raises(B.BsmError) as e:
+        B.bsm_batch_run(ctx, [d])
+    assert e.value.status == B.BSM_ERR_UNSUPPORTED
+    B.bsm_destroy(ctx)

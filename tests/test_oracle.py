@@ -278,6 +278,57 @@ def test_aggregation_is_zero_padded_box_sum(orc):
                 assert (A[:, :, d] == ref.astype(np.int64)).all()
 
 
+# ---------------------------------------------------------------- mask ablations (Eq. 4; both views' masks)
+
+def test_both_masks_brute_force_and_symmetry(orc):
+    # popcount((b ^ o) & m & mo) written bit by bit on tiny planes, the matched pixel's mask taken at x_d
+    rng = np.random.default_rng(41)
+    h, w, nw = 3, 7, 1
+    BL, BR, PL, PR = (rng.integers(0, 2**32, size=(h, w, nw), dtype=np.uint32) for _ in range(4))
+    for y in range(h):
+        for x in range(w):
+            for d in range(4):
+                xd = x - d
+                if xd < 0:
+                    assert orc.cost_at(BL, PL, BR, x, y, d, 0, Phioth=PR) == 32
+                    continue
+                want = sum(1 for i in range(32)
+                           if ((int(BL[y, x, 0]) >> i) & 1) != ((int(BR[y, xd, 0]) >> i) & 1)
+                           and (int(PL[y, x, 0]) >> i) & 1 and (int(PR[y, xd, 0]) >> i) & 1)
+                assert orc.cost_at(BL, PL, BR, x, y, d, 0, Phioth=PR) == want
+                # with both masks the cost no longer depends on which view is the reference
+                assert orc.cost_at(BR, PR, BL, xd, y, d, 1, Phioth=PL) == want
+
+
+def test_both_masks_reduce_to_eq8_and_bound_it(orc):
+    l, r, _ = synth.stereo_pair(40, 12, 10, seed=42)
+    pairs = synth.pair_table(64, 31, seed=43)
+    BL, PhiL = orc.describe(l, pairs)
+    BR, PhiR = orc.describe(r, pairs)
+    ones = np.full_like(PhiR, 0xFFFFFFFF)
+    A8 = orc.aggregate(BL, PhiL, BR, 10, 3, 0)
+    assert (orc.aggregate(BL, PhiL, BR, 10, 3, 0, Phioth=ones) == A8).all()
+    A2 = orc.aggregate(BL, PhiL, BR, 10, 3, 0, Phioth=PhiR)
+    assert (A2 <= A8).all() and (A2 < A8).any()
+
+
+def test_no_mask_pipeline_is_eq4(orc):
+    # MASK_NONE: Phi is all ones, so the WTA runs on the plain Hamming distance of Eq. 4
+    l, r, _ = synth.stereo_pair(36, 14, 9, seed=44)
+    pairs = synth.pair_table(64, 31, seed=45)
+    ref = orc.pipeline(l, r, pairs, 9, win=1, R=3, mask_mode=orc.MASK_NONE)
+    assert (ref["PhiL"] == 0xFFFFFFFF).all() and (ref["PhiR"] == 0xFFFFFFFF).all()
+    BL, BR = ref["BL"], ref["BR"]
+    for x in range(36):
+        ham = np.stack([bitcount(BL[:, x] ^ BR[:, x - d]).sum(axis=1) if x - d >= 0 else np.full(14, 64)
+                        for d in range(9)], axis=1)
+        assert (ref["dL"][:, x] == np.argmin(ham, axis=1)).all()
+    # describe with k = n sets every mask bit: the same maps
+    kn = orc.pipeline(l, r, pairs, 9, win=1, R=3, k=64)
+    assert (kn["PhiL"] == 0xFFFFFFFF).all()
+    assert (kn["dL"] == ref["dL"]).all() and (kn["disp"] == ref["disp"]).all()
+
+
 # ---------------------------------------------------------------- WTA (Eq. 1)
 
 def test_wta_is_first_argmin(orc):

@@ -43,6 +43,8 @@ MUTANTS = {
     "Eq. 10 lambda_c": ("Ec[c] = (uint32_t)std::lround(32768.0 * std::exp(-(double)c / lambda_c));",
                         "Ec[c] = (uint32_t)std::lround(32768.0 * std::exp(-(double)c / lambda_e));"),
     "Eq. 9 largest d on ties": ("        if (W[d] > best) {", "        if (W[d] >= best && W[d] > 0) {"),
+    "both-mask ablation at x": ("const uint32_t *mo = Phioth + ((size_t)y * w + xd) * nw;",
+                                "const uint32_t *mo = Phioth + ((size_t)y * w + x) * nw;"),
     "fallback max": ("if (left >= 0 && right >= 0) arg = std::min(left, right);",
                      "if (left >= 0 && right >= 0) arg = std::max(left, right);"),
 }
