@@ -59,6 +59,7 @@ def parse():
     ap.add_argument("--batch-rows", type=int, default=0, help="rows per task of the batched cost kernel (0: 64)")
     ap.add_argument("--no-autotune", action="store_true", help="skip the launch-shape autotuner")
     ap.add_argument("--n-bits", type=int, default=N_BITS, help="descriptor length n (32 ... 4096)")
+    ap.add_argument("--sgm", default="", help="P1,P2,paths: semi-global aggregation of both cost volumes")
     ap.add_argument("--quality", action="store_true",
                     help="bad-pixel rates against the generator's ground truth: mask ablation, radiometric 3x3")
     ap.add_argument("--sweep-n", action="store_true",
@@ -488,6 +489,12 @@ def run_pair(args, cfg, world, rank, local, n_bits=N_BITS, window_S=WINDOW_S, si
     out = torch.empty_like(dL)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
     ev = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(args.steps)]
+    sgm = tuple(int(v) for v in args.sgm.split(",")) if args.sgm else None
+    if sgm:  # semi-global aggregation of both views' cost volumes replaces Eq. 1 on the box sums
+        cL = torch.empty((h, w, dmax), dtype=torch.int16, device=dev)
+        cR = torch.empty_like(cL)
+        S = torch.empty((h, w, dmax), dtype=torch.int32, device=dev)
+        sL, sR = torch.empty_like(dL), torch.empty_like(dL)
 
     def step(e=None):
         if e: e[0].record(stream)
@@ -495,9 +502,14 @@ def run_pair(args, cfg, world, rank, local, n_bits=N_BITS, window_S=WINDOW_S, si
         if e: e[1].record(stream)
         bsm.bsm_describe(ctx, dr, w, h, pitch, BR, PR, s)
         if e: e[2].record(stream)
-        bsm.bsm_cost_aggregate_wta(ctx, BL, PL, BR, PR, w, h, dmax, dL, dR, None, s)
+        if sgm:
+            bsm.bsm_cost_volumes(ctx, BL, PL, BR, PR, w, h, dmax, dL, dR, cL, cR, s)
+            bsm.bsm_sgm(ctx, cL, w, h, dmax, *sgm, S, sL, s)
+            bsm.bsm_sgm(ctx, cR, w, h, dmax, *sgm, S, sR, s)
+        else:
+            bsm.bsm_cost_aggregate_wta(ctx, BL, PL, BR, PR, w, h, dmax, dL, dR, None, s)
         if e: e[3].record(stream)
-        bsm.bsm_refine(ctx, dl, pitch, dL, dR, w, h, dmax, out, s)
+        bsm.bsm_refine(ctx, dl, pitch, *((sL, sR) if sgm else (dL, dR)), w, h, dmax, out, s)
         if e: e[4].record(stream)
 
     with torch.cuda.stream(stream):
@@ -543,11 +555,12 @@ def run_pair(args, cfg, world, rank, local, n_bits=N_BITS, window_S=WINDOW_S, si
                    "parallelism": f"replicas x{world}",
                    "l2": f"flushed between timed steps ({L2_FLUSH_BYTES >> 20} MiB write)"},
         "stage_ms": {"describe_left": float(per[:, 0].mean()), "describe_right": float(per[:, 1].mean()),
-                     "cost_aggregate_wta": float(per[:, 2].mean()), "refine": float(per[:, 3].mean())},
+                     ("cost_volumes_and_sgm" if sgm else "cost_aggregate_wta"): float(per[:, 2].mean()),
+                     "refine": float(per[:, 3].mean())},
         "pairs_per_s": world / (t_step * 1e-3),
         "bad_pixel_rate": bad,  # |d - d_gt| > 1 against the generator's ground truth, rank 0's pair
         # colour pre-pass + describe per view, the cost stage's kernels, refine
-        "gpu_launches": (4 + klaunch + 1) * args.steps,
+        "gpu_launches": (4 + klaunch + 1 + (2 * sgm[2] if sgm else 0)) * args.steps,
         "roofline": {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": peak,
                      "unit": "Gpopc/s", "frac": achieved / peak, "traffic": traffic,
                      "work_per_launch": word_ops,
@@ -555,7 +568,10 @@ def run_pair(args, cfg, world, rank, local, n_bits=N_BITS, window_S=WINDOW_S, si
         "clocks": clocks,
         "tuning": tuning,
     }
-    if e2e:
+    if sgm:
+        line["config"]["sgm"] = {"P1": sgm[0], "P2": sgm[1], "paths": sgm[2]}
+        line["roofline"] = None  # the cost stage also holds both views' semi-global aggregation
+    if e2e and not sgm:
         # end to end through the host-buffer C-ABI call (H2D of both views and D2H of the map inside)
         hl = torch.from_numpy(left).pin_memory()
         hr = torch.from_numpy(right).pin_memory()
@@ -615,7 +631,7 @@ def run_quality(args, cfg, world, rank, local):
     # this library's default descriptor, and the paper's (n = 4096, S = 26, sigma = 4) with a 3 x 3 box
     settings = {"n=256, S=31": (256, 31, None, AGG), "n=4096, S=26, sigma=4": (4096, 26, 4.0, 3)}
 
-    def evaluate(setting, mode, agg, transform=None):
+    def evaluate(setting, mode, agg, transform=None, sgm=None):
         n, S, sigma, _ = settings[setting]
         pairs = synth.pair_table(n, S, sigma=sigma, seed=PAIR_SEED)
         m = bsm.Matcher(pairs, window_S=S + (S % 2 == 0), agg_window=agg, dmax=dmax, vote_radius=VOTE_R,
@@ -625,7 +641,8 @@ def run_quality(args, cfg, world, rank, local):
             left, right, gt = views[s]
             if transform is not None:
                 right = transform(right)
-            out = m.match(torch.from_numpy(left).cuda(), torch.from_numpy(np.ascontiguousarray(right)).cuda(), dmax)
+            dl, dr = torch.from_numpy(left).cuda(), torch.from_numpy(np.ascontiguousarray(right)).cuda()
+            out = m.match(dl, dr, dmax) if sgm is None else m.match_sgm(dl, dr, dmax, *sgm)
             rates.append(bad_pixel_rate(out.cpu().numpy(), gt))
         m.close()
         return float(np.mean(rates))
@@ -635,6 +652,12 @@ def run_quality(args, cfg, world, rank, local):
         for mode in (0, 1, 2):
             for agg in (1, agg_box):
                 table[f"{setting}: {MASK_NAMES[mode]}, window {agg}"] = evaluate(setting, mode, agg)
+            if setting.startswith("n=256"):
+                for agg in (1, agg_box):
+                    for P1, P2 in ((2, 8), (4, 32)):
+                        P1w, P2w = P1 * agg * agg, P2 * agg * agg
+                        table[f"{setting}: {MASK_NAMES[mode]}, window {agg}, SGM 8 paths P1={P1w} P2={P2w}"] = \
+                            evaluate(setting, mode, agg, sgm=(P1w, P2w, 8))
             radio[f"{setting}: {MASK_NAMES[mode]}, window {agg_box}"] = {
                 f"gain {g} gamma {gm}": evaluate(setting, mode, agg_box,
                                                  lambda r, g=g, gm=gm: synth.radiometric_fixed(r, g, gm))

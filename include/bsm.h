@@ -127,6 +127,32 @@ bsm_status bsm_cost_aggregate_wta(bsm_ctx *ctx, const uint32_t *BL, const uint32
                                   const uint32_t *PhiR, int32_t w, int32_t h, int32_t dmax, int32_t *dispL,
                                   int32_t *dispR, uint16_t *costL_or_null, void *stream);
 
+/*
+ * bsm_cost_aggregate_wta writing both aggregated cost volumes: costL[y][x][d] = A(x, d) with the left
+ * view as reference (match x - d) and costR[y][x][d] with the right view as reference (match x + d),
+ * device uint16 [h][w][dmax] each (both required). Same kernels, same WTA outputs, same errors.
+ */
+bsm_status bsm_cost_volumes(bsm_ctx *ctx, const uint32_t *BL, const uint32_t *PhiL, const uint32_t *BR,
+                            const uint32_t *PhiR, int32_t w, int32_t h, int32_t dmax, int32_t *dispL, int32_t *dispR,
+                            uint16_t *costL, uint16_t *costR, void *stream);
+
+/*
+ * Global optimisation of a cost volume, the extension the paper names as future work (Sec. 5):
+ * semi-global aggregation of the (box-aggregated) Eq. 8 cost along `paths` image directions, then
+ * Eq. 1 on the result. Directions: 4 = left-to-right, right-to-left, top-down, bottom-up; 8 adds the
+ * four diagonals. Per direction r, with m = min_k L_r(p - r, k):
+ *   L_r(p, d) = C(p, d) + min(L_r(p-r, d), L_r(p-r, d-1) + P1, L_r(p-r, d+1) + P1, m + P2) - m,
+ * and L_r(p, d) = C(p, d) where p - r leaves the image.
+ *   cost  device uint16 [h][w][dmax], e.g. bsm_cost_volumes' costL or costR (read only)
+ *   S     device uint32 [h][w][dmax] output: S(p, d) = sum over the directions of L_r(p, d)
+ *   disp  device int32 [h][w] output: the smallest d with the minimum S(p, d)
+ * 0 <= P1 <= P2 <= 65535; paths 4 or 8; dmax <= the context's dmax. Asynchronous on `stream`
+ * (one launch per direction). Errors: BSM_ERR_INVALID_ARG for a NULL or misaligned pointer or a
+ * value out of range.
+ */
+bsm_status bsm_sgm(bsm_ctx *ctx, const uint16_t *cost, int32_t w, int32_t h, int32_t dmax, int32_t P1, int32_t P2,
+                   int32_t paths, uint32_t *S, int32_t *disp, void *stream);
+
 /* One stereo pair of a batch: every pointer is a DEVICE pointer owned by the caller. */
 typedef struct {
   const uint8_t *rgbL, *rgbR;  /* RGB views, h rows of pitch_bytes each */

@@ -27,6 +27,9 @@
 //       over valid pixels of a (2R+1)^2 window; Eq. 9 keeps the smallest d on ties; if no vote is
 //       positive the nearest valid disparities to the left and right on the row are used (their
 //       minimum; the one that exists; else 0).
+//   R10 the global optimisation the paper names as future work (Sec. 5) is read as semi-global
+//       aggregation of the cost volume along straight image paths with penalties P1 (disparity change
+//       of 1) and P2 (larger change), the disparity being the smallest d with the minimum path sum.
 //
 // Parity against the paper's own numbers is unpinned for every function here: the paper prints no
 // worked example or intermediate value. Each function is pinned instead by closed forms, invariants,
@@ -343,6 +346,55 @@ int oracle_refine_region(const uint8_t *rgb, int pitch, const int32_t *dL, const
       }
       o = arg;
     }
+  return 0;
+}
+
+// Reading R10: semi-global aggregation of the cost volume C[y][x][d] along the directions
+// dirs[2 i], dirs[2 i + 1] (dx, dy), i < ndirs. For each direction, pixels are visited so that p - r
+// comes before p, and
+//   L(p, d) = C(p, d) + min(L(p-r, d), L(p-r, d-1) + P1, L(p-r, d+1) + P1, min_k L(p-r, k) + P2)
+//             - min_k L(p-r, k),
+// with L(p, d) = C(p, d) where p - r is outside the image. S = sum of L over the directions (written
+// to S when it is not null); disp = the smallest d with the minimum S(p, d).
+int oracle_sgm(const uint16_t *C, int w, int h, int dmax, int P1, int P2, const int *dirs, int ndirs, uint32_t *S,
+               int32_t *disp) {
+  if (w <= 0 || h <= 0 || dmax < 1 || P1 < 0 || P2 < 0 || ndirs < 1) return -1;
+  const size_t npx = (size_t)w * h;
+  std::vector<int64_t> sum(npx * dmax, 0), L(npx * dmax);
+  for (int r = 0; r < ndirs; ++r) {
+    const int dx = dirs[2 * r], dy = dirs[2 * r + 1];
+    if ((dx == 0 && dy == 0) || dx < -1 || dx > 1 || dy < -1 || dy > 1) return -1;
+    for (int yi = 0; yi < h; ++yi) {
+      const int y = dy >= 0 ? yi : h - 1 - yi;
+      for (int xi = 0; xi < w; ++xi) {
+        const int x = dx >= 0 ? xi : w - 1 - xi;
+        const size_t p = (size_t)y * w + x;
+        const int px = x - dx, py = y - dy;
+        if (px < 0 || px >= w || py < 0 || py >= h) {
+          for (int d = 0; d < dmax; ++d) L[p * dmax + d] = C[p * dmax + d];
+          continue;
+        }
+        const int64_t *prev = &L[((size_t)py * w + px) * dmax];
+        int64_t m = prev[0];
+        for (int k = 1; k < dmax; ++k) m = std::min(m, prev[k]);
+        for (int d = 0; d < dmax; ++d) {
+          int64_t best = std::min(prev[d], m + P2);
+          if (d > 0) best = std::min(best, prev[d - 1] + P1);
+          if (d < dmax - 1) best = std::min(best, prev[d + 1] + P1);
+          L[p * dmax + d] = C[p * dmax + d] + best - m;
+        }
+      }
+    }
+    for (size_t i = 0; i < npx * dmax; ++i) sum[i] += L[i];
+  }
+  for (size_t p = 0; p < npx; ++p) {
+    int arg = 0;
+    for (int d = 1; d < dmax; ++d)
+      if (sum[p * dmax + d] < sum[p * dmax + arg]) arg = d;
+    disp[p] = arg;
+    if (S != nullptr)
+      for (int d = 0; d < dmax; ++d) S[p * dmax + d] = (uint32_t)sum[p * dmax + d];
+  }
   return 0;
 }
 

@@ -50,6 +50,8 @@ def bind(L):
         L.oracle_refine.restype = I
         L.oracle_refine_region.argtypes = [P, I, P, P, I, I, I, I, D, D, I, I, I, I, P]
         L.oracle_refine_region.restype = I
+        L.oracle_sgm.argtypes = [P, I, I, I, I, I, P, I, P, P]
+        L.oracle_sgm.restype = I
     return L
 
 
@@ -205,23 +207,45 @@ def refine_region(imgL, dL, valid, dmax, x0, x1, y0, y1, R=15, lambda_c=9.0, lam
     return out
 
 
+SGM_DIRS4 = ((1, 0), (-1, 0), (0, 1), (0, -1))
+SGM_DIRS8 = SGM_DIRS4 + ((1, 1), (-1, 1), (1, -1), (-1, -1))
+
+
+def sgm(C, P1, P2, dirs=SGM_DIRS4):
+    """Semi-global aggregation (reading R10) of a cost volume C[h][w][dmax]: returns (S uint32, disp int32)."""
+    C = np.ascontiguousarray(C, dtype=np.uint16)
+    h, w, dmax = C.shape
+    d = np.ascontiguousarray(np.asarray(dirs, np.int32).reshape(-1))
+    S = np.zeros((h, w, dmax), np.uint32)
+    disp = np.zeros((h, w), np.int32)
+    if lib().oracle_sgm(_p(C), w, h, dmax, int(P1), int(P2), _p(d), len(d) // 2, _p(S), _p(disp)) != 0:
+        raise ValueError("oracle_sgm rejected its arguments")
+    return S, disp
+
+
 MASK_REFERENCE, MASK_NONE, MASK_BOTH = 0, 1, 2
 
 
 def pipeline(imgL, imgR, pairs, dmax, win=5, k=None, tol=1, R=15, lambda_c=9.0, lambda_e=16.0,
-             mask_mode=MASK_REFERENCE):
+             mask_mode=MASK_REFERENCE, sgm_params=None):
     """The whole method of Sec. 3 on one pair: returns dict of every intermediate and the final map.
 
     mask_mode: MASK_REFERENCE is Eq. 8 as printed; MASK_NONE drops the mask (Eq. 4, every Phi bit set);
-    MASK_BOTH also ANDs the matched pixel's Phi (the mask ablation)."""
+    MASK_BOTH also ANDs the matched pixel's Phi (the mask ablation). sgm_params = (P1, P2, dirs) replaces
+    Eq. 1 on the aggregated cost by semi-global aggregation followed by Eq. 1 (reading R10)."""
     BL, PhiL = describe(imgL, pairs, k)
     BR, PhiR = describe(imgR, pairs, k)
     if mask_mode == MASK_NONE:
         PhiL = np.full_like(PhiL, 0xFFFFFFFF)
         PhiR = np.full_like(PhiR, 0xFFFFFFFF)
     both = mask_mode == MASK_BOTH
-    dL = wta(BL, PhiL, BR, dmax, win, 0, Phioth=PhiR if both else None)
-    dR = wta(BR, PhiR, BL, dmax, win, 1, Phioth=PhiL if both else None)
+    if sgm_params is None:
+        dL = wta(BL, PhiL, BR, dmax, win, 0, Phioth=PhiR if both else None)
+        dR = wta(BR, PhiR, BL, dmax, win, 1, Phioth=PhiL if both else None)
+    else:  # reading R10 on the aggregated cost volumes of both reference views
+        P1, P2, dirs = sgm_params
+        dL = sgm(aggregate(BL, PhiL, BR, dmax, win, 0, Phioth=PhiR if both else None), P1, P2, dirs)[1]
+        dR = sgm(aggregate(BR, PhiR, BL, dmax, win, 1, Phioth=PhiL if both else None), P1, P2, dirs)[1]
     valid = lr_check(dL, dR, tol)
     out = refine(imgL, dL, valid, dmax, R, lambda_c, lambda_e)
     return {"BL": BL, "PhiL": PhiL, "BR": BR, "PhiR": PhiR, "dL": dL, "dR": dR, "valid": valid, "disp": out}

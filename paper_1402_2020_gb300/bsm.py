@@ -29,6 +29,7 @@ EXPORTED = (
     "bsm_abi_version", "bsm_set_tuning", "bsm_get_tuning", "bsm_reserve", "bsm_describe_noalloc",
     "bsm_batch_run", "bsm_reserve_batch", "bsm_last_cuda_error", "bsm_server_create", "bsm_server_submit",
     "bsm_server_poll", "bsm_server_drain", "bsm_server_get_stats", "bsm_server_destroy", "bsm_debug_set",
+    "bsm_cost_volumes", "bsm_sgm",
 )
 BSM_DEBUG_WITHHOLD_ARRIVALS = 1
 BSM_MAX_BATCH = 1024
@@ -111,6 +112,10 @@ def lib():
         L.bsm_describe.restype = S
         L.bsm_cost_aggregate_wta.argtypes = [P, P, P, P, P, I, I, I, P, P, P, P]
         L.bsm_cost_aggregate_wta.restype = S
+        L.bsm_cost_volumes.argtypes = [P, P, P, P, P, I, I, I, P, P, P, P, P]
+        L.bsm_cost_volumes.restype = S
+        L.bsm_sgm.argtypes = [P, P, I, I, I, I, I, I, P, P, P]
+        L.bsm_sgm.restype = S
         L.bsm_refine.argtypes = [P, P, I, P, P, I, I, I, P, P]
         L.bsm_refine.restype = S
         L.bsm_match_host.argtypes = [P, P, P, I, I, I, I, P, P]
@@ -261,6 +266,17 @@ def bsm_cost_aggregate_wta(ctx: int, BL, PhiL, BR, PhiR, w: int, h: int, dmax: i
                                         _ptr(dispR), _ptr(cost), _stream(stream)), "bsm_cost_aggregate_wta", ctx)
 
 
+def bsm_cost_volumes(ctx: int, BL, PhiL, BR, PhiR, w: int, h: int, dmax: int, dispL, dispR, costL, costR,
+                     stream=None) -> None:
+    _check(lib().bsm_cost_volumes(ctx, _ptr(BL), _ptr(PhiL), _ptr(BR), _ptr(PhiR), w, h, dmax, _ptr(dispL),
+                                  _ptr(dispR), _ptr(costL), _ptr(costR), _stream(stream)), "bsm_cost_volumes", ctx)
+
+
+def bsm_sgm(ctx: int, cost, w: int, h: int, dmax: int, P1: int, P2: int, paths: int, S, disp, stream=None) -> None:
+    _check(lib().bsm_sgm(ctx, _ptr(cost), w, h, dmax, P1, P2, paths, _ptr(S), _ptr(disp), _stream(stream)),
+           "bsm_sgm", ctx)
+
+
 def bsm_refine(ctx: int, rgbL, pitch: int, dispL, dispR, w: int, h: int, dmax: int, out, stream=None) -> None:
     _check(lib().bsm_refine(ctx, _ptr(rgbL), pitch, _ptr(dispL), _ptr(dispR), w, h, dmax, _ptr(out),
                             _stream(stream)), "bsm_refine", ctx)
@@ -373,6 +389,22 @@ class Matcher:
         BR, PhiR = self.describe(rgbR, stream)
         dL, dR, _ = self.cost_wta(BL, PhiL, BR, PhiR, dmax, stream=stream)
         return self.refine(rgbL, dL, dR, dmax, stream)
+
+    def match_sgm(self, rgbL, rgbR, dmax, P1, P2, paths=8, stream=None):
+        """The method with semi-global aggregation of both views' cost volumes before Eq. 1."""
+        t = self.torch
+        h, w, _ = rgbL.shape
+        BL, PhiL = self.describe(rgbL, stream)
+        BR, PhiR = self.describe(rgbR, stream)
+        dL = t.empty((h, w), dtype=t.int32, device=rgbL.device)
+        dR, sL, sR = t.empty_like(dL), t.empty_like(dL), t.empty_like(dL)
+        cL = t.empty((h, w, dmax), dtype=t.int16, device=rgbL.device)
+        cR = t.empty_like(cL)
+        S = t.empty((h, w, dmax), dtype=t.int32, device=rgbL.device)
+        bsm_cost_volumes(self.ctx, BL, PhiL, BR, PhiR, w, h, dmax, dL, dR, cL, cR, stream)
+        bsm_sgm(self.ctx, cL, w, h, dmax, P1, P2, paths, S, sL, stream)
+        bsm_sgm(self.ctx, cR, w, h, dmax, P1, P2, paths, S, sR, stream)
+        return self.refine(rgbL, sL, sR, dmax, stream)
 
 
 def bsm_server_create(params: bsm_params, lanes: int = 2, max_batch: int = 64, device_budget: int = 0,

@@ -205,7 +205,28 @@ bsm_status bsm_cost_aggregate_wta(bsm_ctx *ctx, const uint32_t *BL, const uint32
   if (!size_ok(w, h) || dmax < 1 || dmax > ctx->p.dmax) return BSM_ERR_INVALID_ARG;
   if (!aligned16(BL) || !aligned16(PhiL) || !aligned16(BR) || !aligned16(PhiR)) return BSM_ERR_INVALID_ARG;
   return from_cuda(ctx, bsm::launch_cost_wta(ctx, BL, PhiL, BR, PhiR, w, h, dmax, dispL, dispR, costL_or_null,
+                                             nullptr, (cudaStream_t)stream));
+}
+
+bsm_status bsm_cost_volumes(bsm_ctx *ctx, const uint32_t *BL, const uint32_t *PhiL, const uint32_t *BR,
+                            const uint32_t *PhiR, int32_t w, int32_t h, int32_t dmax, int32_t *dispL, int32_t *dispR,
+                            uint16_t *costL, uint16_t *costR, void *stream) {
+  if (ctx == nullptr || BL == nullptr || PhiL == nullptr || BR == nullptr || PhiR == nullptr || dispL == nullptr ||
+      dispR == nullptr || costL == nullptr || costR == nullptr)
+    return BSM_ERR_INVALID_ARG;
+  if (!size_ok(w, h) || dmax < 1 || dmax > ctx->p.dmax) return BSM_ERR_INVALID_ARG;
+  if (!aligned16(BL) || !aligned16(PhiL) || !aligned16(BR) || !aligned16(PhiR)) return BSM_ERR_INVALID_ARG;
+  return from_cuda(ctx, bsm::launch_cost_wta(ctx, BL, PhiL, BR, PhiR, w, h, dmax, dispL, dispR, costL, costR,
                                              (cudaStream_t)stream));
+}
+
+bsm_status bsm_sgm(bsm_ctx *ctx, const uint16_t *cost, int32_t w, int32_t h, int32_t dmax, int32_t P1, int32_t P2,
+                   int32_t paths, uint32_t *S, int32_t *disp, void *stream) {
+  if (ctx == nullptr || cost == nullptr || S == nullptr || disp == nullptr) return BSM_ERR_INVALID_ARG;
+  if (!size_ok(w, h) || dmax < 1 || dmax > ctx->p.dmax) return BSM_ERR_INVALID_ARG;
+  if (P1 < 0 || P2 < P1 || P2 > 65535 || (paths != 4 && paths != 8)) return BSM_ERR_INVALID_ARG;
+  if (((uintptr_t)cost & 1) != 0 || ((uintptr_t)S & 3) != 0 || ((uintptr_t)disp & 3) != 0) return BSM_ERR_INVALID_ARG;
+  return from_cuda(ctx, bsm::launch_sgm(cost, w, h, dmax, P1, P2, paths, S, disp, (cudaStream_t)stream));
 }
 
 bsm_status bsm_refine(bsm_ctx *ctx, const uint8_t *rgbL_dev, int32_t pitch_bytes, const int32_t *dispL,
@@ -250,7 +271,8 @@ bsm_status bsm_match_host(bsm_ctx *ctx, const uint8_t *rgbL_host, const uint8_t 
   if (e == cudaSuccess) e = cudaMemcpyAsync(dr, rgbR_host, (size_t)h * pitch_bytes, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = bsm::launch_describe(ctx, dl, w, h, pitch_bytes, ctx->plane, BL, PhiL, s);
   if (e == cudaSuccess) e = bsm::launch_describe(ctx, dr, w, h, pitch_bytes, ctx->plane, BR, PhiR, s);
-  if (e == cudaSuccess) e = bsm::launch_cost_wta(ctx, BL, PhiL, BR, PhiR, w, h, dmax, dispL, dispR, nullptr, s);
+  if (e == cudaSuccess)
+    e = bsm::launch_cost_wta(ctx, BL, PhiL, BR, PhiR, w, h, dmax, dispL, dispR, nullptr, nullptr, s);
   if (e == cudaSuccess) e = bsm::launch_refine(ctx, dl, pitch_bytes, dispL, dispR, w, h, dmax, out, s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(out_host, out, (size_t)w * h * 4, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);

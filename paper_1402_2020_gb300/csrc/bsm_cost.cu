@@ -35,7 +35,7 @@ struct CostArgs {
   const uint32_t *Phi[2];  // reference masks per direction
   const uint32_t *O[2];    // other view's descriptors per direction
   int32_t *disp[2];
-  uint16_t *cost;          // optional, direction 0 only
+  uint16_t *cost[2];       // optional aggregated cost volume per reference view
   uint32_t *status;
   int w, h, dmax, rows;
   int withhold;            // test hook: skip the mbarrier arrivals so the bounded waits run out
@@ -357,7 +357,7 @@ __device__ __forceinline__ bool cost_task(const CostTask &t, uint8_t *smem_raw, 
         const uint32_t ae = A & 0xFFFFu, ao = A >> 16;
         if (de < dmax) key = min(key, (ae << 10) | (uint32_t)de);
         if (de + 1 < dmax) key = min(key, (ao << 10) | (uint32_t)(de + 1));
-        if (DIR == 0 && t.cost != nullptr && out_lane) {
+        if (t.cost != nullptr && out_lane) {
           uint16_t *cp = t.cost + ((size_t)yo * w + x) * dmax;
           if (de < dmax) cp[de] = (uint16_t)ae;
           if (de + 1 < dmax) cp[de + 1] = (uint16_t)ao;
@@ -393,7 +393,7 @@ __global__ void __launch_bounds__(1024, 1) cost_wta_kernel(const CostArgs a) {
   t.Phiref = dir == 0 ? a.Phi[0] : a.Phi[1];
   t.Both = dir == 0 ? a.O[0] : a.O[1];
   t.disp = dir == 0 ? a.disp[0] : a.disp[1];
-  t.cost = dir == 0 ? a.cost : nullptr;
+  t.cost = dir == 0 ? a.cost[0] : a.cost[1];
   t.w = a.w; t.h = a.h; t.dmax = a.dmax;
   t.x0 = blockIdx.x * OUTC - WIN / 2;
   t.yb = blockIdx.y * a.rows;
@@ -532,18 +532,18 @@ int pick_rows(int w, int h, int win, int dmax) {
 }  // namespace
 
 cudaError_t launch_cost_wta(const bsm_ctx *ctx, const uint32_t *BL, const uint32_t *PhiL, const uint32_t *BR,
-                            const uint32_t *PhiR, int w, int h, int dmax, int32_t *dL, int32_t *dR, uint16_t *cost,
-                            cudaStream_t s) {
+                            const uint32_t *PhiR, int w, int h, int dmax, int32_t *dL, int32_t *dR, uint16_t *costL,
+                            uint16_t *costR, cudaStream_t s) {
   if (ctx->nw > 8 || ctx->p.mask_mode == BSM_MASK_BOTH)
-    return launch_cost_long(ctx, BL, PhiL, BR, PhiR, w, h, dmax, dL, dR, cost, s);
+    return launch_cost_long(ctx, BL, PhiL, BR, PhiR, w, h, dmax, dL, dR, costL, costR, s);
   // The two-column kernel has no staging wait to withhold, so the failure-detection hook keeps the
   // one-column kernel.
   if (ctx->cost_variant != 1 && cost2_supported(ctx) && !ctx->withhold_arrivals)
-    return launch_cost2(ctx, BL, PhiL, BR, PhiR, w, h, dmax, dL, dR, cost, s);
+    return launch_cost2(ctx, BL, PhiL, BR, PhiR, w, h, dmax, dL, dR, costL, costR, s);
   CostArgs a{};
   a.B[0] = BL; a.Phi[0] = PhiL; a.O[0] = BR; a.disp[0] = dL;
   a.B[1] = BR; a.Phi[1] = PhiR; a.O[1] = BL; a.disp[1] = dR;
-  a.cost = cost;
+  a.cost[0] = costL; a.cost[1] = costR;
   a.status = ctx->status;
   a.w = w; a.h = h; a.dmax = dmax;
   a.rows = ctx->cost_rows > 0 ? ctx->cost_rows : pick_rows(w, h, ctx->p.agg_window, dmax);

@@ -26,7 +26,7 @@ constexpr int kMaxWarps = 16;
 struct Cost2Args {
   const uint32_t *B[2], *Phi[2], *O[2];
   int32_t *disp[2];
-  uint16_t *cost;  // optional, left reference only
+  uint16_t *cost[2];  // optional aggregated cost volume per reference view
   int w, h, dmax, rows, ndr;  // ndr: disparity ranges per (column block, band, view)
 };
 
@@ -310,14 +310,14 @@ __device__ __forceinline__ void cost2_body(const Cost2Args &a, uint8_t *smem_raw
             kb = min(kb, (b_hi << 10) | (uint32_t)(de + 1));
           }
         }
-        if (DIR == 0 && a.cost != nullptr) {
+        if (a.cost[DIR] != nullptr) {
           if (2 * lane >= R && 2 * lane < 64 - R && ina) {
-            uint16_t *cp = a.cost + ((size_t)yo * w + xa) * dmax;
+            uint16_t *cp = a.cost[DIR] + ((size_t)yo * w + xa) * dmax;
             if (de < dmax) cp[de] = (uint16_t)a_lo;
             if (de + 1 < dmax) cp[de + 1] = (uint16_t)a_hi;
           }
           if (2 * lane + 1 >= R && 2 * lane + 1 < 64 - R && inb) {
-            uint16_t *cp = a.cost + ((size_t)yo * w + xb) * dmax;
+            uint16_t *cp = a.cost[DIR] + ((size_t)yo * w + xb) * dmax;
             if (de < dmax) cp[de] = (uint16_t)b_lo;
             if (de + 1 < dmax) cp[de + 1] = (uint16_t)b_hi;
           }
@@ -394,12 +394,12 @@ int pick_rows2(int w, int h, int win, int ctas_z) {
 bool cost2_supported(const bsm_ctx *ctx) { return ctx->nw == 4 || ctx->nw == 8; }
 
 cudaError_t launch_cost2(const bsm_ctx *ctx, const uint32_t *BL, const uint32_t *PhiL, const uint32_t *BR,
-                         const uint32_t *PhiR, int w, int h, int dmax, int32_t *dL, int32_t *dR, uint16_t *cost,
-                         cudaStream_t s) {
+                         const uint32_t *PhiR, int w, int h, int dmax, int32_t *dL, int32_t *dR, uint16_t *costL,
+                         uint16_t *costR, cudaStream_t s) {
   Cost2Args a{};
   a.B[0] = BL; a.Phi[0] = PhiL; a.O[0] = BR; a.disp[0] = dL;
   a.B[1] = BR; a.Phi[1] = PhiR; a.O[1] = BL; a.disp[1] = dR;
-  a.cost = cost;
+  a.cost[0] = costL; a.cost[1] = costR;
   a.w = w; a.h = h; a.dmax = dmax;
   const int need = (dmax + kDC - 1) / kDC;
   const int nwarps = min(kMaxWarps, need);

@@ -105,7 +105,7 @@ cudaError_t launch_describe_plane(const bsm_ctx *ctx, const uint32_t *plane, int
 cudaError_t launch_describe(const bsm_ctx *ctx, const uint8_t *rgb, int w, int h, int pitch, uint32_t *plane,
                             uint32_t *B, uint32_t *Phi, cudaStream_t s);
 cudaError_t launch_cost_wta(const bsm_ctx *ctx, const uint32_t *BL, const uint32_t *PhiL, const uint32_t *BR,
-                            const uint32_t *PhiR, int w, int h, int dmax, int32_t *dL, int32_t *dR, uint16_t *cost,
+                            const uint32_t *PhiR, int w, int h, int dmax, int32_t *dL, int32_t *dR, uint16_t *costL, uint16_t *costR,
                             cudaStream_t s);
 // Batched kernels: prepare_* sets kernel attributes and returns the persistent grid (outside any
 // stream capture); launch_* only enqueues.
@@ -116,11 +116,13 @@ void wide_offsets(const bsm_ctx *ctx, int32_t *out);
 cudaError_t launch_describe_wide(const bsm_ctx *ctx, const uint32_t *plane, int w, int h, uint32_t *B, uint32_t *Phi,
                                  cudaStream_t s);
 cudaError_t launch_cost_long(const bsm_ctx *ctx, const uint32_t *BL, const uint32_t *PhiL, const uint32_t *BR,
-                             const uint32_t *PhiR, int w, int h, int dmax, int32_t *dL, int32_t *dR, uint16_t *cost,
+                             const uint32_t *PhiR, int w, int h, int dmax, int32_t *dL, int32_t *dR, uint16_t *costL, uint16_t *costR,
                              cudaStream_t s);
 bool cost2_supported(const bsm_ctx *ctx);
+cudaError_t launch_sgm(const uint16_t *C, int w, int h, int dmax, int P1, int P2, int paths, uint32_t *S,
+                       int32_t *disp, cudaStream_t s);
 cudaError_t launch_cost2(const bsm_ctx *ctx, const uint32_t *BL, const uint32_t *PhiL, const uint32_t *BR,
-                         const uint32_t *PhiR, int w, int h, int dmax, int32_t *dL, int32_t *dR, uint16_t *cost,
+                         const uint32_t *PhiR, int w, int h, int dmax, int32_t *dL, int32_t *dR, uint16_t *costL, uint16_t *costR,
                          cudaStream_t s);
 cudaError_t launch_refine(const bsm_ctx *ctx, const uint8_t *rgb, int pitch, const int32_t *dL, const int32_t *dR,
                           int w, int h, int dmax, int32_t *out, cudaStream_t s);

@@ -146,7 +146,7 @@ constexpr int kDC = 8, kDP = 4, kChunkWords = 8;
 struct LongArgs {
   const uint32_t *B[2], *Phi[2], *O[2], *OPhi[2];
   int32_t *disp[2];
-  uint16_t *cost;
+  uint16_t *cost[2];  // optional aggregated cost volume per reference view
   int w, h, dmax, rows, nw;
 };
 
@@ -324,8 +324,8 @@ __device__ __forceinline__ void cost_long_body(const LongArgs &a, uint8_t *smem_
         const uint32_t ae = A & 0xFFFFu, ao = A >> 16;
         if (de < dmax) key = min(key, (ae << 10) | (uint32_t)de);
         if (de + 1 < dmax) key = min(key, (ao << 10) | (uint32_t)(de + 1));
-        if (DIR == 0 && a.cost != nullptr && out_lane) {
-          uint16_t *cp = a.cost + ((size_t)yo * w + x) * dmax;
+        if (a.cost[DIR] != nullptr && out_lane) {
+          uint16_t *cp = a.cost[DIR] + ((size_t)yo * w + x) * dmax;
           if (de < dmax) cp[de] = (uint16_t)ae;
           if (de + 1 < dmax) cp[de + 1] = (uint16_t)ao;
         }
@@ -396,12 +396,12 @@ void wide_offsets(const bsm_ctx *ctx, int32_t *out) {
 }
 
 cudaError_t launch_cost_long(const bsm_ctx *ctx, const uint32_t *BL, const uint32_t *PhiL, const uint32_t *BR,
-                             const uint32_t *PhiR, int w, int h, int dmax, int32_t *dL, int32_t *dR, uint16_t *cost,
-                             cudaStream_t s) {
+                             const uint32_t *PhiR, int w, int h, int dmax, int32_t *dL, int32_t *dR, uint16_t *costL,
+                             uint16_t *costR, cudaStream_t s) {
   LongArgs a{};
   a.B[0] = BL; a.Phi[0] = PhiL; a.O[0] = BR; a.OPhi[0] = PhiR; a.disp[0] = dL;
   a.B[1] = BR; a.Phi[1] = PhiR; a.O[1] = BL; a.OPhi[1] = PhiL; a.disp[1] = dR;
-  a.cost = cost;
+  a.cost[0] = costL; a.cost[1] = costR;
   a.w = w; a.h = h; a.dmax = dmax; a.nw = ctx->nw;
   a.rows = ctx->cost_rows > 0 ? ctx->cost_rows : (h >= 256 ? 64 : 16);
   if (a.nw % kChunkWords != 0) return cudaErrorInvalidValue;

@@ -1,0 +1,232 @@
+// Semi-global aggregation of a cost volume (the global optimisation the paper leaves to future work,
+// Sec. 5), over Eq. 8's cost (box-aggregated or not) kept in HBM as [h][w][dmax] uint16.
+//
+// For each path direction r the path cost obeys
+//   L_r(p, d) = C(p, d) + min(L_r(p-r, d), L_r(p-r, d-1) + P1, L_r(p-r, d+1) + P1, m + P2) - m,
+//   m = min_k L_r(p-r, k),
+// starting with L_r(p, d) = C(p, d) where p - r leaves the image; S = sum over the paths of L_r and
+// the disparity is the smallest d reaching min_d S(p, d) (Eq. 1 applied to S).
+//
+// One warp walks one scanline of one direction; lane l holds disparities l*D .. l*D + D - 1
+// (D = ceil(dmax / 32) rounded up to a power of two), so d - 1 and d + 1 are in the same lane or one
+// shuffle away, and m is one warp-wide unsigned-min reduction. The loads of the next kPF pixels are
+// in flight while a pixel is computed (a register ring, refilled as each slot is consumed), and move
+// as 16-byte vectors when dmax allows. Paths run as separate launches on the stream: the first writes S, the
+// others add to it, and the last also reduces (S << 8 | d) keys to the disparity. Every value is an
+// exact integer: L_r <= C + P2 and S <= paths * (65535 + P2) < 2^24, so the keys fit 32 bits.
+#include "bsm_internal.cuh"
+
+namespace bsm {
+namespace {
+
+constexpr uint32_t kInf = 0x3FFFFFFFu;  // above any path cost; keeps + P2 free of overflow
+
+struct SgmArgs {
+  const uint16_t *C;
+  uint32_t *S;
+  int32_t *disp;
+  int w, h, dmax;
+  uint32_t P1, P2;
+  int dx, dy;     // path direction r
+  int nlines;
+  int mode;       // 0: S = L, 1: S += L, 2: S += L and disparity
+};
+
+// First pixel of scanline i for direction (dx, dy): every pixel whose predecessor p - r is outside.
+__device__ __forceinline__ void line_start(const SgmArgs &a, int i, int &x, int &y) {
+  if (a.dy == 0) {  // one line per row
+    y = i;
+    x = a.dx > 0 ? 0 : a.w - 1;
+  } else if (a.dx == 0) {  // one line per column
+    x = i;
+    y = a.dy > 0 ? 0 : a.h - 1;
+  } else if (i < a.w) {  // diagonals entering through the first row of the scan
+    x = i;
+    y = a.dy > 0 ? 0 : a.h - 1;
+  } else {  // ... and through the first column of the scan (its corner pixel belongs to the row)
+    const int j = i - a.w + 1;
+    x = a.dx > 0 ? 0 : a.w - 1;
+    y = a.dy > 0 ? j : a.h - 1 - j;
+  }
+}
+
+// Pixels on the scanline that starts at (x, y): steps until p leaves the image.
+__device__ __forceinline__ int line_length(const SgmArgs &a, int x, int y) {
+  int n = 0x7FFFFFFF;
+  if (a.dx > 0) n = min(n, a.w - x);
+  if (a.dx < 0) n = min(n, x + 1);
+  if (a.dy > 0) n = min(n, a.h - y);
+  if (a.dy < 0) n = min(n, y + 1);
+  return n;
+}
+
+// Costs and running sums of the lane's D disparities at one pixel. VEC: dmax is a multiple of D, so
+// a lane's D values are all in range or all out, and they move as 2 D-byte / 4 D-byte vectors.
+template <int D, bool VEC>
+__device__ __forceinline__ void fetch(const SgmArgs &a, size_t base, int d0, uint32_t (&c)[D], uint32_t (&s)[D]) {
+  if constexpr (VEC) {
+    if (d0 < a.dmax) {
+      const uint16_t *cp = a.C + base + d0;
+      const uint32_t *sp = a.S + base + d0;
+      uint32_t cw[D / 2 > 0 ? D / 2 : 1];
+      if constexpr (D == 8) {
+        const uint4 v = *reinterpret_cast<const uint4 *>(cp);
+        cw[0] = v.x; cw[1] = v.y; cw[2] = v.z; cw[3] = v.w;
+      } else if constexpr (D == 4) {
+        const uint2 v = *reinterpret_cast<const uint2 *>(cp);
+        cw[0] = v.x; cw[1] = v.y;
+      } else if constexpr (D == 2) {
+        cw[0] = *reinterpret_cast<const uint32_t *>(cp);
+      }
+      if constexpr (D == 1) {
+        c[0] = cp[0];
+      } else {
+#pragma unroll
+        for (int j = 0; j < D; ++j) c[j] = (cw[j >> 1] >> (16 * (j & 1))) & 0xFFFFu;
+      }
+      if (a.mode != 0) {
+#pragma unroll
+        for (int j = 0; j < D; j += 4 <= D ? 4 : D) {
+          if constexpr (D >= 4) {
+            const uint4 v = *reinterpret_cast<const uint4 *>(sp + j);
+            s[j] = v.x; s[j + 1] = v.y; s[j + 2] = v.z; s[j + 3] = v.w;
+          } else if constexpr (D == 2) {
+            const uint2 v = *reinterpret_cast<const uint2 *>(sp);
+            s[0] = v.x; s[1] = v.y;
+          } else {
+            s[0] = sp[0];
+          }
+        }
+      } else {
+#pragma unroll
+        for (int j = 0; j < D; ++j) s[j] = 0;
+      }
+    } else {
+#pragma unroll
+      for (int j = 0; j < D; ++j) c[j] = s[j] = 0;
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+      const int d = d0 + j;
+      c[j] = d < a.dmax ? (uint32_t)a.C[base + d] : 0u;
+      s[j] = (a.mode != 0 && d < a.dmax) ? a.S[base + d] : 0u;
+    }
+  }
+}
+
+template <int D, bool VEC>
+__device__ __forceinline__ void store_s(const SgmArgs &a, size_t base, int d0, const uint32_t (&t)[D]) {
+  if constexpr (VEC && D >= 4) {
+    if (d0 < a.dmax) {
+#pragma unroll
+      for (int j = 0; j < D; j += 4)
+        *reinterpret_cast<uint4 *>(a.S + base + d0 + j) = make_uint4(t[j], t[j + 1], t[j + 2], t[j + 3]);
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < D; ++j)
+      if (d0 + j < a.dmax) a.S[base + d0 + j] = t[j];
+  }
+}
+
+constexpr int kPF = 3;  // pixels of the scanline whose loads are in flight ahead of the arithmetic
+
+template <int D, bool VEC>
+__global__ void __launch_bounds__(128) sgm_path_kernel(const SgmArgs a) {
+  const int lane = threadIdx.x & 31;
+  const int line = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (line >= a.nlines) return;
+  int x0, y0;
+  line_start(a, line, x0, y0);
+  const int len = line_length(a, x0, y0);
+  const int d0 = lane * D, dmax = a.dmax;
+  auto pixel = [&](int k) { return ((size_t)(y0 + k * a.dy) * a.w + (x0 + k * a.dx)) * dmax; };
+
+  uint32_t c[kPF][D], s[kPF][D], Lp[D];
+#pragma unroll
+  for (int u = 0; u < kPF; ++u)
+    if (u < len) fetch<D, VEC>(a, pixel(u), d0, c[u], s[u]);
+
+  for (int k0 = 0; k0 < len; k0 += kPF) {
+#pragma unroll
+    for (int u = 0; u < kPF; ++u) {
+      const int k = k0 + u;
+      if (k >= len) break;
+      uint32_t L[D];
+      if (k == 0) {
+#pragma unroll
+        for (int j = 0; j < D; ++j) L[j] = d0 + j < dmax ? c[u][j] : kInf;
+      } else {
+        uint32_t lmin = kInf;
+#pragma unroll
+        for (int j = 0; j < D; ++j) lmin = min(lmin, Lp[j]);
+        const uint32_t m = __reduce_min_sync(0xFFFFFFFFu, lmin);
+        const uint32_t below = __shfl_up_sync(0xFFFFFFFFu, Lp[D - 1], 1);  // L(p-r, d0 - 1)
+        const uint32_t above = __shfl_down_sync(0xFFFFFFFFu, Lp[0], 1);    // L(p-r, d0 + D)
+#pragma unroll
+        for (int j = 0; j < D; ++j) {
+          const uint32_t lo = j > 0 ? Lp[j - 1] : (lane > 0 ? below : kInf);
+          const uint32_t hi = j < D - 1 ? Lp[j + 1] : (lane < 31 ? above : kInf);
+          const uint32_t best = min(min(Lp[j], min(lo, hi) + a.P1), m + a.P2);
+          L[j] = d0 + j < dmax ? c[u][j] + best - m : kInf;
+        }
+      }
+      const size_t base = pixel(k);
+      uint32_t tot[D];
+#pragma unroll
+      for (int j = 0; j < D; ++j) tot[j] = s[u][j] + L[j];
+      store_s<D, VEC>(a, base, d0, tot);
+      if (a.mode == 2) {
+        uint32_t key = 0xFFFFFFFFu;
+#pragma unroll
+        for (int j = 0; j < D; ++j)
+          if (d0 + j < dmax) key = min(key, (tot[j] << 8) | (uint32_t)(d0 + j));
+        key = __reduce_min_sync(0xFFFFFFFFu, key);
+        if (lane == 0) a.disp[base / dmax] = (int32_t)(key & 0xFFu);
+      }
+#pragma unroll
+      for (int j = 0; j < D; ++j) Lp[j] = L[j];
+      if (k + kPF < len) fetch<D, VEC>(a, pixel(k + kPF), d0, c[u], s[u]);  // refill this slot
+    }
+  }
+}
+
+template <int D, bool VEC>
+cudaError_t launch_paths(SgmArgs a, int paths, cudaStream_t s) {
+  static const int dirs[8][2] = {{1, 0}, {-1, 0}, {0, 1}, {0, -1}, {1, 1}, {-1, 1}, {1, -1}, {-1, -1}};
+  for (int r = 0; r < paths; ++r) {
+    a.dx = dirs[r][0];
+    a.dy = dirs[r][1];
+    a.nlines = a.dy == 0 ? a.h : (a.dx == 0 ? a.w : a.w + a.h - 1);
+    a.mode = r == 0 ? 0 : (r == paths - 1 ? 2 : 1);
+    const int warps = 4;
+    sgm_path_kernel<D, VEC><<<(a.nlines + warps - 1) / warps, warps * 32, 0, s>>>(a);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+}  // namespace
+
+cudaError_t launch_sgm(const uint16_t *C, int w, int h, int dmax, int P1, int P2, int paths, uint32_t *S,
+                       int32_t *disp, cudaStream_t s) {
+  SgmArgs a{};
+  a.C = C; a.S = S; a.disp = disp;
+  a.w = w; a.h = h; a.dmax = dmax;
+  a.P1 = (uint32_t)P1; a.P2 = (uint32_t)P2;
+  // vector loads need every pixel's row of dmax values to start on a 2 D-byte boundary
+  const bool vec = ((uintptr_t)C % 16 == 0) && ((uintptr_t)S % 16 == 0);
+  switch ((dmax + 31) / 32) {
+    case 1: return vec ? launch_paths<1, true>(a, paths, s) : launch_paths<1, false>(a, paths, s);
+    case 2: return vec && dmax % 2 == 0 ? launch_paths<2, true>(a, paths, s) : launch_paths<2, false>(a, paths, s);
+    case 3: case 4:
+      return vec && dmax % 4 == 0 ? launch_paths<4, true>(a, paths, s) : launch_paths<4, false>(a, paths, s);
+    case 5: case 6: case 7: case 8:
+      return vec && dmax % 8 == 0 ? launch_paths<8, true>(a, paths, s) : launch_paths<8, false>(a, paths, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace bsm

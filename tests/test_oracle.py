@@ -483,3 +483,68 @@ def test_pipeline_tracks_ground_truth(orc):
     inner = (slice(16, -16), slice(32, -16))
     bad = np.abs(res["disp"][inner] - gt[inner]) > 1
     assert bad.mean() < 0.35, bad.mean()
+
+
+# ---------------------------------------------------------------- semi-global aggregation (reading R10)
+
+def test_sgm_without_penalties_is_a_sum_of_costs(orc):
+    C = np.random.default_rng(51).integers(0, 60, size=(6, 9, 7)).astype(np.uint16)
+    for dirs in (orc.SGM_DIRS4, orc.SGM_DIRS8):
+        S, disp = orc.sgm(C, 0, 0, dirs)
+        assert (S == len(dirs) * C.astype(np.uint32)).all()
+        assert (disp == np.argmin(C, axis=2)).all()
+
+
+def _viterbi_brute_force(C, chain, P1, P2):
+    """Minimum over every labelling of the chain of sum C + penalties, per label of the last pixel."""
+    import itertools
+
+    dmax = C.shape[2]
+    best = np.full(dmax, np.iinfo(np.int64).max)
+    for labels in itertools.product(range(dmax), repeat=len(chain)):
+        cost = sum(int(C[y, x, d]) for (x, y), d in zip(chain, labels))
+        for a, b in zip(labels, labels[1:]):
+            cost += 0 if a == b else (P1 if abs(a - b) == 1 else P2)
+        best[labels[-1]] = min(best[labels[-1]], cost)
+    return best
+
+
+@pytest.mark.parametrize("direction", [(1, 0), (-1, 0), (0, 1), (0, -1), (1, 1), (-1, 1), (1, -1), (-1, -1)])
+def test_sgm_path_cost_is_the_best_labelling(orc, direction):
+    # One direction: L(p, .) is, up to a constant, the cheapest labelling of the path that ends at p.
+    rng = np.random.default_rng(52)
+    h, w, dmax, P1, P2 = 4, 5, 3, 2, 5
+    C = rng.integers(0, 9, size=(h, w, dmax)).astype(np.uint16)
+    S, _ = orc.sgm(C, P1, P2, (direction,))
+    dx, dy = direction
+    for y in range(h):
+        for x in range(w):
+            chain = [(x, y)]
+            while 0 <= chain[0][0] - dx < w and 0 <= chain[0][1] - dy < h:
+                chain.insert(0, (chain[0][0] - dx, chain[0][1] - dy))
+            V = _viterbi_brute_force(C, chain, P1, P2)
+            L = S[y, x].astype(np.int64)
+            assert (L - L.min() == V - V.min()).all(), (x, y)
+
+
+def test_sgm_transpose_and_mirror(orc):
+    C = np.random.default_rng(53).integers(0, 40, size=(7, 10, 6)).astype(np.uint16)
+    for dirs in (orc.SGM_DIRS4, orc.SGM_DIRS8):
+        S, d = orc.sgm(C, 3, 11, dirs)
+        St, dt = orc.sgm(np.ascontiguousarray(C.transpose(1, 0, 2)), 3, 11, dirs)
+        assert (St.transpose(1, 0, 2) == S).all() and (dt.T == d).all()
+        Sm, dm = orc.sgm(np.ascontiguousarray(C[:, ::-1]), 3, 11, dirs)
+        assert (Sm[:, ::-1] == S).all() and (dm[:, ::-1] == d).all()
+
+
+def test_sgm_smooths_an_outlier(orc):
+    # a constant disparity 2 everywhere except one pixel whose cost prefers 5: the penalties pull it back
+    h, w, dmax = 9, 9, 8
+    C = np.full((h, w, dmax), 20, np.uint16)
+    C[:, :, 2] = 10
+    C[4, 4, :] = 20
+    C[4, 4, 5] = 8
+    _, d0 = orc.sgm(C, 0, 0)
+    assert d0[4, 4] == 5
+    _, d1 = orc.sgm(C, 4, 30, orc.SGM_DIRS8)
+    assert (d1 == 2).all()

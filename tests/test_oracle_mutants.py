@@ -45,6 +45,12 @@ MUTANTS = {
     "Eq. 9 largest d on ties": ("        if (W[d] > best) {", "        if (W[d] >= best && W[d] > 0) {"),
     "both-mask ablation at x": ("const uint32_t *mo = Phioth + ((size_t)y * w + xd) * nw;",
                                 "const uint32_t *mo = Phioth + ((size_t)y * w + x) * nw;"),
+    "SGM without the d-1 neighbour": ("if (d > 0) best = std::min(best, prev[d - 1] + P1);", "if (d > 0) best = best;"),
+    "SGM without normalisation": ("L[p * dmax + d] = C[p * dmax + d] + best - m;", "L[p * dmax + d] = C[p * dmax + d] + best;"),
+    "SGM P2 for P1": ("int64_t best = std::min(prev[d], m + P2);", "int64_t best = std::min(prev[d], m + P1);"),
+    "SGM largest d on ties": ("if (sum[p * dmax + d] < sum[p * dmax + arg]) arg = d;",
+                              "if (sum[p * dmax + d] <= sum[p * dmax + arg]) arg = d;"),
+    "SGM direction reversed": ("const int px = x - dx, py = y - dy;", "const int px = x + dx, py = y + dy;"),
     "fallback max": ("if (left >= 0 && right >= 0) arg = std::min(left, right);",
                      "if (left >= 0 && right >= 0) arg = std::max(left, right);"),
 }
