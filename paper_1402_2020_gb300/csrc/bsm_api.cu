@@ -288,7 +288,8 @@ bsm_status bsm_set_tuning(bsm_ctx *ctx, const bsm_tuning *t) {
   if (ctx == nullptr || t == nullptr) return BSM_ERR_INVALID_ARG;
   for (int i = 0; i < 4; ++i)
     if (t->reserved[i] != 0) return BSM_ERR_INVALID_ARG;
-  if (t->cost_variant < 0 || t->cost_variant > 2) return BSM_ERR_INVALID_ARG;
+  if (t->cost_variant < 0 || t->cost_variant > 3) return BSM_ERR_INVALID_ARG;
+  if (t->cost_variant == 3 && !bsm::cost_tc_supported(ctx)) return BSM_ERR_UNSUPPORTED;
   if (t->cost_variant == 2 && ((ctx->nw != 4 && ctx->nw != 8) || ctx->p.mask_mode == BSM_MASK_BOTH))
     return BSM_ERR_UNSUPPORTED;
   if (t->cost_rows != 0 && (t->cost_rows < 8 || t->cost_rows > 512)) return BSM_ERR_INVALID_ARG;

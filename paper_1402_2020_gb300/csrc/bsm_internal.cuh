@@ -119,6 +119,10 @@ cudaError_t launch_cost_long(const bsm_ctx *ctx, const uint32_t *BL, const uint3
                              const uint32_t *PhiR, int w, int h, int dmax, int32_t *dL, int32_t *dR, uint16_t *costL, uint16_t *costR,
                              cudaStream_t s);
 bool cost2_supported(const bsm_ctx *ctx);
+bool cost_tc_supported(const bsm_ctx *ctx);
+cudaError_t launch_cost_tc(const bsm_ctx *ctx, const uint32_t *BL, const uint32_t *PhiL, const uint32_t *BR,
+                           const uint32_t *PhiR, int w, int h, int dmax, int32_t *dL, int32_t *dR, uint16_t *costL,
+                           uint16_t *costR, cudaStream_t s);
 cudaError_t launch_sgm(const uint16_t *C, int w, int h, int dmax, int P1, int P2, int paths, uint32_t *S,
                        int32_t *disp, cudaStream_t s);
 cudaError_t launch_cost2(const bsm_ctx *ctx, const uint32_t *BL, const uint32_t *PhiL, const uint32_t *BR,
