@@ -4,49 +4,67 @@
 // bits, popcount((B(x) XOR O) AND Phi(x)) = popcount(Phi(x) AND B(x)) + sum_i s_i(x) o_i exactly, so the
 // costs of 128 reference columns (TMEM lanes) against the band of other-view columns their
 // disparities reach (TMEM columns) are one product S O^T. The window's vertical sum is a running
-// accumulator: every input row adds [s(new row) | -s(old row)] . [o(new row) | o(old row)] (K = 2n)
-// with tcgen05.mma kind::f8f6f4, E4M3 operands +-2^-6 and 2^-6, fp32 accumulation in TMEM: every value
-// is an integer times 2^-12 below 2^11, so the products and sums are exact.
+// accumulator: every input row adds s(entering row) . o(entering row) and, with the A operand negated
+// by the instruction descriptor, subtracts s(leaving row) . o(leaving row); tcgen05.mma kind::f8f6f4,
+// E4M3 operands +-2^-6 and 2^-6, fp32 accumulation in TMEM: every value is an integer times 2^-12
+// below 2^11, so the products and sums are exact.
 //
-// Per input row (one CTA: 128 columns, a band of rows, one reference view):
-//   1. the K dimension is expanded from bits to E4M3 bytes in 64-byte chunks, double-buffered in the
-//      no-swizzle K-major canonical layout (8-row x 16-byte core matrices; rows 16 bytes apart, K
-//      groups of 16 bytes one operand height apart): 128 threads build the A rows from the reference
-//      B / Phi words, 384 threads the B rows from the other view's words (read through L1, which
-//      keeps each pixel's 32 bytes for the row's four chunks); after each chunk one thread issues its
-//      MMAs (2 k-steps x up to 2 N-blocks) and commits them to the chunk buffer's mbarrier;
-//   2. once the row's MMAs are done, every warp reads its lane quadrant of the accumulator
-//      (tcgen05.ld 32x32b.x32) and writes term(x, d) = V(x, x_d) + the window's popcount(Phi AND B)
-//      of column x (or the out-of-image sentinel n per in-image row) into a shared [x][d] table with
-//      one fused multiply-add and one store per value;
-//   3. one warp per run of 8 output columns, 8 disparities per lane: the horizontal box sum slides
-//      along x on packed 16-bit pairs (128-bit table reads), (A << 3 | d % 8) keys reduce with
-//      min.u16x2, and one warp-wide unsigned minimum of (A << 8 | d) gives Eq. 1's smallest d.
-// Every wait is bounded; a wait that gives up latches BSM_ERR_TIMEOUT and the CTA stops.
+// 1. tc_expand_kernel writes, per view, the E4M3 plane S of the s bytes in a K-group-major layout
+//    [y][16 groups of 16 K bytes][x][16 bytes], and popcount(Phi AND B) per pixel. The K order within a
+//    32-bit word is a fixed permutation of its bits (byte k of output word q is bit 8k + q), the same
+//    for both operands.
+// 2. cost_tc_kernel, one CTA per (128 reference columns, band of rows, reference view), 18 warps:
+//    - warp 0 (producer) loads, by TMA, the other view's descriptor words of the entering and the
+//      leaving row (32 bytes per band column) and, per 64-byte K chunk, the A operand (4 groups x 128
+//      columns of S); the tensor maps fill columns outside the image with zeros;
+//    - warps 2..5 build each chunk's B operand (4 groups x up to 384 band columns of o bytes, 2^-6
+//      where the bit is set) from those words in shared memory;
+//    - warp 1 owns the TMEM accumulator and issues the MMAs (2 k-steps x 2 N-blocks per chunk), commits
+//      each chunk to its buffer's "empty" barrier and each finished output row to "acc_full"; before the
+//      next row's MMAs it waits until the epilogue has read the accumulator;
+//    - warps 6..17 (epilogue) read their lane quadrant of the accumulator (tcgen05.ld 32x32b.x32) and
+//      write term(x, d) = V(x, x_d) + the window's popcount(Phi AND B) of column x (or the sentinel n
+//      per in-image row when the match leaves the image) into a shared [x][d] table, release the
+//      accumulator, then slide the horizontal box sum along x on packed 16-bit pairs and reduce
+//      (A << 3 | d % 8) keys with min.u16x2 and one warp-wide minimum of (A << 8 | d): Eq. 1's
+//      smallest d. This pass overlaps the next row's MMAs.
+// Every wait is bounded; a wait that gives up latches BSM_ERR_TIMEOUT and the CTA winds down.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include "bsm_internal.cuh"
 
 namespace bsm {
 namespace {
 
-constexpr int kTM = 128;         // reference columns per CTA: MMA M, TMEM lanes
-constexpr int kNB = 384;         // rows of the B operand buffer: the band of 128 + 256 - 1 other columns
-constexpr int kChunk = 64;       // K bytes per operand chunk (= descriptor bits)
-constexpr int kThreads = 512;    // 128 threads build A rows, 384 build B rows
-constexpr int kTP = 264;         // u16 pitch of the term table T[x][d] (rows 16-byte aligned)
-constexpr int kAB = kTM * kChunk;        // A chunk bytes
-constexpr int kBB = kNB * kChunk;        // B chunk bytes
-constexpr int kOpB = kAB + kBB;          // one operand buffer
+constexpr int kTM = 128;          // reference columns per CTA: MMA M, TMEM lanes
+constexpr int kNB = 384;          // B operand rows: the band of 128 + 256 - 1 other-view columns
+constexpr int kChunk = 64;        // K bytes per operand chunk: 4 K groups of 16 bytes (2 descriptor words)
+constexpr int kBuf = 3;           // operand buffers
+constexpr int kWarps = 18;        // producer, MMA, 4 B-operand builders, 12 epilogue warps
+constexpr int kThreads = 32 * kWarps;
+constexpr int kXpd = 4 * 32;      // B-operand builder threads (warps 2..5)
+constexpr int kEpi = 12 * 32;     // epilogue threads (warps 6..17)
+constexpr int kTP = 264;          // u16 pitch of the term table T[x][d] (rows 16-byte aligned)
+constexpr int kAB = kTM * kChunk;         // A chunk: 4 groups x 128 rows x 16 bytes
+constexpr int kBB = kNB * kChunk;         // B chunk: 4 groups x 384 rows x 16 bytes
+constexpr int kOpB = kAB + kBB;           // one operand buffer (32 KB)
+constexpr int kRawRow = kNB * 32;         // other-view words of one row of the band (8 words per column)
 constexpr int kOffOp = 0;
-constexpr int kOffT = kOffOp + 2 * kOpB;
+constexpr int kOffRaw = kOffOp + kBuf * kOpB;          // 2 slots x (entering, leaving) rows
+constexpr int kOffT = kOffRaw + 2 * 2 * kRawRow;
 constexpr int kOffC0 = kOffT + kTM * kTP * 2;
 constexpr int kOffMisc = kOffC0 + kTM * 4;
-constexpr int kSmem = kOffMisc + 64;
+constexpr int kSmem = kOffMisc + 128;
 static_assert(kSmem <= 232448, "shared memory of one CTA");
-static_assert(kOffT % 16 == 0 && kOffMisc % 16 == 0 && (kTP * 2) % 16 == 0, "alignment");
+static_assert(kOffRaw % 1024 == 0 && kOffT % 1024 == 0 && kOffMisc % 16 == 0 && (kTP * 2) % 16 == 0, "alignment");
 constexpr long long kWait = 1LL << 31;  // about one second at the GB300 clock
 
 struct TcArgs {
-  const uint32_t *B[2], *Phi[2], *O[2];
+  CUtensorMap smap[2];    // S planes (A operand), box 16 bytes x 128 columns x 4 groups; per reference view
+  CUtensorMap bmap0[2];   // descriptor plane of the other view, box 32 bytes x 256 columns x 1 row
+  CUtensorMap bmap1[2];   // the same, box 32 bytes x 128 columns x 1 row
+  const uint16_t *c0[2];  // popcount(Phi AND B) per pixel of the reference view
   int32_t *disp[2];
   uint16_t *cost[2];
   uint32_t *status;
@@ -54,10 +72,6 @@ struct TcArgs {
 };
 
 __device__ __forceinline__ uint32_t saddr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(saddr(dst)), "l"(src) : "memory");
-}
 
 __device__ __forceinline__ bool mbar_try(uint64_t *bar, uint32_t parity) {
   uint32_t ok;
@@ -74,6 +88,38 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
   return true;
 }
 
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(saddr(bar)), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(saddr(bar)) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(saddr(bar)), "r"(bytes) : "memory");
+}
+
+// 3-D tile copy (16 bytes x columns x K groups) of an operand plane into shared memory.
+__device__ __forceinline__ void tma_load3(void *dst, const CUtensorMap *map, int x, int row, uint64_t *bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
+      ::"r"(saddr(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(0), "r"(x), "r"(row), "r"(saddr(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void epi_sync() {  // named barrier of the epilogue warps
+  asm volatile("bar.sync 1, %0;" ::"r"(kEpi) : "memory");
+}
+
+// The same barrier, returning whether every epilogue thread passed `ok`.
+__device__ __forceinline__ bool epi_sync_and(bool ok) {
+  uint32_t r;
+  asm volatile("{\n.reg .pred p, q;\nsetp.ne.u32 q, %1, 0;\nbarrier.cta.red.and.pred p, 1, %2, q;\nselp.u32 %0, 1, 0, p;\n}"
+               : "=r"(r) : "r"((uint32_t)ok), "r"(kEpi) : "memory");
+  return r != 0;
+}
+
 // Shared-memory matrix descriptor: no swizzle, K-major; lbo = bytes between K groups of 16 bytes,
 // sbo = bytes between 8-row groups.
 __device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
@@ -81,14 +127,20 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint3
          ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | (1ull << 46);
 }
 
-// Instruction descriptor of kind::f8f6f4: E4M3 x E4M3 -> F32, both K-major, M = 128, N = n.
-__device__ __forceinline__ uint32_t instr_desc(int n) {
-  return (1u << 4) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(kTM >> 4) << 24);
+// Instruction descriptor of kind::f8f6f4: E4M3 x E4M3 -> F32, both K-major, M = 128, N = n; bit 13
+// negates A.
+__device__ __forceinline__ uint32_t instr_desc(int n, bool neg_a) {
+  return (1u << 4) | (neg_a ? (1u << 13) : 0u) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(kTM >> 4) << 24);
 }
 
 __device__ __forceinline__ void mma_f8(uint32_t tmem, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t acc) {
   asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\ntcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}"
                ::"r"(tmem), "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t *bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(saddr(bar))
+               : "memory");
 }
 
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
@@ -103,8 +155,13 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-// Byte k (k = 0..3) of output word q takes bit 8k + q of w, placed at bit `pos` of the byte: the
-// expansion's K order is a fixed permutation of the descriptor bits, the same for both operands.
+__device__ __forceinline__ uint32_t vmin_u16x2(uint32_t a, uint32_t b) {
+  uint32_t r;
+  asm("min.u16x2 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(b));
+  return r;
+}
+
+// Byte k (k = 0..3) of output word q takes bit 8k + q of w, placed at bit `pos` of the byte.
 template <int Q, int POS>
 __device__ __forceinline__ uint32_t spread(uint32_t w) {
   constexpr int sh = POS - Q;
@@ -113,21 +170,37 @@ __device__ __forceinline__ uint32_t spread(uint32_t w) {
   else return (w >> (-sh)) & mask;
 }
 
-// 32 K bytes of the A operand from one reference word pair: +-2^-6 (0x08 / 0x88) where the mask bit
-// is set, the sign from the descriptor bit (negated for the row that leaves the window).
-__device__ __forceinline__ void expand_a(uint32_t b, uint32_t m, bool neg, uint8_t *dst_g0, uint8_t *dst_g1) {
-  const uint32_t sb = m & (neg ? ~b : b);
-  uint32_t o[8];
-  o[0] = spread<0, 3>(m) | spread<0, 7>(sb);
-  o[1] = spread<1, 3>(m) | spread<1, 7>(sb);
-  o[2] = spread<2, 3>(m) | spread<2, 7>(sb);
-  o[3] = spread<3, 3>(m) | spread<3, 7>(sb);
-  o[4] = spread<4, 3>(m) | spread<4, 7>(sb);
-  o[5] = spread<5, 3>(m) | spread<5, 7>(sb);
-  o[6] = spread<6, 3>(m) | spread<6, 7>(sb);
-  o[7] = spread<7, 3>(m) | spread<7, 7>(sb);
-  *reinterpret_cast<uint4 *>(dst_g0) = make_uint4(o[0], o[1], o[2], o[3]);
-  *reinterpret_cast<uint4 *>(dst_g1) = make_uint4(o[4], o[5], o[6], o[7]);
+// ---------------------------------------------------------------- operand planes
+
+// One thread per pixel: S bytes of the 16 K groups (2 per descriptor word) and popcount(Phi AND B).
+// s = +-2^-6 (0x08 / 0x88) where the mask bit is set, signed by the descriptor bit.
+__global__ void __launch_bounds__(128) tc_expand_kernel(const uint32_t *__restrict__ B0, const uint32_t *__restrict__ P0,
+                                                        const uint32_t *__restrict__ B1, const uint32_t *__restrict__ P1,
+                                                        uint4 *S0, uint16_t *c00, uint4 *S1, uint16_t *c01, int w, int h) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y, v = blockIdx.z;
+  if (x >= w) return;
+  const uint32_t *Bp = v ? B1 : B0, *Pp = v ? P1 : P0;
+  uint4 *S = v ? S1 : S0;
+  uint16_t *c0 = v ? c01 : c00;
+  const size_t pix = (size_t)y * w + x;
+  const uint4 b01 = __ldg(reinterpret_cast<const uint4 *>(Bp + pix * 8));
+  const uint4 b23 = __ldg(reinterpret_cast<const uint4 *>(Bp + pix * 8 + 4));
+  const uint4 m01 = __ldg(reinterpret_cast<const uint4 *>(Pp + pix * 8));
+  const uint4 m23 = __ldg(reinterpret_cast<const uint4 *>(Pp + pix * 8 + 4));
+  const uint32_t bw[8] = {b01.x, b01.y, b01.z, b01.w, b23.x, b23.y, b23.z, b23.w};
+  const uint32_t mw[8] = {m01.x, m01.y, m01.z, m01.w, m23.x, m23.y, m23.z, m23.w};
+  int pc = 0;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const uint32_t m = mw[j], sb = m & bw[j];
+    pc += __popc(sb);
+    const size_t g0 = ((size_t)y * 16 + 2 * j) * w + x, g1 = g0 + w;  // K groups 2j, 2j + 1
+    S[g0] = make_uint4(spread<0, 3>(m) | spread<0, 7>(sb), spread<1, 3>(m) | spread<1, 7>(sb),
+                       spread<2, 3>(m) | spread<2, 7>(sb), spread<3, 3>(m) | spread<3, 7>(sb));
+    S[g1] = make_uint4(spread<4, 3>(m) | spread<4, 7>(sb), spread<5, 3>(m) | spread<5, 7>(sb),
+                       spread<6, 3>(m) | spread<6, 7>(sb), spread<7, 3>(m) | spread<7, 7>(sb));
+  }
+  c0[pix] = (uint16_t)pc;
 }
 
 // 32 K bytes of the B operand from one other-view word: 2^-6 (0x08) where the bit is set.
@@ -138,20 +211,15 @@ __device__ __forceinline__ void expand_b(uint32_t o, uint8_t *dst_g0, uint8_t *d
       make_uint4(spread<4, 3>(o), spread<5, 3>(o), spread<6, 3>(o), spread<7, 3>(o));
 }
 
-__device__ __forceinline__ uint32_t vmin_u16x2(uint32_t a, uint32_t b) {
-  uint32_t r;
-  asm("min.u16x2 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(b));
-  return r;
-}
+// ---------------------------------------------------------------- cost kernel
 
 template <int WIN, int DIR>
 __device__ __forceinline__ void cost_tc_body(const TcArgs &a, uint8_t *smem) {
   constexpr int R = WIN / 2, OUTC = kTM - 2 * R;
   constexpr bool PK = 256 * WIN * WIN < 8192;  // aggregated costs below 2^13: 16-bit (A << 3 | dd) keys
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const uint32_t *__restrict__ Bref = DIR ? a.B[1] : a.B[0];
-  const uint32_t *__restrict__ Phiref = DIR ? a.Phi[1] : a.Phi[0];
-  const uint32_t *__restrict__ Both = DIR ? a.O[1] : a.O[0];
+  const CUtensorMap *smap = &a.smap[DIR], *bmap0 = &a.bmap0[DIR], *bmap1 = &a.bmap1[DIR];
+  const uint16_t *__restrict__ c0p = DIR ? a.c0[1] : a.c0[0];
   int32_t *__restrict__ disp = DIR ? a.disp[1] : a.disp[0];
   uint16_t *cost = DIR ? a.cost[1] : a.cost[0];
   const int w = a.w, h = a.h, dmax = a.dmax;
@@ -166,18 +234,30 @@ __device__ __forceinline__ void cost_tc_body(const TcArgs &a, uint8_t *smem) {
   // every column of the tile is in the image and every match of it lies inside the other view
   const bool fast = X0 >= 0 && X0 + kTM <= w && (DIR == 0 ? X0 >= D - 1 : X0 + kTM - 1 + D - 1 < w);
 
-  uint64_t *mbar = reinterpret_cast<uint64_t *>(smem + kOffMisc);
-  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + kOffMisc + 16);
+  uint64_t *full = reinterpret_cast<uint64_t *>(smem + kOffMisc);  // [kBuf]
+  uint64_t *empty = full + kBuf;                                    // [kBuf]
+  uint64_t *raw_full = empty + kBuf, *raw_empty = raw_full + 2;     // [2] each
+  uint64_t *acc_full = raw_empty + 2, *acc_empty = acc_full + 1;
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(acc_empty + 1);
+  uint32_t *abort_flag = tmem_slot + 1;
   uint16_t *T = reinterpret_cast<uint16_t *>(smem + kOffT);
   int32_t *c0v = reinterpret_cast<int32_t *>(smem + kOffC0);
 
   if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(&mbar[0])));
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(&mbar[1])));
+    for (int b = 0; b < kBuf; ++b) {
+      mbar_init(&full[b], 1 + kXpd / 32);  // the A copy's arrival and every builder warp
+      mbar_init(&empty[b], 1);
+    }
+    for (int k = 0; k < 2; ++k) {
+      mbar_init(&raw_full[k], 1);
+      mbar_init(&raw_empty[k], kXpd / 32);
+    }
+    mbar_init(acc_full, 1);
+    mbar_init(acc_empty, kEpi / 32);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (tid < kTM) c0v[tid] = 0;
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-  if (warp == 0) {
+  if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(saddr(tmem_slot)),
                  "r"(ncols));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
@@ -187,131 +267,188 @@ __device__ __forceinline__ void cost_tc_body(const TcArgs &a, uint8_t *smem) {
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *tmem_slot;
 
-  // this thread's operand row: A row `arow` (tid < 128) or B row `brow`
-  const bool is_a = tid < kTM;
-  const int arow = tid, brow = tid - kTM;
-  const int xa = X0 + arow, xo = xb0 + brow;
-  const bool row_ok = is_a ? (xa >= 0 && xa < w) : (brow < ntot && xo >= 0 && xo < w);
-  const size_t pix_col = is_a ? (size_t)xa : (size_t)xo;
+  auto row_new = [&](int i) { const int y = y_first + i; return y >= 0 && y < h; };
+  auto row_old = [&](int i) { const int y = y_first + i - (2 * R + 1); return i >= 2 * R + 1 && y >= 0 && y < h; };
 
-  uint32_t uses0 = 0, uses1 = 0;  // commits made to each operand buffer's mbarrier (uniform)
-  int last_buf = -1;              // buffer of the newest commit not yet waited for
-  bool acc_init = false, ok = true;
-  uint32_t nchunk = 0;
-
-  for (int i = 0; i < n_it && ok; ++i) {
-    const int yn = y_first + i, yold = yn - (2 * R + 1), yout = yn - R;
-    const bool has_new = yn >= 0 && yn < h, has_old = i >= 2 * R + 1 && yold >= 0 && yold < h;
-    int c0acc = 0;
-    for (int c = 0; c < 8; ++c) {
-      const bool is_new = c < 4;
-      if (!(is_new ? has_new : has_old)) continue;
-      const int j0 = 2 * (c & 3);
-      // this chunk's two words of the thread's pixel (an L1 hit after the row's first chunk)
-      uint2 bw = make_uint2(0u, 0u), mw = make_uint2(0u, 0u);
-      if (row_ok) {
-        const size_t off = ((size_t)(is_new ? yn : yold) * w + pix_col) * 8 + j0;
-        if (is_a) {
-          bw = __ldg(reinterpret_cast<const uint2 *>(Bref + off));
-          mw = __ldg(reinterpret_cast<const uint2 *>(Phiref + off));
+  if (warp == 0) {
+    // ---- producer: per input row the other view's words, per chunk the A operand, in order
+    if (lane == 0) {
+      uint32_t slot = 0;
+      const uint32_t rowbytes = (uint32_t)(256 * 32 + (nb1 > 0 ? 128 * 32 : 0));
+      bool ok = true;
+      for (int i = 0; i < n_it && ok; ++i) {
+        const int rs = i & 1;
+        if (i >= 2) ok = mbar_wait(&raw_empty[rs], ((i >> 1) - 1) & 1u);
+        if (!ok) break;
+        const bool hn = row_new(i), ho = row_old(i);
+        uint8_t *raw = smem + kOffRaw + rs * 2 * kRawRow;
+        if (hn || ho) {
+          mbar_expect_tx(&raw_full[rs], (hn ? rowbytes : 0u) + (ho ? rowbytes : 0u));
+          for (int k = 0; k < 2; ++k) {
+            if (!(k == 0 ? hn : ho)) continue;
+            const int y = k == 0 ? y_first + i : y_first + i - (2 * R + 1);
+            tma_load3(raw + k * kRawRow, bmap0, xb0, y, &raw_full[rs]);
+            if (nb1 > 0) tma_load3(raw + k * kRawRow + 256 * 32, bmap1, xb0 + 256, y, &raw_full[rs]);
+          }
         } else {
-          bw = __ldg(reinterpret_cast<const uint2 *>(Both + off));
+          mbar_arrive(&raw_full[rs]);
+        }
+        for (int c = 0; c < 8 && ok; ++c) {
+          const bool is_new = c < 4;
+          if (!(is_new ? hn : ho)) continue;
+          const int y = is_new ? y_first + i : y_first + i - (2 * R + 1);
+          const int b = (int)(slot % kBuf);
+          if (slot >= kBuf) ok = mbar_wait(&empty[b], ((slot / kBuf) - 1) & 1u);
+          if (!ok) break;
+          mbar_expect_tx(&full[b], (uint32_t)kAB);
+          tma_load3(smem + kOffOp + b * kOpB, smap, X0, y * 16 + 4 * (c & 3), &full[b]);
+          ++slot;
         }
       }
-      const int bb = (int)(nchunk & 1u);
-      const uint32_t ub = bb ? uses1 : uses0;
-      if (ub > 0) ok = mbar_wait(&mbar[bb], (ub - 1) & 1u);  // the MMAs two chunks back
-      ok = __syncthreads_and(ok) != 0;
-      if (!ok) break;
-      uint8_t *opA = smem + kOffOp + bb * kOpB, *opB = opA + kAB;
-      if (is_a) {
-        expand_a(bw.x, mw.x, !is_new, opA + 0 * (kTM * 16) + arow * 16, opA + 1 * (kTM * 16) + arow * 16);
-        expand_a(bw.y, mw.y, !is_new, opA + 2 * (kTM * 16) + arow * 16, opA + 3 * (kTM * 16) + arow * 16);
-        const int pc = __popc(bw.x & mw.x) + __popc(bw.y & mw.y);
-        c0acc += is_new ? pc : -pc;
-      } else if (brow < ntot) {
-        expand_b(bw.x, opB + 0 * (kNB * 16) + brow * 16, opB + 1 * (kNB * 16) + brow * 16);
-        expand_b(bw.y, opB + 2 * (kNB * 16) + brow * 16, opB + 3 * (kNB * 16) + brow * 16);
-      }
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      __syncthreads();
-      if (tid == 0) {
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      if (!ok) atomicExch(abort_flag, 1u);
+      if (!ok && slot > 0) mbar_wait(&full[(slot - 1) % kBuf], ((slot - 1) / kBuf) & 1u);  // let copies land
+    }
+  } else if (warp == 1) {
+    // ---- MMA issuer
+    if (lane == 0) {
+      uint32_t slot = 0, outs = 0;
+      bool ok = true, acc_init = false, pending = false;
+      for (int i = 0; i < n_it && ok; ++i) {
+        if (pending) {  // the epilogue has read the previous output row's accumulator
+          ok = mbar_wait(acc_empty, (outs - 1) & 1u);
+          pending = false;
+          if (!ok) break;
+        }
+        for (int c = 0; c < 8 && ok; ++c) {
+          const bool is_new = c < 4;
+          if (!(is_new ? row_new(i) : row_old(i))) continue;
+          const int b = (int)(slot % kBuf);
+          ok = mbar_wait(&full[b], (slot / kBuf) & 1u);
+          if (!ok) break;
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint32_t op = saddr(smem + kOffOp + b * kOpB);
 #pragma unroll
-        for (int ks = 0; ks < 2; ++ks) {
-          const uint64_t ad = smem_desc(saddr(opA) + ks * 2 * (kTM * 16), kTM * 16, 128);
-          const uint32_t acc = (acc_init || ks > 0) ? 1u : 0u;
-          mma_f8(tmem, ad, smem_desc(saddr(opB) + ks * 2 * (kNB * 16), kNB * 16, 128), instr_desc(nb0), acc);
-          if (nb1 > 0)
-            mma_f8(tmem + 256, ad, smem_desc(saddr(opB) + ks * 2 * (kNB * 16) + 256 * 16, kNB * 16, 128),
-                   instr_desc(nb1), acc);
+          for (int ks = 0; ks < 2; ++ks) {
+            const uint64_t ad = smem_desc(op + ks * 2 * (kTM * 16), kTM * 16, 128);
+            const uint32_t acc = (acc_init || ks > 0) ? 1u : 0u;
+            mma_f8(tmem, ad, smem_desc(op + kAB + ks * 2 * (kNB * 16), kNB * 16, 128), instr_desc(nb0, !is_new), acc);
+            if (nb1 > 0)
+              mma_f8(tmem + 256, ad, smem_desc(op + kAB + ks * 2 * (kNB * 16) + 256 * 16, kNB * 16, 128),
+                     instr_desc(nb1, !is_new), acc);
+          }
+          mma_commit(&empty[b]);
+          acc_init = true;
+          ++slot;
         }
-        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                         saddr(&mbar[bb]))
-                     : "memory");
+        if (ok && y_first + i - R >= yb) {  // an output row: hand the accumulator to the epilogue
+          mma_commit(acc_full);
+          ++outs;
+          pending = true;
+        }
       }
-      acc_init = true;
-      if (bb) ++uses1;
-      else ++uses0;
-      last_buf = bb;
-      ++nchunk;
+      if (!ok) atomicExch(abort_flag, 1u);
     }
-    if (!ok) break;
-    if (is_a) c0v[arow] += c0acc;  // the window's popcount(Phi AND B) per reference column
-    if (yout < yb) {
-      __syncthreads();
-      continue;  // the window is not full yet
+  } else if (warp < 2 + kXpd / 32) {
+    // ---- B-operand builders: band column r, r + 128, r + 256 of each chunk
+    const int t = tid - 64;
+    uint32_t slot = 0;
+    bool ok = true;
+    for (int i = 0; i < n_it && ok; ++i) {
+      const int rs = i & 1;
+      const bool hn = row_new(i), ho = row_old(i);
+      ok = mbar_wait(&raw_full[rs], (i >> 1) & 1u);
+      if (!ok) break;
+      const uint8_t *raw = smem + kOffRaw + rs * 2 * kRawRow;
+      for (int c = 0; c < 8 && ok; ++c) {
+        const bool is_new = c < 4;
+        if (!(is_new ? hn : ho)) continue;
+        const int b = (int)(slot % kBuf);
+        if (slot >= kBuf) ok = mbar_wait(&empty[b], ((slot / kBuf) - 1) & 1u);
+        if (!ok) break;
+        const uint32_t *rw = reinterpret_cast<const uint32_t *>(raw + (is_new ? 0 : kRawRow));
+        uint8_t *opB = smem + kOffOp + b * kOpB + kAB;
+        const int w0 = 2 * (c & 3);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          const int r = t + 128 * k;
+          if (r < ntot) {
+            const uint2 ow = *reinterpret_cast<const uint2 *>(rw + r * 8 + w0);
+            expand_b(ow.x, opB + 0 * (kNB * 16) + r * 16, opB + 1 * (kNB * 16) + r * 16);
+            expand_b(ow.y, opB + 2 * (kNB * 16) + r * 16, opB + 3 * (kNB * 16) + r * 16);
+          }
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&full[b]);
+        ++slot;
+      }
+      __syncwarp();
+      if (lane == 0 && ok) mbar_arrive(&raw_empty[rs]);  // this row's words are no longer needed
     }
-
-    // ---- the accumulator holds V(x, x_d) for output row yout
-    if (last_buf >= 0) {
-      ok = mbar_wait(&mbar[last_buf], ((last_buf ? uses1 : uses0) - 1) & 1u);
-      last_buf = -1;
-    }
-    ok = __syncthreads_and(ok) != 0;  // also publishes c0v
-    if (!ok) break;
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    {
+    if (!ok) atomicExch(abort_flag, 1u);
+  } else {
+    // ---- epilogue: warps 6..17; lane quadrant q = warp % 4, g = its index among the quadrant's warps
+    const int q = warp & 3, g = (warp - 6) >> 2, ew = warp - 6, r = 32 * q + lane, xr = X0 + r;
+    const bool col_in = xr >= 0 && xr < w;
+    int c0run = 0;  // warps with g == 0: the window's popcount(Phi AND B) of column r
+    uint32_t outs = 0;
+    bool ok = true;
+    for (int i = 0; i < n_it && ok; ++i) {
+      const int yn = y_first + i, yold = yn - (2 * R + 1), yout = yn - R;
+      if (g == 0 && col_in) {
+        if (row_new(i)) c0run += c0p[(size_t)yn * w + xr];
+        if (row_old(i)) c0run -= c0p[(size_t)yold * w + xr];
+      }
+      if (yout < yb) continue;
+      if (g == 0) c0v[r] = c0run;
+      ok = mbar_wait(acc_full, outs & 1u);
+      if (*reinterpret_cast<volatile uint32_t *>(abort_flag) != 0) ok = false;  // the other roles gave up
+      ++outs;
+      // c0v published; the previous row's horizontal pass is done with T; all agree on ok
+      ok = epi_sync_and(ok);
+      if (!ok) break;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       int nh = 0;
 #pragma unroll
       for (int v = -R; v <= R; ++v) nh += (yout + v >= 0 && yout + v < h) ? 1 : 0;
-      const int q = warp & 3, g = warp >> 2, r = 32 * q + lane, xr = X0 + r;
-      const float base = (float)c0v[r] + 12582912.0f;  // 1.5 * 2^23: the sum's integer sits in the low bits
-      uint16_t *Trow = T + r * kTP;
-      const int nck = D / 32 + 1;
-      for (int k = g; k < nck; k += 4) {
-        uint32_t v[32];
-        tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(32 * q + 32 * k), v);
-        // band column 32 q + 32 k + t is disparity d = DIR ? rel : D - 1 - rel, rel = 32 k + t - lane
-        if (fast && k > 0 && k < nck - 1) {
-          uint16_t *p0 = DIR == 0 ? Trow + (D - 1 - 32 * k + lane) : Trow + (32 * k - lane);
+      {
+        const float base = (float)c0v[r] + 12582912.0f;  // 1.5 * 2^23: the sum's integer in the low bits
+        uint16_t *Trow = T + r * kTP;
+        const int nck = D / 32 + 1;
+        for (int k = g; k < nck; k += 3) {
+          uint32_t v[32];
+          tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(32 * q + 32 * k), v);
+          // band column 32 q + 32 k + t is disparity d = DIR ? rel : D - 1 - rel, rel = 32 k + t - lane
+          if (fast && k > 0 && k < nck - 1) {
+            uint16_t *p0 = DIR == 0 ? Trow + (D - 1 - 32 * k + lane) : Trow + (32 * k - lane);
 #pragma unroll
-          for (int t = 0; t < 32; ++t) {
-            const uint32_t val = __float_as_uint(fmaf(__uint_as_float(v[t]), 4096.0f, base));
-            if (DIR == 0) p0[-t] = (uint16_t)val;
-            else p0[t] = (uint16_t)val;
-          }
-        } else {
-          const bool col_in = xr >= 0 && xr < w;
-          const uint32_t sentinel = (uint32_t)nh * 256u;
+            for (int t = 0; t < 32; ++t) {
+              const uint32_t val = __float_as_uint(fmaf(__uint_as_float(v[t]), 4096.0f, base));
+              if (DIR == 0) p0[-t] = (uint16_t)val;
+              else p0[t] = (uint16_t)val;
+            }
+          } else {
+            const uint32_t sentinel = (uint32_t)nh * 256u;
 #pragma unroll
-          for (int t = 0; t < 32; ++t) {
-            const int rel = 32 * k + t - lane;
-            if (rel < 0 || rel >= D) continue;
-            const int d = DIR == 0 ? D - 1 - rel : rel;
-            uint32_t val = __float_as_uint(fmaf(__uint_as_float(v[t]), 4096.0f, base));
-            const bool match_in = DIR == 0 ? xr - d >= 0 : xr + d < w;
-            if (!match_in) val = sentinel;
-            Trow[d] = (uint16_t)(col_in ? val : 0u);
+            for (int t = 0; t < 32; ++t) {
+              const int rel = 32 * k + t - lane;
+              if (rel < 0 || rel >= D) continue;
+              const int d = DIR == 0 ? D - 1 - rel : rel;
+              uint32_t val = __float_as_uint(fmaf(__uint_as_float(v[t]), 4096.0f, base));
+              const bool match_in = DIR == 0 ? xr - d >= 0 : xr + d < w;
+              if (!match_in) val = sentinel;
+              Trow[d] = (uint16_t)(col_in ? val : 0u);
+            }
           }
         }
       }
-    }
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();  // T complete; the accumulator may be overwritten by the next row's MMAs
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mbar_arrive(acc_empty);  // this warp is done with the accumulator
+      epi_sync();                              // T complete
 
-    {  // warp: output columns rr0 .. rr1 - 1; lane: disparities 8 lane .. 8 lane + 7
-      const int rr0 = R + 8 * warp, rr1 = min(rr0 + 8, kTM - R);
+      // horizontal box sum + Eq. 1: warp ew takes output columns rr0 .. rr1 - 1, lane 8 disparities
+      const int rr0 = R + 11 * ew, rr1 = min(rr0 + 11, kTM - R);
       const int d8 = 8 * lane;
       if (rr0 < rr1) {
         const bool lane_on = d8 < D;
@@ -323,8 +460,7 @@ __device__ __forceinline__ void cost_tc_body(const TcArgs &a, uint8_t *smem) {
             s4[0] += t4.x; s4[1] += t4.y; s4[2] += t4.z; s4[3] += t4.w;
           }
         }
-        // halves holding a disparity at or above dmax never win
-        uint32_t inval[4];
+        uint32_t inval[4];  // halves holding a disparity at or above dmax never win
 #pragma unroll
         for (int j = 0; j < 4; ++j)
           inval[j] = (d8 + 2 * j < dmax ? 0u : 0xFFFFu) | (d8 + 2 * j + 1 < dmax ? 0u : 0xFFFF0000u);
@@ -366,18 +502,16 @@ __device__ __forceinline__ void cost_tc_body(const TcArgs &a, uint8_t *smem) {
         }
       }
     }
-    __syncthreads();  // every warp is done with T
+    if (!ok && tid == 6 * 32) atomicCAS(a.status, 0u, (uint32_t)BSM_ERR_TIMEOUT);
   }
-
-  if (!ok && tid == 0) atomicCAS(a.status, 0u, (uint32_t)BSM_ERR_TIMEOUT);
-  if (ok && last_buf >= 0) ok = mbar_wait(&mbar[last_buf], ((last_buf ? uses1 : uses0) - 1) & 1u);  // in flight
+  if (tid == 0 && *abort_flag != 0) atomicCAS(a.status, 0u, (uint32_t)BSM_ERR_TIMEOUT);
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
-  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols));
+  if (warp == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols));
 }
 
 template <int WIN>
-__global__ void __launch_bounds__(kThreads, 1) cost_tc_kernel(const TcArgs a) {
+__global__ void __launch_bounds__(kThreads, 1) cost_tc_kernel(const __grid_constant__ TcArgs a) {
   extern __shared__ __align__(1024) uint8_t smem[];
   if (blockIdx.z == 0) cost_tc_body<WIN, 0>(a, smem);
   else cost_tc_body<WIN, 1>(a, smem);
@@ -402,16 +536,79 @@ int pick_rows_tc(int w, int h, int win) {
   return (h + bands - 1) / bands;
 }
 
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (fn == nullptr) {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
+
+// Operand plane [h][16][w][16 bytes] as a 3-D byte tensor (16, w, 16 h); box 16 x cols x 4.
+bool plane_map(CUtensorMap *map, void *base, int w, int h, int cols) {
+  auto fn = encode_fn();
+  if (fn == nullptr) return false;
+  const cuuint64_t dims[3] = {16, (cuuint64_t)w, (cuuint64_t)16 * h};
+  const cuuint64_t strides[2] = {16, (cuuint64_t)16 * w};
+  const cuuint32_t box[3] = {16, (cuuint32_t)cols, 4};
+  const cuuint32_t elem[3] = {1, 1, 1};
+  return fn(map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 3, base, dims, strides, box, elem, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// Descriptor plane [h][w][8 words] as a 3-D byte tensor (32, w, h); box 32 x cols x 1.
+bool desc_map(CUtensorMap *map, const void *base, int w, int h, int cols) {
+  auto fn = encode_fn();
+  if (fn == nullptr) return false;
+  const cuuint64_t dims[3] = {32, (cuuint64_t)w, (cuuint64_t)h};
+  const cuuint64_t strides[2] = {32, (cuuint64_t)32 * w};
+  const cuuint32_t box[3] = {32, (cuuint32_t)cols, 1};
+  const cuuint32_t elem[3] = {1, 1, 1};
+  return fn(map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 3, const_cast<void *>(base), dims, strides, box, elem,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+size_t round256(size_t b) { return (b + 255) & ~(size_t)255; }
+
 }  // namespace
 
 bool cost_tc_supported(const bsm_ctx *ctx) { return ctx->nw == 8 && ctx->p.mask_mode != BSM_MASK_BOTH; }
 
+// Scratch of one call: S planes of both views (256 bytes per pixel) and popcount planes.
+size_t cost_tc_scratch_bytes(int w, int h) {
+  const size_t px = (size_t)w * h;
+  return 2 * round256(px * 256) + 2 * round256(px * 2);
+}
+
 cudaError_t launch_cost_tc(const bsm_ctx *ctx, const uint32_t *BL, const uint32_t *PhiL, const uint32_t *BR,
                            const uint32_t *PhiR, int w, int h, int dmax, int32_t *dL, int32_t *dR, uint16_t *costL,
                            uint16_t *costR, cudaStream_t s) {
+  const size_t px = (size_t)w * h;
+  if (ctx->tc_ws == nullptr || ctx->tc_ws_bytes < cost_tc_scratch_bytes(w, h)) return cudaErrorInvalidValue;
+  uint8_t *base = static_cast<uint8_t *>(ctx->tc_ws);
+  uint8_t *SL = base, *SR = SL + round256(px * 256);
+  uint16_t *cL = reinterpret_cast<uint16_t *>(SR + round256(px * 256));
+  uint16_t *cR = reinterpret_cast<uint16_t *>(reinterpret_cast<uint8_t *>(cL) + round256(px * 2));
+  dim3 eg((w + 127) / 128, h, 2);
+  tc_expand_kernel<<<eg, 128, 0, s>>>(BL, PhiL, BR, PhiR, reinterpret_cast<uint4 *>(SL), cL,
+                                      reinterpret_cast<uint4 *>(SR), cR, w, h);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
   TcArgs a{};
-  a.B[0] = BL; a.Phi[0] = PhiL; a.O[0] = BR; a.disp[0] = dL; a.cost[0] = costL;
-  a.B[1] = BR; a.Phi[1] = PhiR; a.O[1] = BL; a.disp[1] = dR; a.cost[1] = costR;
+  // left reference: A = S of the left view, B from the right view's descriptors; right reference the other way
+  if (!plane_map(&a.smap[0], SL, w, h, 128) || !plane_map(&a.smap[1], SR, w, h, 128) ||
+      !desc_map(&a.bmap0[0], BR, w, h, 256) || !desc_map(&a.bmap0[1], BL, w, h, 256) ||
+      !desc_map(&a.bmap1[0], BR, w, h, 128) || !desc_map(&a.bmap1[1], BL, w, h, 128))
+    return cudaErrorInvalidValue;
+  a.c0[0] = cL; a.c0[1] = cR;
+  a.disp[0] = dL; a.disp[1] = dR;
+  a.cost[0] = costL; a.cost[1] = costR;
   a.status = ctx->status;
   a.w = w; a.h = h; a.dmax = dmax;
   a.rows = ctx->cost_rows > 0 ? ctx->cost_rows : pick_rows_tc(w, h, ctx->p.agg_window);
