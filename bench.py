@@ -447,11 +447,34 @@ def cost_kernel(tuning, nw, dmax):
     if nw > 8:
         return "cost_long_kernel", "bsm_long.cu", 1
     v = tuning["cost_variant"]
+    if v == 3:
+        return "cost_tc_kernel", "bsm_cost_tc.cu", 2  # + the E4M3 operand-plane pass
     if v == 2 or (v == 0 and nw in (4, 8)):
         need = (dmax + 7) // 8
         split = (need + min(16, need) - 1) // min(16, need) > 1
         return "cost2_kernel", "bsm_cost2.cu", 2 if split else 1  # + keep_disparity_bits after a split
     return "cost_wta_kernel", "bsm_cost.cu", 1
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def tensor_roofline(units, n_bits, seconds, traffic):
+    """Eq. 8 as a contraction: n multiply-adds per (x, d) and reference view, against the E4M3 dense
+    peak (the measured bf16 GEMM rate times the nominal fp8 / bf16 ratio of 2)."""
+    flops = 2 * units * 2 * n_bits
+    bf16 = measured_peaks().get("bf16_tflops")
+    peak, basis = (2 * bf16, "measured bf16 x 2 (nominal fp8/bf16)") if bf16 else (3800.0, "fallback 1.9 PF bf16 x 2")
+    achieved = flops / seconds / 1e12
+    return {"bound": "tensor", "kernel": "cost_tc_kernel", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak, "traffic": traffic, "work_per_launch": flops, "peak_basis": basis,
+            "note": "stage time including the E4M3 operand-plane pass; the MMAs also run the window's entering "
+                    "and leaving rows and the band around the disparity range"}
 
 
 def run_pair(args, cfg, world, rank, local, n_bits=N_BITS, window_S=WINDOW_S, sigma=None, agg=AGG, e2e=True,
@@ -561,10 +584,11 @@ def run_pair(args, cfg, world, rank, local, n_bits=N_BITS, window_S=WINDOW_S, si
         "bad_pixel_rate": bad,  # |d - d_gt| > 1 against the generator's ground truth, rank 0's pair
         # colour pre-pass + describe per view, the cost stage's kernels, refine
         "gpu_launches": (4 + klaunch + 1 + (2 * sgm[2] if sgm else 0)) * args.steps,
-        "roofline": {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": peak,
-                     "unit": "Gpopc/s", "frac": achieved / peak, "traffic": traffic,
-                     "work_per_launch": word_ops,
-                     "peak_basis": f"{SMS} SMs x {POPC_PER_CLK_SM} POPC/clk x {MAX_SM_MHZ} MHz"},
+        "roofline": ({"bound": "alu", "kernel": kname, "achieved": achieved, "peak": peak,
+                      "unit": "Gpopc/s", "frac": achieved / peak, "traffic": traffic,
+                      "work_per_launch": word_ops,
+                      "peak_basis": f"{SMS} SMs x {POPC_PER_CLK_SM} POPC/clk x {MAX_SM_MHZ} MHz"}
+                     if kname != "cost_tc_kernel" else tensor_roofline(units, n_bits, t_k2, traffic)),
         "clocks": clocks,
         "tuning": tuning,
     }

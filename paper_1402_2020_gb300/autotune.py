@@ -17,7 +17,7 @@ from . import bsm
 
 COST_ROWS = (16, 32, 64, 128, 256)
 POPC_FORMS = (0, 1, 2)
-VARIANTS = (1, 2)  # one or two columns per lane
+VARIANTS = (1, 2, 3)  # one or two columns per lane, tensor cores
 BATCH_ROWS = (32, 64, 128)
 
 
@@ -35,7 +35,7 @@ def bucket(v: int) -> int:
 
 
 def key(gpu: str, n_bits: int, win: int, w: int, h: int, dmax: int) -> str:
-    return f"{gpu}|n{n_bits}|win{win}|d{bucket(dmax)}|px{bucket(w * h)}|v3"
+    return f"{gpu}|n{n_bits}|win{win}|d{bucket(dmax)}|px{bucket(w * h)}|v4"
 
 
 def load() -> dict:
@@ -96,9 +96,16 @@ def tune_cost(ctx, n_bits: int, win: int, w: int, h: int, dmax: int, reps: int =
         planes = [torch.randint(-2 ** 31, 2 ** 31 - 1, (h, w, nw), dtype=torch.int32, device="cuda", generator=gen)
                   for _ in range(4)]
         forms = POPC_FORMS if nw == 8 else (0,)
-        variants = VARIANTS if nw in (4, 8) else (1,)
-        cands = [(r, p, v) for v in variants for r in COST_ROWS if r <= max(16, 2 * h) for p in forms
+        variants = VARIANTS if nw == 8 else ((1, 2) if nw == 4 else (1,))
+        if 3 in variants:  # the tensor-core kernel is refused for the both-masks ablation
+            try:
+                bsm.bsm_set_tuning(ctx, 0, 0, 0, 3)
+            except bsm.BsmError:
+                variants = tuple(v for v in variants if v != 3)
+        cands = [(r, p, v) for v in variants if v != 3 for r in COST_ROWS if r <= max(16, 2 * h) for p in forms
                  if not (v == 1 and p == 2)]
+        if 3 in variants:  # the tensor-core kernel: its own band heights, popcount form unused
+            cands += [(r, 0, 3) for r in (0, 16, 32, 64, 128) if r <= max(16, 2 * h)]
         best, timings = choose(cands, lambda c: _time_cost(ctx, planes, w, h, dmax, c[0], c[1], c[2], reps, torch))
         cache[k] = {"cost_rows": best[0], "cost_popc_plain": best[1], "cost_variant": best[2], "timings_ms": timings}
         if use_cache:

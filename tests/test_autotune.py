@@ -6,7 +6,7 @@ def test_bucket_and_key():
     assert [autotune.bucket(v) for v in (1, 2, 3, 64, 65, 1390 * 1110)] == [1, 2, 4, 64, 128, 2 ** 21]
     k1 = autotune.key("GB300", 256, 5, 1390, 1110, 256)
     k2 = autotune.key("GB300", 256, 5, 1400, 1100, 200)
-    assert k1 == k2 == "GB300|n256|win5|d256|px2097152|v3"
+    assert k1 == k2 == "GB300|n256|win5|d256|px2097152|v4"
     assert autotune.key("GB300", 256, 5, 3840, 2160, 256) != k1
 
 

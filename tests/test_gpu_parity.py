@@ -260,7 +260,8 @@ def test_autotuner_applies_a_candidate_and_bits_stay(B, orc):
     pairs = synth.pair_table(256, 31, seed=260)
     c = Ctx(B, pairs, agg_window=5, dmax=dmax)
     t = autotune.tune_cost(c.ctx, 256, 5, w, h, dmax, reps=1, use_cache=False)
-    assert t["cost_rows"] in autotune.COST_ROWS and t["cost_popc_plain"] in (0, 1)
+    assert t["cost_rows"] in autotune.COST_ROWS + (0,) and t["cost_popc_plain"] in (0, 1, 2)
+    assert t["cost_variant"] in autotune.VARIANTS
     assert B.bsm_get_tuning(c.ctx)["cost_rows"] == t["cost_rows"]
     l, r, _ = synth.stereo_pair(w, h, dmax, seed=261)
     BL, PL, _, _ = c.describe(l)
