@@ -58,6 +58,8 @@ def parse():
     ap.add_argument("--cost-popc-plain", type=int, default=0, help="1: plain popcount in the cost kernel")
     ap.add_argument("--batch-rows", type=int, default=0, help="rows per task of the batched cost kernel (0: 64)")
     ap.add_argument("--no-autotune", action="store_true", help="skip the launch-shape autotuner")
+    ap.add_argument("--cost-variant", type=int, default=0,
+                    help="cost kernel: 1 one column per lane, 2 two columns, 3 tensor cores (0: autotuned)")
     ap.add_argument("--n-bits", type=int, default=N_BITS, help="descriptor length n (32 ... 4096)")
     ap.add_argument("--sgm", default="", help="P1,P2,paths: semi-global aggregation of both cost volumes")
     ap.add_argument("--quality", action="store_true",
@@ -493,8 +495,8 @@ def run_pair(args, cfg, world, rank, local, n_bits=N_BITS, window_S=WINDOW_S, si
                              vote_radius=VOTE_R)
     ctx = bsm.bsm_create(params)
     nw = n_bits // 32
-    bsm.bsm_set_tuning(ctx, args.cost_rows, args.cost_popc_plain, args.batch_rows)
-    if not args.no_autotune and args.cost_rows == 0:
+    bsm.bsm_set_tuning(ctx, args.cost_rows, args.cost_popc_plain, args.batch_rows, args.cost_variant)
+    if not args.no_autotune and args.cost_rows == 0 and args.cost_variant == 0:
         from paper_1402_2020_gb300 import autotune
 
         autotune.tune_cost(ctx, n_bits, agg, w, h, dmax)
