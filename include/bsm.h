@@ -339,7 +339,10 @@ typedef struct {
                               1: one column per lane; 2: two columns per lane (n_bits 128 or 256);
                               3: tensor cores (Eq. 8 as an exact E4M3 product on tcgen05, n_bits 256,
                               reference or no mask) */
-  int32_t reserved[4];     /* must be zero */
+  int32_t describe_variant; /* 0: automatic (warp per pixel from n_bits 256 on, thread per pixel below);
+                               1: thread per pixel (n_bits <= 256); 2: warp per pixel (n_bits / 32 even;
+                               always for n_bits > 256). Results identical. */
+  int32_t reserved[3];     /* must be zero */
 } bsm_tuning;
 
 /* Set / read the context's launch shapes. Synchronous, host only. */

@@ -64,7 +64,8 @@ BSM_MASK_REFERENCE, BSM_MASK_NONE, BSM_MASK_BOTH = 0, 1, 2
 
 class bsm_tuning(ctypes.Structure):
     _fields_ = [("cost_rows", ctypes.c_int32), ("cost_popc_plain", ctypes.c_int32), ("batch_rows", ctypes.c_int32),
-                ("cost_variant", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4)]
+                ("cost_variant", ctypes.c_int32), ("describe_variant", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 3)]
 
 
 class bsm_pair_desc(ctypes.Structure):
@@ -305,12 +306,13 @@ def bsm_reserve(ctx: int, max_w: int, max_h: int) -> None:
 
 
 def bsm_set_tuning(ctx: int, cost_rows: int = 0, cost_popc_plain: int = 0, batch_rows: int = 0,
-                   cost_variant: int = 0) -> None:
+                   cost_variant: int = 0, describe_variant: int = 0) -> None:
     t = bsm_tuning()
     t.cost_rows = cost_rows
     t.cost_popc_plain = cost_popc_plain
     t.batch_rows = batch_rows
     t.cost_variant = cost_variant
+    t.describe_variant = describe_variant
     _check(lib().bsm_set_tuning(ctx, ctypes.byref(t)), "bsm_set_tuning")
 
 
@@ -318,7 +320,7 @@ def bsm_get_tuning(ctx: int) -> dict:
     t = bsm_tuning()
     _check(lib().bsm_get_tuning(ctx, ctypes.byref(t)), "bsm_get_tuning")
     return {"cost_rows": t.cost_rows, "cost_popc_plain": t.cost_popc_plain, "batch_rows": t.batch_rows,
-            "cost_variant": t.cost_variant}
+            "cost_variant": t.cost_variant, "describe_variant": t.describe_variant}
 
 
 def pair_desc(rgbL, rgbR, w, h, pitch, dmax, BL, PhiL, BR, PhiR, dispL, dispR, out) -> bsm_pair_desc:

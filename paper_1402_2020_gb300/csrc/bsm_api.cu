@@ -176,7 +176,7 @@ bsm_status bsm_create(const bsm_params *p, bsm_ctx **out) {
       delete[] Es;
     }
   }
-  if (e == cudaSuccess && ctx->nw > 8) {
+  if (e == cudaSuccess) {  // pair offsets of the warp-per-pixel describe kernel (every n)
     int32_t *offs = new (std::nothrow) int32_t[p->n_bits];
     if (offs == nullptr) {
       e = cudaErrorMemoryAllocation;
@@ -305,8 +305,11 @@ bsm_status bsm_reserve(bsm_ctx *ctx, int32_t max_w, int32_t max_h) {
 
 bsm_status bsm_set_tuning(bsm_ctx *ctx, const bsm_tuning *t) {
   if (ctx == nullptr || t == nullptr) return BSM_ERR_INVALID_ARG;
-  for (int i = 0; i < 4; ++i)
+  for (int i = 0; i < 3; ++i)
     if (t->reserved[i] != 0) return BSM_ERR_INVALID_ARG;
+  if (t->describe_variant < 0 || t->describe_variant > 2) return BSM_ERR_INVALID_ARG;
+  if (t->describe_variant == 1 && ctx->nw > 8) return BSM_ERR_UNSUPPORTED;
+  if (t->describe_variant == 2 && ctx->nw % 2 != 0) return BSM_ERR_UNSUPPORTED;
   if (t->cost_variant < 0 || t->cost_variant > 3) return BSM_ERR_INVALID_ARG;
   if (t->cost_variant == 3 && !bsm::cost_tc_supported(ctx)) return BSM_ERR_UNSUPPORTED;
   if (t->cost_variant == 2 && ((ctx->nw != 4 && ctx->nw != 8) || ctx->p.mask_mode == BSM_MASK_BOTH))
@@ -318,6 +321,7 @@ bsm_status bsm_set_tuning(bsm_ctx *ctx, const bsm_tuning *t) {
   ctx->cost_plain_popc = t->cost_popc_plain;
   ctx->batch_rows = t->batch_rows;
   ctx->cost_variant = t->cost_variant;
+  ctx->describe_variant = t->describe_variant;
   return BSM_OK;
 }
 
@@ -328,6 +332,7 @@ bsm_status bsm_get_tuning(bsm_ctx *ctx, bsm_tuning *t) {
   t->cost_popc_plain = ctx->cost_plain_popc;
   t->batch_rows = ctx->batch_rows;
   t->cost_variant = ctx->cost_variant;
+  t->describe_variant = ctx->describe_variant;
   return BSM_OK;
 }
 

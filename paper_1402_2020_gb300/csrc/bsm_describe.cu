@@ -356,7 +356,9 @@ cudaError_t launch_color_plane(const bsm_ctx *ctx, const uint8_t *rgb, int w, in
 
 cudaError_t launch_describe_plane(const bsm_ctx *ctx, const uint32_t *plane, int w, int h, uint32_t *B,
                                   uint32_t *Phi, cudaStream_t s) {
-  if (ctx->nw > 8) return launch_describe_wide(ctx, plane, w, h, B, Phi, s);
+  // warp per pixel: chosen, or automatic from n = 256 on (measured faster there; thread per pixel below)
+  if (ctx->nw > 8 || ctx->describe_variant == 2 || (ctx->describe_variant == 0 && ctx->nw == 8))
+    return launch_describe_wide(ctx, plane, w, h, B, Phi, s);
   DescribeArgs a{plane, B, Phi, w, h, ctx->mask_rank, ctx->halo};
   const PairTable pt = make_pair_table(ctx);
   switch (ctx->nw) {

@@ -75,7 +75,8 @@ struct bsm_ctx {
   uint32_t *plane = nullptr;
   size_t plane_px = 0;
   int batch_rows = 0;       // rows per task of the batched cost kernel
-  int cost_variant = 0;     // 0 automatic, 1 one column per lane, 2 two columns per lane
+  int cost_variant = 0;     // 0 automatic, 1 one column per lane, 2 two columns per lane, 3 tensor cores
+  int describe_variant = 0; // 0 automatic, 1 thread per pixel, 2 warp per pixel
   int withhold_arrivals = 0;  // test hook: cost kernels skip their mbarrier arrivals
   // Batched execution (bsm_batch_run).
   int sms = 0;

@@ -377,6 +377,9 @@ cudaError_t launch_describe_wide(const bsm_ctx *ctx, const uint32_t *plane, int 
                                  cudaStream_t s) {
   const WideArgs a{plane, ctx->wide_offs, B, Phi, w, h, ctx->mask_rank, ctx->halo};
   switch (ctx->nw) {
+    case 2: return launch_wide_nw<2>(a, s);
+    case 4: return launch_wide_nw<4>(a, s);
+    case 8: return launch_wide_nw<8>(a, s);
     case 16: return launch_wide_nw<16>(a, s);
     case 32: return launch_wide_nw<32>(a, s);
     case 64: return launch_wide_nw<64>(a, s);

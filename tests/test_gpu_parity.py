@@ -99,6 +99,20 @@ def test_describe_bit_exact(B, orc, w, h, n, k, pad):
     c.close()
 
 
+@pytest.mark.parametrize("w,h,n,k", [(450, 375, 256, 0), (37, 23, 256, 100), (33, 2, 64, 64), (5, 7, 128, 1)])
+def test_describe_warp_per_pixel_bit_exact(B, orc, w, h, n, k):
+    l, _, _ = synth.stereo_pair(w, h, 16, seed=120 + w)
+    pairs = synth.pair_table(n, 31, seed=w + h + 1)
+    c = Ctx(B, pairs, mask_rank=k, dmax=16)
+    B.bsm_set_tuning(c.ctx, 0, 0, 0, 0, 2)
+    Bp, Pp, _, _ = c.describe(l, 3)
+    torch.cuda.synchronize()
+    oB, oP = orc.describe(l, pairs, k if k else None)
+    assert (u32(Bp) == oB).all()
+    assert (u32(Pp) == oP).all()
+    c.close()
+
+
 @pytest.mark.parametrize("win,n,dmax", [(1, 256, 24), (3, 64, 24), (5, 256, 24), (7, 128, 24), (5, 32, 24),
                                         (3, 256, 150), (7, 256, 137), (1, 128, 140)])
 def test_cost_volume_bit_exact(B, orc, win, n, dmax):
@@ -131,7 +145,7 @@ def test_tuning_does_not_change_bits(B, orc, rows, plain, variant, dmax):
     c = Ctx(B, pairs, agg_window=5, dmax=dmax)
     B.bsm_set_tuning(c.ctx, rows, plain, 0, variant)
     assert B.bsm_get_tuning(c.ctx) == {"cost_rows": rows, "cost_popc_plain": plain, "batch_rows": 0,
-                                       "cost_variant": variant}
+                                       "cost_variant": variant, "describe_variant": 0}
     BL, PL, _, _ = c.describe(l)
     BR, PR, _, _ = c.describe(r)
     dL, dR, cost = c.cost_wta(BL, PL, BR, PR, dmax, want_cost=True)
