@@ -215,6 +215,102 @@ __global__ void __launch_bounds__(kTY * 32) describe_kernel(const DescribeArgs a
   describe_tile<NW>(a, pt, blockIdx.x * 32, blockIdx.y * kTY, smem);
 }
 
+// Warp per pixel for n <= 256 (NW = 2, 4, 8 words): lane l evaluates pairs l, l + 32, ..., keeping
+// their tile offsets in registers for the whole CTA. Descriptor word j is __ballot_sync of its 32 tau
+// bits (Eq. 3) and lands in lane j; the lane's NW weights (Eq. 5) are packed two per register as fp16
+// 1024 + w, T (Eq. 6) is found by bisection with one warp-wide sum per step, and Phi's words are ballots
+// of w <= T (Eq. 7). One warp covers a row of 32 pixels, one pixel at a time.
+constexpr int kWY = 4;  // rows (warps) per CTA of describe_warp_kernel
+
+template <int NW>
+__global__ void __launch_bounds__(kWY * 32) describe_warp_kernel(const DescribeArgs a, const __grid_constant__ PairTable pt) {
+  constexpr int NH = NW / 2;
+  extern __shared__ __align__(16) uint32_t smem[];
+  const int halo = a.halo, tp = 32 + 2 * halo, th = kWY + 2 * halo;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int x0 = blockIdx.x * 32, y0 = blockIdx.y * kWY;
+  uint32_t *tile = smem;
+  for (int i = threadIdx.x; i < th * tp; i += blockDim.x) {
+    const int ty = i / tp, tx = i - ty * tp;
+    const int gx = min(max(x0 + tx - halo, 0), a.w - 1);
+    const int gy = min(max(y0 + ty - halo, 0), a.h - 1);
+    cp_async4(tile + i, a.plane + (size_t)gy * a.w + gx);
+  }
+  int op[NW], oq[NW];
+#pragma unroll
+  for (int j = 0; j < NW; ++j) {
+    op[j] = pt.off[32 * j + lane][0];
+    oq[j] = pt.off[32 * j + lane][1];
+  }
+  asm volatile("cp.async.wait_all;" ::: "memory");
+  __syncthreads();
+  const int y = y0 + warp;
+  if (y >= a.h) return;
+  const int npx = min(32, a.w - x0);
+  const uint32_t *row = tile + (warp + halo) * tp + halo;
+  for (int px = 0; px < npx; ++px) {
+    const uint32_t *c = row + px;  // the same for every lane
+    const uint32_t cw = *c;
+    uint32_t bword = 0, w[NW];
+#pragma unroll
+    for (int j = 0; j < NW; ++j) {
+      const uint32_t pw = c[op[j]], qw = c[oq[j]];
+      const uint32_t bits = __ballot_sync(0xFFFFFFFFu, pw > (qw | kLabMask));
+      bword = lane == j ? bits : bword;
+      w[j] = max(lab_sad(cw, pw), lab_sad(cw, qw));
+    }
+    uint32_t wv[NH];
+#pragma unroll
+    for (int m = 0; m < NH; ++m) wv[m] = __byte_perm(w[2 * m], w[2 * m + 1], 0x5410) | kHalfBias;
+    __half2 mn = *reinterpret_cast<const __half2 *>(&wv[0]), mx = mn;
+#pragma unroll
+    for (int m = 1; m < NH; ++m) {
+      mn = __hmin2(mn, *reinterpret_cast<const __half2 *>(&wv[m]));
+      mx = __hmax2(mx, *reinterpret_cast<const __half2 *>(&wv[m]));
+    }
+    const uint32_t mnb = *reinterpret_cast<const uint32_t *>(&mn), mxb = *reinterpret_cast<const uint32_t *>(&mx);
+    uint32_t lo = __reduce_min_sync(0xFFFFFFFFu, min(mnb & 0xFFFFu, mnb >> 16)) & 0x3FFu;
+    uint32_t hi = __reduce_max_sync(0xFFFFFFFFu, max(mxb & 0xFFFFu, mxb >> 16)) & 0x3FFu;
+    while (lo < hi) {  // T in [lo, hi] with count(w <= hi) >= k; every step halves the interval
+      const uint32_t mid = (lo + hi) >> 1;
+      const uint32_t tb = (0x6400u | mid) * 0x10001u;
+      const __half2 t2 = *reinterpret_cast<const __half2 *>(&tb);
+      __half2 acc = __hle2(*reinterpret_cast<const __half2 *>(&wv[0]), t2);
+#pragma unroll
+      for (int m = 1; m < NH; ++m) acc = __hadd2(acc, __hle2(*reinterpret_cast<const __half2 *>(&wv[m]), t2));
+      const __half cnt = __hadd(__hadd(__low2half(acc), __high2half(acc)), __ushort_as_half((unsigned short)0x6400));
+      const int total = (int)__reduce_add_sync(0xFFFFFFFFu, (uint32_t)__half_as_ushort(cnt) & 0x3FFu);
+      if (total >= a.k) hi = mid;
+      else lo = mid + 1;
+    }
+    const uint32_t tb = 0x6400u | lo;
+    uint32_t fword = 0;
+#pragma unroll
+    for (int m = 0; m < NH; ++m) {
+      const uint32_t f0 = __ballot_sync(0xFFFFFFFFu, (wv[m] & 0xFFFFu) <= tb);
+      const uint32_t f1 = __ballot_sync(0xFFFFFFFFu, (wv[m] >> 16) <= tb);
+      fword = lane == 2 * m ? f0 : fword;
+      fword = lane == 2 * m + 1 ? f1 : fword;
+    }
+    if (lane < NW) {
+      const size_t o = ((size_t)y * a.w + x0 + px) * NW + lane;
+      a.B[o] = bword;
+      a.Phi[o] = fword;
+    }
+  }
+}
+
+template <int NW>
+cudaError_t launch_warp_nw(const DescribeArgs &a, const PairTable &pt, cudaStream_t s) {
+  const int tp = 32 + 2 * a.halo, th = kWY + 2 * a.halo;
+  const size_t smem = 4 * (size_t)th * tp;
+  cudaError_t e = cudaFuncSetAttribute(describe_warp_kernel<NW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  dim3 grid((a.w + 31) / 32, (a.h + kWY - 1) / kWY);
+  describe_warp_kernel<NW><<<grid, kWY * 32, smem, s>>>(a, pt);
+  return cudaGetLastError();
+}
+
 // Binary search: the last pair whose first ticket of the stage is <= tk.
 template <typename F>
 __device__ __forceinline__ int find_pair(const BatchPair *pairs, int count, int tk, F base) {
@@ -356,11 +452,18 @@ cudaError_t launch_color_plane(const bsm_ctx *ctx, const uint8_t *rgb, int w, in
 
 cudaError_t launch_describe_plane(const bsm_ctx *ctx, const uint32_t *plane, int w, int h, uint32_t *B,
                                   uint32_t *Phi, cudaStream_t s) {
-  // warp per pixel: chosen, or automatic from n = 256 on (measured faster there; thread per pixel below)
-  if (ctx->nw > 8 || ctx->describe_variant == 2 || (ctx->describe_variant == 0 && ctx->nw == 8))
-    return launch_describe_wide(ctx, plane, w, h, B, Phi, s);
+  if (ctx->nw > 8) return launch_describe_wide(ctx, plane, w, h, B, Phi, s);
   DescribeArgs a{plane, B, Phi, w, h, ctx->mask_rank, ctx->halo};
   const PairTable pt = make_pair_table(ctx);
+  // warp per pixel: chosen, or automatic from n = 256 on (measured faster there; thread per pixel below)
+  if (ctx->describe_variant == 2 || (ctx->describe_variant == 0 && ctx->nw == 8)) {
+    switch (ctx->nw) {
+      case 2: return launch_warp_nw<2>(a, pt, s);
+      case 4: return launch_warp_nw<4>(a, pt, s);
+      case 8: return launch_warp_nw<8>(a, pt, s);
+      default: return cudaErrorInvalidValue;
+    }
+  }
   switch (ctx->nw) {
     case 1: return launch_nw<1>(a, pt, s);
     case 2: return launch_nw<2>(a, pt, s);
