@@ -187,12 +187,13 @@ bsm_status bsm_reserve_batch(bsm_ctx *ctx, int64_t total_pixels);
  *
  * A scheduler thread owns `lanes` lanes (each a context with the engine's parameters and its own
  * stream). Whenever a lane is free it admits queued requests in arrival order while the engine's
- * device-memory budget allows, and runs them as one bsm_batch_run with the copies of their views in
- * and their refined maps out, so batches of different lanes overlap on the device and requests that
- * arrive while others run are admitted as soon as a lane and memory free up. Request buffers are
- * allocated from the engine's own stream-ordered pool; each lane's context also keeps batch scratch
- * (grown to the largest batch it has seen) outside the budget. Results are bit-identical to the
- * per-pair calls.
+ * device-memory budget allows, and runs them with the copies of their views in and their refined maps
+ * out: the small requests as one bsm_batch_run, the large ones (w h dmax >= 1280 x 720 x 128) through
+ * the per-pair calls with the tensor-core cost kernel where the parameters allow it. Batches of
+ * different lanes overlap on the device and requests that arrive while others run are admitted as soon
+ * as a lane and memory free up. Request buffers are allocated from the engine's own stream-ordered
+ * pool; each lane's context also keeps batch and per-pair scratch (grown to the largest seen) outside
+ * the budget. Results are bit-identical to the per-pair calls.
  */
 typedef struct bsm_server bsm_server;
 

@@ -6,8 +6,10 @@
 // in arrival order while the engine's device-memory budget allows (each request needs its two views,
 // four descriptor planes, three maps and its share of the batch scratch), allocates their buffers
 // from the engine's own stream-ordered memory pool, and enqueues on the lane's stream: the host-to-
-// device copies of the views, one bsm_batch_run for the whole batch, the device-to-host copies of the
-// refined maps, the frees, and a completion event. Requests that arrive while lanes are busy wait
+// device copies of the views, one bsm_batch_run for the batch's small requests, the per-pair calls
+// (describe, the tensor-core cost kernel where the parameters allow it, refine) for its large ones
+// (w h dmax at least 1280 x 720 x 128: there a single pair fills the GPU and the per-pair kernels are
+// the faster ones), the device-to-host copies of the refined maps, the frees, and a completion event. Requests that arrive while lanes are busy wait
 // only until a lane and memory free up. Completed request ids (with a status each) are handed to
 // bsm_server_poll. A request too large for the budget completes with BSM_ERR_INVALID_ARG; a batch
 // whose launch fails completes every request of that batch with the failing status.
@@ -24,6 +26,8 @@
 namespace {
 
 size_t round256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+constexpr int64_t kPerPairWork = 1280LL * 720 * 128;  // w h dmax from which a request runs on its own
 
 struct Pending {
   bsm_request req;
@@ -124,8 +128,22 @@ bsm_status launch_batch(bsm_server *s, Lane &lane) {
         cudaMemcpyAsync((void *)d.rgbR, r.rgbR, (size_t)r.h * r.pitch_bytes, cudaMemcpyHostToDevice, st) != cudaSuccess)
       return BSM_ERR_CUDA;
   }
-  const bsm_status b = bsm_batch_run(lane.ctx, descs.data(), (int32_t)descs.size(), st);
-  if (b != BSM_OK) return b;
+  std::vector<bsm_pair_desc> small;
+  for (const bsm_pair_desc &d : descs)
+    if ((int64_t)d.w * d.h * d.dmax < kPerPairWork) small.push_back(d);
+  if (!small.empty()) {
+    const bsm_status b = bsm_batch_run(lane.ctx, small.data(), (int32_t)small.size(), st);
+    if (b != BSM_OK) return b;
+  }
+  for (const bsm_pair_desc &d : descs) {
+    if ((int64_t)d.w * d.h * d.dmax < kPerPairWork) continue;
+    bsm_status b = bsm_describe(lane.ctx, d.rgbL, d.w, d.h, d.pitch_bytes, d.BL, d.PhiL, st);
+    if (b == BSM_OK) b = bsm_describe(lane.ctx, d.rgbR, d.w, d.h, d.pitch_bytes, d.BR, d.PhiR, st);
+    if (b == BSM_OK)
+      b = bsm_cost_aggregate_wta(lane.ctx, d.BL, d.PhiL, d.BR, d.PhiR, d.w, d.h, d.dmax, d.dispL, d.dispR, nullptr, st);
+    if (b == BSM_OK) b = bsm_refine(lane.ctx, d.rgbL, d.pitch_bytes, d.dispL, d.dispR, d.w, d.h, d.dmax, d.out, st);
+    if (b != BSM_OK) return b;
+  }
   for (size_t i = 0; i < lane.batch.size(); ++i) {
     const bsm_request &r = lane.batch[i].p.req;
     if (cudaMemcpyAsync(r.out, descs[i].out, (size_t)r.w * r.h * 4, cudaMemcpyDeviceToHost, st) != cudaSuccess)
@@ -246,6 +264,11 @@ bsm_status bsm_server_create(const bsm_params *params, const bsm_server_config *
   s->lanes.resize(cfg->lanes);
   for (Lane &lane : s->lanes) {
     bsm_status st = bsm_create(&s->params, &lane.ctx);
+    if (st == BSM_OK) {  // the per-pair requests use the tensor-core cost kernel where it is built
+      bsm_tuning t{};
+      t.cost_variant = 3;
+      if (bsm_set_tuning(lane.ctx, &t) != BSM_OK) t.cost_variant = 0;
+    }
     if (st == BSM_OK && cudaStreamCreateWithFlags(&lane.stream, cudaStreamNonBlocking) != cudaSuccess) st = BSM_ERR_CUDA;
     if (st == BSM_OK && cudaEventCreateWithFlags(&lane.done, cudaEventDisableTiming) != cudaSuccess) st = BSM_ERR_CUDA;
     if (st == BSM_OK && cudaHostAlloc(&lane.status_host, sizeof(uint32_t), cudaHostAllocDefault) != cudaSuccess)
