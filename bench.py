@@ -60,6 +60,8 @@ def parse():
     ap.add_argument("--no-autotune", action="store_true", help="skip the launch-shape autotuner")
     ap.add_argument("--cost-variant", type=int, default=0,
                     help="cost kernel: 1 one column per lane, 2 two columns, 3 tensor cores (0: autotuned)")
+    ap.add_argument("--describe-variant", type=int, default=0,
+                    help="describe kernel: 0 auto, 1 thread per pixel, 2 warp per pixel")
     ap.add_argument("--n-bits", type=int, default=N_BITS, help="descriptor length n (32 ... 4096)")
     ap.add_argument("--sgm", default="", help="P1,P2,paths: semi-global aggregation of both cost volumes")
     ap.add_argument("--quality", action="store_true",
@@ -238,7 +240,7 @@ def run_batch(args, cfg, world, rank, local):
     pairs = synth.pair_table(N_BITS, WINDOW_S, seed=PAIR_SEED)
     params = bsm.make_params(pairs, window_S=WINDOW_S, agg_window=AGG, dmax=256, vote_radius=VOTE_R)
     ctx = bsm.bsm_create(params)
-    bsm.bsm_set_tuning(ctx, args.cost_rows, args.cost_popc_plain, args.batch_rows)
+    bsm.bsm_set_tuning(ctx, args.cost_rows, args.cost_popc_plain, args.batch_rows, 0, args.describe_variant)
     nw = N_BITS // 32
     ts = []
     for (w, h, dmax, seed) in shapes:
@@ -495,7 +497,8 @@ def run_pair(args, cfg, world, rank, local, n_bits=N_BITS, window_S=WINDOW_S, si
                              vote_radius=VOTE_R)
     ctx = bsm.bsm_create(params)
     nw = n_bits // 32
-    bsm.bsm_set_tuning(ctx, args.cost_rows, args.cost_popc_plain, args.batch_rows, args.cost_variant)
+    bsm.bsm_set_tuning(ctx, args.cost_rows, args.cost_popc_plain, args.batch_rows, args.cost_variant,
+                       args.describe_variant)
     if not args.no_autotune and args.cost_rows == 0 and args.cost_variant == 0:
         from paper_1402_2020_gb300 import autotune
 

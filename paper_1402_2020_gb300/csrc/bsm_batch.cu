@@ -54,6 +54,9 @@ cudaError_t ensure_batch_buffers(bsm_ctx *ctx, size_t plane_words) {
   return e;
 }
 
+// The kernel choices baked into the captured graph: a change of either means a new capture.
+int graph_variant(const bsm_ctx *ctx) { return ctx->cost_plain_popc + 16 * ctx->describe_variant; }
+
 cudaError_t capture_graph(bsm_ctx *ctx) {
   cudaStream_t cs = ctx->batch_capture;
   // Attributes and occupancy first: nothing but stream work may happen inside the capture.
@@ -84,7 +87,7 @@ cudaError_t capture_graph(bsm_ctx *ctx) {
   ctx->batch_graph = nullptr;
   e = cudaGraphInstantiate(&ctx->batch_graph, graph, 0);
   cudaGraphDestroy(graph);
-  if (e == cudaSuccess) ctx->batch_graph_variant = ctx->cost_plain_popc;
+  if (e == cudaSuccess) ctx->batch_graph_variant = graph_variant(ctx);
   return e;
 }
 
@@ -155,7 +158,7 @@ extern "C" bsm_status bsm_batch_run(bsm_ctx *ctx, const bsm_pair_desc *descs, in
   hdr->total[2] = t_cost;
   hdr->total[3] = t_ref;
 
-  if (ctx->batch_graph == nullptr || ctx->batch_graph_variant != ctx->cost_plain_popc) {
+  if (ctx->batch_graph == nullptr || ctx->batch_graph_variant != graph_variant(ctx)) {
     e = capture_graph(ctx);
     if (e != cudaSuccess) return fail(ctx, e);
   }

@@ -222,13 +222,14 @@ __global__ void __launch_bounds__(kTY * 32) describe_kernel(const DescribeArgs a
 // of w <= T (Eq. 7). One warp covers a row of 32 pixels, one pixel at a time.
 constexpr int kWY = 4;  // rows (warps) per CTA of describe_warp_kernel
 
+// One 32 x kWY block with top-left corner (x0, y0). Contains one CTA-wide barrier, which every thread
+// of the CTA reaches.
 template <int NW>
-__global__ void __launch_bounds__(kWY * 32) describe_warp_kernel(const DescribeArgs a, const __grid_constant__ PairTable pt) {
+__device__ __forceinline__ void describe_warp_tile(const DescribeArgs &a, const PairTable &pt, int x0, int y0,
+                                                   uint32_t *smem) {
   constexpr int NH = NW / 2;
-  extern __shared__ __align__(16) uint32_t smem[];
   const int halo = a.halo, tp = 32 + 2 * halo, th = kWY + 2 * halo;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int x0 = blockIdx.x * 32, y0 = blockIdx.y * kWY;
   uint32_t *tile = smem;
   for (int i = threadIdx.x; i < th * tp; i += blockDim.x) {
     const int ty = i / tp, tx = i - ty * tp;
@@ -236,11 +237,13 @@ __global__ void __launch_bounds__(kWY * 32) describe_warp_kernel(const DescribeA
     const int gy = min(max(y0 + ty - halo, 0), a.h - 1);
     cp_async4(tile + i, a.plane + (size_t)gy * a.w + gx);
   }
+  // The offsets differ per lane, so a constant-bank read of them is serialised across the warp: read
+  // them once per tile, through an opaque move that keeps them in registers instead of re-read.
   int op[NW], oq[NW];
 #pragma unroll
   for (int j = 0; j < NW; ++j) {
-    op[j] = pt.off[32 * j + lane][0];
-    oq[j] = pt.off[32 * j + lane][1];
+    asm volatile("mov.b32 %0, %1;" : "=r"(op[j]) : "r"(pt.off[32 * j + lane][0]));
+    asm volatile("mov.b32 %0, %1;" : "=r"(oq[j]) : "r"(pt.off[32 * j + lane][1]));
   }
   asm volatile("cp.async.wait_all;" ::: "memory");
   __syncthreads();
@@ -248,6 +251,7 @@ __global__ void __launch_bounds__(kWY * 32) describe_warp_kernel(const DescribeA
   if (y >= a.h) return;
   const int npx = min(32, a.w - x0);
   const uint32_t *row = tile + (warp + halo) * tp + halo;
+#pragma unroll 2  // two pixels' ballot and reduction chains overlap
   for (int px = 0; px < npx; ++px) {
     const uint32_t *c = row + px;  // the same for every lane
     const uint32_t cw = *c;
@@ -301,9 +305,16 @@ __global__ void __launch_bounds__(kWY * 32) describe_warp_kernel(const DescribeA
 }
 
 template <int NW>
+__global__ void __launch_bounds__(kWY * 32) describe_warp_kernel(const DescribeArgs a, const __grid_constant__ PairTable pt) {
+  extern __shared__ __align__(16) uint32_t smem[];
+  describe_warp_tile<NW>(a, pt, blockIdx.x * 32, blockIdx.y * kWY, smem);
+}
+
+size_t describe_warp_smem(int halo) { return 4 * (size_t)(kWY + 2 * halo) * (32 + 2 * halo); }
+
+template <int NW>
 cudaError_t launch_warp_nw(const DescribeArgs &a, const PairTable &pt, cudaStream_t s) {
-  const int tp = 32 + 2 * a.halo, th = kWY + 2 * a.halo;
-  const size_t smem = 4 * (size_t)th * tp;
+  const size_t smem = describe_warp_smem(a.halo);
   cudaError_t e = cudaFuncSetAttribute(describe_warp_kernel<NW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   dim3 grid((a.w + 31) / 32, (a.h + kWY - 1) / kWY);
@@ -367,6 +378,30 @@ __global__ void __launch_bounds__(kTY * 32) describe_batch_kernel(BatchHeader *h
   }
 }
 
+// Batched describe, warp per pixel: persistent CTAs take (pair, view, tile) tickets of the same tiling.
+template <int NW>
+__global__ void __launch_bounds__(kWY * 32) describe_warp_batch_kernel(BatchHeader *hdr, const BatchPair *pairs, int k,
+                                                                       int halo, const __grid_constant__ PairTable pt) {
+  extern __shared__ __align__(16) uint32_t smem[];
+  __shared__ int s_ticket;
+  const int total = hdr->total[1], count = hdr->count;
+  for (;;) {
+    __syncthreads();  // the previous tile is done with shared memory
+    if (threadIdx.x == 0) s_ticket = (int)atomicAdd(&hdr->counters[1], 1u);
+    __syncthreads();
+    const int tk = s_ticket;
+    if (tk >= total) return;
+    const BatchPair &p = pairs[find_pair(pairs, count, tk, [](const BatchPair &q) { return q.desc_base; })];
+    int r = tk - p.desc_base;
+    const int per_view = p.desc_tx * p.desc_ty;
+    const int view = r / per_view;
+    r -= view * per_view;
+    const int ty = r / p.desc_tx, tx = r - ty * p.desc_tx;
+    const DescribeArgs a{p.plane[view], p.B[view], p.Phi[view], p.w, p.h, k, halo};
+    describe_warp_tile<NW>(a, pt, tx * 32, ty * kWY, smem);
+  }
+}
+
 template <int NW>
 size_t describe_smem(int halo) {
   const int tp = 32 + 2 * halo, th = kTY + 2 * halo;
@@ -383,23 +418,40 @@ cudaError_t launch_nw(const DescribeArgs &a, const PairTable &pt, cudaStream_t s
   return cudaGetLastError();
 }
 
-template <int NW>
+static_assert(kWY == kTY, "the batched describe kernels share one tiling");
+
+template <int NW, bool WARP>
 cudaError_t prepare_batch_nw(int halo, int sms, int *grid) {
-  const size_t smem = describe_smem<NW>(halo);
-  cudaError_t e =
-      cudaFuncSetAttribute(describe_batch_kernel<NW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  size_t smem;
+  void (*kern)(BatchHeader *, const BatchPair *, int, int, const PairTable);
+  if constexpr (WARP) {
+    smem = describe_warp_smem(halo);
+    kern = describe_warp_batch_kernel<NW>;
+  } else {
+    smem = describe_smem<NW>(halo);
+    kern = describe_batch_kernel<NW>;
+  }
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, describe_batch_kernel<NW>, kTY * 32, smem);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kTY * 32, smem);
   *grid = max(1, per_sm) * sms;
   return e;
 }
 
-template <int NW>
+template <int NW, bool WARP>
 cudaError_t launch_batch_nw(BatchHeader *hdr, const BatchPair *pairs, int k, int halo, const PairTable &pt, int grid,
                             cudaStream_t s) {
-  describe_batch_kernel<NW><<<grid, kTY * 32, describe_smem<NW>(halo), s>>>(hdr, pairs, k, halo, pt);
+  if constexpr (WARP)
+    describe_warp_batch_kernel<NW><<<grid, kTY * 32, describe_warp_smem(halo), s>>>(hdr, pairs, k, halo, pt);
+  else
+    describe_batch_kernel<NW><<<grid, kTY * 32, describe_smem<NW>(halo), s>>>(hdr, pairs, k, halo, pt);
   return cudaGetLastError();
+}
+
+// The batched describe follows the per-pair choice: warp per pixel for n = 256 unless told otherwise.
+bool batch_warp(const bsm_ctx *ctx) {
+  return ctx->nw % 2 == 0 && (ctx->describe_variant == 2 || (ctx->describe_variant == 0 && ctx->nw == 8));
 }
 
 PairTable make_pair_table(const bsm_ctx *ctx) {
@@ -422,11 +474,12 @@ cudaError_t launch_color_plane_batch(const bsm_ctx *ctx, const BatchHeader *hdr,
 }
 
 cudaError_t prepare_describe_batch(const bsm_ctx *ctx, int *grid) {
+  const bool wp = batch_warp(ctx);
   switch (ctx->nw) {
-    case 1: return prepare_batch_nw<1>(ctx->halo, ctx->sms, grid);
-    case 2: return prepare_batch_nw<2>(ctx->halo, ctx->sms, grid);
-    case 4: return prepare_batch_nw<4>(ctx->halo, ctx->sms, grid);
-    case 8: return prepare_batch_nw<8>(ctx->halo, ctx->sms, grid);
+    case 1: return prepare_batch_nw<1, false>(ctx->halo, ctx->sms, grid);
+    case 2: return wp ? prepare_batch_nw<2, true>(ctx->halo, ctx->sms, grid) : prepare_batch_nw<2, false>(ctx->halo, ctx->sms, grid);
+    case 4: return wp ? prepare_batch_nw<4, true>(ctx->halo, ctx->sms, grid) : prepare_batch_nw<4, false>(ctx->halo, ctx->sms, grid);
+    case 8: return wp ? prepare_batch_nw<8, true>(ctx->halo, ctx->sms, grid) : prepare_batch_nw<8, false>(ctx->halo, ctx->sms, grid);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -434,11 +487,13 @@ cudaError_t prepare_describe_batch(const bsm_ctx *ctx, int *grid) {
 cudaError_t launch_describe_batch(const bsm_ctx *ctx, BatchHeader *hdr, const BatchPair *pairs, int grid,
                                   cudaStream_t s) {
   const PairTable pt = make_pair_table(ctx);
+  const bool wp = batch_warp(ctx);
+  const int k = ctx->mask_rank, hl = ctx->halo;
   switch (ctx->nw) {
-    case 1: return launch_batch_nw<1>(hdr, pairs, ctx->mask_rank, ctx->halo, pt, grid, s);
-    case 2: return launch_batch_nw<2>(hdr, pairs, ctx->mask_rank, ctx->halo, pt, grid, s);
-    case 4: return launch_batch_nw<4>(hdr, pairs, ctx->mask_rank, ctx->halo, pt, grid, s);
-    case 8: return launch_batch_nw<8>(hdr, pairs, ctx->mask_rank, ctx->halo, pt, grid, s);
+    case 1: return launch_batch_nw<1, false>(hdr, pairs, k, hl, pt, grid, s);
+    case 2: return wp ? launch_batch_nw<2, true>(hdr, pairs, k, hl, pt, grid, s) : launch_batch_nw<2, false>(hdr, pairs, k, hl, pt, grid, s);
+    case 4: return wp ? launch_batch_nw<4, true>(hdr, pairs, k, hl, pt, grid, s) : launch_batch_nw<4, false>(hdr, pairs, k, hl, pt, grid, s);
+    case 8: return wp ? launch_batch_nw<8, true>(hdr, pairs, k, hl, pt, grid, s) : launch_batch_nw<8, false>(hdr, pairs, k, hl, pt, grid, s);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -85,7 +85,7 @@ struct bsm_ctx {
   cudaEvent_t batch_copied = nullptr;   // the graph's table copy has finished
   cudaStream_t batch_capture = nullptr; // stream the graph is captured on
   cudaGraphExec_t batch_graph = nullptr;
-  int batch_graph_variant = -1;         // cost_plain_popc the graph was captured with
+  int batch_graph_variant = -1;         // popcount form and describe variant the graph was captured with
   int batch_grid[4] = {0, 0, 0, 0};     // persistent grid sizes of the four batched kernels
   uint32_t *batch_plane = nullptr;      // colour planes of every view of a batch
   size_t batch_plane_words = 0;

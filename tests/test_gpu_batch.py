@@ -71,19 +71,26 @@ def test_batch_equals_per_pair(B, win, n):
         B.bsm_destroy(ctx)
 
 
-def test_batch_matches_oracle(B, orc):
-    pairs = synth.pair_table(256, 31, seed=1200)
+# describe variants: 0 picks warp per pixel at n = 256 and thread per pixel below; 1 and 2 force one
+@pytest.mark.parametrize("n,variants", [(256, (0, 1)), (128, (2, 1)), (64, (0, 2))])
+def test_batch_matches_oracle(B, orc, n, variants):
+    pairs = synth.pair_table(n, 31, seed=1200 + n)
     ctx = B.bsm_create(B.make_params(pairs, agg_window=5, dmax=64, vote_radius=6))
     try:
-        ts = [make_pair(w, h, d, seed=1300 + i, nw=8) for i, (w, h, d) in enumerate([(90, 40, 32), (47, 29, 64)])]
-        B.bsm_batch_run(ctx, [desc(B, t) for t in ts])
-        torch.cuda.synchronize()
-        for t in ts:
-            ref = orc.pipeline(t["l"], t["r"], pairs, t["dmax"], win=5, R=6)
-            assert (t["dispL"].cpu().numpy() == ref["dL"]).all()
-            assert (t["dispR"].cpu().numpy() == ref["dR"]).all()
-            assert (t["out"].cpu().numpy() == ref["disp"]).all()
-            assert (t["PhiR"].cpu().numpy().view(np.uint32) == ref["PhiR"]).all()
+        for rnd, variant in enumerate(variants):  # the second variant needs a new graph
+            B.bsm_set_tuning(ctx, 0, 0, 0, 0, variant)
+            shapes = [(90, 40, 32), (47, 29, 64), (33, 7, 20)]
+            ts = [make_pair(w, h, d, seed=1300 + 10 * rnd + i, nw=n // 32) for i, (w, h, d) in enumerate(shapes)]
+            B.bsm_batch_run(ctx, [desc(B, t) for t in ts])
+            torch.cuda.synchronize()
+            for t in ts:
+                ref = orc.pipeline(t["l"], t["r"], pairs, t["dmax"], win=5, R=6)
+                assert (t["BL"].cpu().numpy().view(np.uint32) == ref["BL"]).all(), (n, variant)
+                assert (t["PhiR"].cpu().numpy().view(np.uint32) == ref["PhiR"]).all(), (n, variant)
+                assert (t["dispL"].cpu().numpy() == ref["dL"]).all()
+                assert (t["dispR"].cpu().numpy() == ref["dR"]).all()
+                assert (t["out"].cpu().numpy() == ref["disp"]).all()
+        assert B.bsm_last_error(ctx) == B.BSM_OK
     finally:
         B.bsm_destroy(ctx)
 
