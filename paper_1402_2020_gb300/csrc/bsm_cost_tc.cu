@@ -45,7 +45,8 @@ constexpr int kWarps = 18;        // producer, MMA, 4 B-operand builders, 12 epi
 constexpr int kThreads = 32 * kWarps;
 constexpr int kXpd = 4 * 32;      // B-operand builder threads (warps 2..5)
 constexpr int kEpi = 12 * 32;     // epilogue threads (warps 6..17)
-constexpr int kTP = 264;          // u16 pitch of the term table T[x][d] (rows 16-byte aligned)
+constexpr int kTP = 288;          // u16 pitch of the term table T[x][d] (rows 16-byte aligned)
+constexpr int kTPad = 32;         // u16 in front of row 0; row r's band terms past d = 255 land in row r + 1's first 32
 constexpr int kAB = kTM * kChunk;         // A chunk: 4 groups x 128 rows x 16 bytes
 constexpr int kBB = kNB * kChunk;         // B chunk: 4 groups x 384 rows x 16 bytes
 constexpr int kOpB = kAB + kBB;           // one operand buffer (32 KB)
@@ -53,11 +54,13 @@ constexpr int kRawRow = kNB * 32;         // other-view words of one row of the 
 constexpr int kOffOp = 0;
 constexpr int kOffRaw = kOffOp + kBuf * kOpB;          // 2 slots x (entering, leaving) rows
 constexpr int kOffT = kOffRaw + 2 * 2 * kRawRow;
-constexpr int kOffC0 = kOffT + kTM * kTP * 2;
+constexpr int kOffC0 = kOffT + (kTM * kTP + kTPad) * 2;
 constexpr int kOffMisc = kOffC0 + kTM * 4;
 constexpr int kSmem = kOffMisc + 128;
 static_assert(kSmem <= 232448, "shared memory of one CTA");
-static_assert(kOffRaw % 1024 == 0 && kOffT % 1024 == 0 && kOffMisc % 16 == 0 && (kTP * 2) % 16 == 0, "alignment");
+static_assert(kOffRaw % 1024 == 0 && kOffT % 1024 == 0 && kOffC0 % 16 == 0 && kOffMisc % 16 == 0 && (kTP * 2) % 16 == 0 &&
+                  (kTPad * 2) % 16 == 0 && kTP >= 256 + kTPad,
+              "alignment");
 constexpr long long kWait = 1LL << 31;  // about one second at the GB300 clock
 
 struct TcArgs {
@@ -240,7 +243,7 @@ __device__ __forceinline__ void cost_tc_body(const TcArgs &a, uint8_t *smem) {
   uint64_t *acc_full = raw_empty + 2, *acc_empty = acc_full + 1;
   uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(acc_empty + 1);
   uint32_t *abort_flag = tmem_slot + 1;
-  uint16_t *T = reinterpret_cast<uint16_t *>(smem + kOffT);
+  uint16_t *T = reinterpret_cast<uint16_t *>(smem + kOffT) + kTPad;
   int32_t *c0v = reinterpret_cast<int32_t *>(smem + kOffC0);
 
   if (tid == 0) {
@@ -359,28 +362,43 @@ __device__ __forceinline__ void cost_tc_body(const TcArgs &a, uint8_t *smem) {
       ok = mbar_wait(&raw_full[rs], (i >> 1) & 1u);
       if (!ok) break;
       const uint8_t *raw = smem + kOffRaw + rs * 2 * kRawRow;
-      for (int c = 0; c < 8 && ok; ++c) {
-        const bool is_new = c < 4;
-        if (!(is_new ? hn : ho)) continue;
-        const int b = (int)(slot % kBuf);
-        if (slot >= kBuf) ok = mbar_wait(&empty[b], ((slot / kBuf) - 1) & 1u);
-        if (!ok) break;
-        const uint32_t *rw = reinterpret_cast<const uint32_t *>(raw + (is_new ? 0 : kRawRow));
-        uint8_t *opB = smem + kOffOp + b * kOpB + kAB;
-        const int w0 = 2 * (c & 3);
+      // per row half (entering, leaving): the 8 words of each of the thread's band columns, read once
+#pragma unroll
+      for (int half = 0; half < 2; ++half) {
+        if (!ok || !(half == 0 ? hn : ho)) continue;
+        const uint32_t *rw = reinterpret_cast<const uint32_t *>(raw + half * kRawRow);
+        uint4 qw[3][2];
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
           const int r = t + 128 * k;
           if (r < ntot) {
-            const uint2 ow = *reinterpret_cast<const uint2 *>(rw + r * 8 + w0);
-            expand_b(ow.x, opB + 0 * (kNB * 16) + r * 16, opB + 1 * (kNB * 16) + r * 16);
-            expand_b(ow.y, opB + 2 * (kNB * 16) + r * 16, opB + 3 * (kNB * 16) + r * 16);
+            qw[k][0] = *reinterpret_cast<const uint4 *>(rw + r * 8);
+            qw[k][1] = *reinterpret_cast<const uint4 *>(rw + r * 8 + 4);
+          } else {
+            qw[k][0] = qw[k][1] = make_uint4(0u, 0u, 0u, 0u);
           }
         }
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&full[b]);
-        ++slot;
+#pragma unroll
+        for (int cc = 0; cc < 4; ++cc) {  // chunk cc: descriptor words 2 cc and 2 cc + 1
+          if (!ok) break;
+          const int b = (int)(slot % kBuf);
+          if (slot >= kBuf) ok = mbar_wait(&empty[b], ((slot / kBuf) - 1) & 1u);
+          if (!ok) break;
+          uint8_t *opB = smem + kOffOp + b * kOpB + kAB;
+#pragma unroll
+          for (int k = 0; k < 3; ++k) {
+            const int r = t + 128 * k;
+            if (r < ntot) {
+              const uint4 &qq = qw[k][cc >> 1];
+              expand_b((cc & 1) ? qq.z : qq.x, opB + 0 * (kNB * 16) + r * 16, opB + 1 * (kNB * 16) + r * 16);
+              expand_b((cc & 1) ? qq.w : qq.y, opB + 2 * (kNB * 16) + r * 16, opB + 3 * (kNB * 16) + r * 16);
+            }
+          }
+          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&full[b]);
+          ++slot;
+        }
       }
       __syncwarp();
       if (lane == 0 && ok) mbar_arrive(&raw_empty[rs]);  // this row's words are no longer needed
@@ -413,39 +431,76 @@ __device__ __forceinline__ void cost_tc_body(const TcArgs &a, uint8_t *smem) {
       for (int v = -R; v <= R; ++v) nh += (yout + v >= 0 && yout + v < h) ? 1 : 0;
       {
         const float base = (float)c0v[r] + 12582912.0f;  // 1.5 * 2^23: the sum's integer in the low bits
-        uint16_t *Trow = T + r * kTP;
         const int nck = D / 32 + 1;
-        for (int k = g; k < nck; k += 3) {
-          uint32_t v[32];
-          tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(32 * q + 32 * k), v);
-          // band column 32 q + 32 k + t is disparity d = DIR ? rel : D - 1 - rel, rel = 32 k + t - lane
-          if (fast && k > 0 && k < nck - 1) {
-            uint16_t *p0 = DIR == 0 ? Trow + (D - 1 - 32 * k + lane) : Trow + (32 * k - lane);
+        const uint32_t sentinel = col_in ? (uint32_t)nh * 256u : 0u;
+        // Element t of chunk k is disparity c - t (left reference) or c + t (right); its terms are
+        // consecutive 16-bit entries of row r from u16 index a0 = r kTP + c down (left) or up (right),
+        // written as 32-bit words: where a0 sits mid-word, 15 whole words and two single entries. Terms
+        // of d outside [0, D) land in row padding that is never read. The first chunk is written at
+        // once; the other two are held in registers until the accumulator is released.
+        uint32_t *T32 = reinterpret_cast<uint32_t *>(T);
+        uint32_t wd[2][16];
+        auto put = [&](int a0, bool al, const uint32_t(&wk)[16]) {
+          if (DIR == 0) {
+            uint32_t *wp = T32 + ((a0 - 1) >> 1);
 #pragma unroll
-            for (int t = 0; t < 32; ++t) {
-              const uint32_t val = __float_as_uint(fmaf(__uint_as_float(v[t]), 4096.0f, base));
-              if (DIR == 0) p0[-t] = (uint16_t)val;
-              else p0[t] = (uint16_t)val;
-            }
+            for (int p = 0; p < 16; ++p)
+              if (p < 15 || al) wp[-p] = wk[p];
           } else {
-            const uint32_t sentinel = (uint32_t)nh * 256u;
+            uint32_t *wp = T32 + ((a0 + 1) >> 1);
 #pragma unroll
-            for (int t = 0; t < 32; ++t) {
-              const int rel = 32 * k + t - lane;
-              if (rel < 0 || rel >= D) continue;
-              const int d = DIR == 0 ? D - 1 - rel : rel;
-              uint32_t val = __float_as_uint(fmaf(__uint_as_float(v[t]), 4096.0f, base));
-              const bool match_in = DIR == 0 ? xr - d >= 0 : xr + d < w;
-              if (!match_in) val = sentinel;
-              Trow[d] = (uint16_t)(col_in ? val : 0u);
+            for (int p = 0; p < 16; ++p)
+              if (p < 15 || al) wp[p] = wk[p];
+          }
+        };
+        auto chunk_a0 = [&](int k) { return r * kTP + (DIR == 0 ? D - 1 - 32 * k + lane : 32 * k - lane); };
+        auto whole = [&](int a0) { return DIR == 0 ? (a0 & 1) != 0 : (a0 & 1) == 0; };  // 16 whole words
+#pragma unroll
+        for (int kk = 0; kk < 3; ++kk) {
+          const int k = g + 3 * kk;
+          if (k < nck) {
+            uint32_t v[32];
+            tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(32 * q + 32 * k), v);
+#pragma unroll
+            for (int t = 0; t < 32; ++t) v[t] = __float_as_uint(fmaf(__uint_as_float(v[t]), 4096.0f, base));
+            const int a0 = chunk_a0(k);
+            if (!fast) {  // the sentinel where the match leaves the other view; 0 for columns off the image
+              const int c = a0 - r * kTP;
+              const int cut = DIR == 0 ? (col_in ? c - xr : 64) : (col_in ? w - xr - c : -1);
+#pragma unroll
+              for (int t = 0; t < 32; ++t) v[t] = (DIR == 0 ? t >= cut : t < cut) ? v[t] : sentinel;
+            }
+            const bool al = whole(a0);
+            const uint32_t sel = (al == (DIR == 0)) ? 0x5410u : 0x1054u;
+            uint32_t wk[16];
+#pragma unroll
+            for (int p = 0; p < 16; ++p)
+              wk[p] = __byte_perm(v[2 * p + 1], al ? v[2 * p] : v[2 * p + 2 < 32 ? 2 * p + 2 : 31], sel);
+            if (!al) {
+              T[a0] = (uint16_t)v[0];
+              T[DIR == 0 ? a0 - 31 : a0 + 31] = (uint16_t)v[31];
+            }
+            if (kk == 0) {
+              put(a0, al, wk);
+            } else {
+#pragma unroll
+              for (int p = 0; p < 16; ++p) wd[kk - 1][p] = wk[p];
             }
           }
         }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncwarp();
+        if (lane == 0) mbar_arrive(acc_empty);  // the next row's MMAs may start; the stores below overlap them
+#pragma unroll
+        for (int kk = 1; kk < 3; ++kk) {
+          const int k = g + 3 * kk;
+          if (k < nck) {
+            const int a0 = chunk_a0(k);
+            put(a0, whole(a0), wd[kk - 1]);
+          }
+        }
       }
-      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-      __syncwarp();
-      if (lane == 0) mbar_arrive(acc_empty);  // this warp is done with the accumulator
-      epi_sync();                              // T complete
+      epi_sync();  // T complete
 
       // horizontal box sum + Eq. 1: warp ew takes output columns rr0 .. rr1 - 1, lane 8 disparities
       const int rr0 = R + 11 * ew, rr1 = min(rr0 + 11, kTM - R);
