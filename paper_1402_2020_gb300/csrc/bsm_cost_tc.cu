@@ -519,11 +519,20 @@ __device__ __forceinline__ void cost_tc_body(const TcArgs &a, uint8_t *smem) {
 #pragma unroll
         for (int j = 0; j < 4; ++j)
           inval[j] = (d8 + 2 * j < dmax ? 0u : 0xFFFFu) | (d8 + 2 * j + 1 < dmax ? 0u : 0xFFFF0000u);
+        // the next column's entering and leaving rows are loaded one column ahead
+        uint4 tn = make_uint4(0u, 0u, 0u, 0u), to = tn;
+        if (lane_on && rr0 + 1 < rr1) {
+          tn = *reinterpret_cast<const uint4 *>(T + (rr0 + 1 + R) * kTP + d8);
+          to = *reinterpret_cast<const uint4 *>(T + (rr0 - R) * kTP + d8);
+        }
+#pragma unroll 2
         for (int rr = rr0; rr < rr1; ++rr) {
-          if (rr > rr0 && lane_on) {
-            const uint4 tn = *reinterpret_cast<const uint4 *>(T + (rr + R) * kTP + d8);
-            const uint4 to = *reinterpret_cast<const uint4 *>(T + (rr - R - 1) * kTP + d8);
+          if (rr > rr0) {
             s4[0] += tn.x - to.x; s4[1] += tn.y - to.y; s4[2] += tn.z - to.z; s4[3] += tn.w - to.w;
+            if (lane_on && rr + 1 < rr1) {
+              tn = *reinterpret_cast<const uint4 *>(T + (rr + 1 + R) * kTP + d8);
+              to = *reinterpret_cast<const uint4 *>(T + (rr - R) * kTP + d8);
+            }
           }
           uint32_t key;
           if constexpr (PK) {
