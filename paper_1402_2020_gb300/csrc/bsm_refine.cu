@@ -59,10 +59,14 @@ __device__ __forceinline__ void load_vote_tables(const uint32_t *Ec, const uint3
 }
 
 // One 32 x 8 block with top-left corner (x0, y0); `tabs` holds the vote tables, `work` the tile.
-// Every thread of the CTA reaches its two CTA-wide barriers.
+// Every thread of the CTA reaches its two CTA-wide barriers. RT > 0: the window radius is RT (the
+// window's 2 RT + 1 <= 32 columns are lanes and its rows an unrolled loop, so every shared-memory
+// address is a per-lane base plus a constant); RT == 0: any radius, a.R.
+template <int RT>
 __device__ __forceinline__ void refine_tile(const RefineArgs &a, int x0, int y0, const uint32_t *tabs,
                                             uint32_t *work) {
-  const int R = a.R, side = 2 * R + 1;
+  static_assert(RT == 0 || 2 * RT + 1 <= 32, "one lane per window column");
+  const int R = RT > 0 ? RT : a.R, side = 2 * R + 1;
   const int tp = kTX + 2 * R, th = kTY + 2 * R;
   const uint32_t *sEc = tabs;
   const uint32_t *sEs = tabs + (kMaxSad + 1);
@@ -108,6 +112,8 @@ __device__ __forceinline__ void refine_tile(const RefineArgs &a, int x0, int y0,
 
   const int count = *s_count;
   uint32_t *hist = shist + warp * a.hist_stride;
+  // Es of window column `lane`: row wy at the constant offset (wy - RT)^2
+  const uint32_t *es = sEs + (RT > 0 && lane < 2 * RT + 1 ? (lane - RT) * (lane - RT) : 0);
   for (int it = warp; it < count; it += kWarps) {
     const int t = s_list[it];
     const int tx = t & (kTX - 1), ty = t / kTX;
@@ -115,7 +121,29 @@ __device__ __forceinline__ void refine_tile(const RefineArgs &a, int x0, int y0,
     for (int d = lane; d < a.dmax; d += 32) hist[d] = 0;
     __syncwarp();
     const uint32_t labx = slab[(ty + R) * tp + tx + R];
-    for (int wx = lane; wx < side; wx += 32) {
+    if constexpr (RT > 0) {
+      if (lane < 2 * RT + 1) {
+        const int16_t *dcol = sd + ty * tp + tx + lane;
+        const uint32_t *lcol = slab + ty * tp + tx + lane;
+        int run_d = -1;
+        uint32_t run = 0;
+#pragma unroll
+        for (int wy = 0; wy < 2 * RT + 1; ++wy) {
+          const int dv = dcol[wy * tp];
+          if (dv >= 0) {
+            const uint32_t v = (sEc[lab_sad(labx, lcol[wy * tp])] * es[(wy - RT) * (wy - RT)]) >> kVoteShift;
+            if (dv != run_d) {
+              if (run) atomicAdd(&hist[run_d], run);
+              run_d = dv;
+              run = 0;
+            }
+            run += v;
+          }
+        }
+        if (run) atomicAdd(&hist[run_d], run);
+      }
+    }
+    for (int wx = lane; RT == 0 && wx < side; wx += 32) {
       const int dx2 = (wx - R) * (wx - R);
       const int16_t *dcol = sd + ty * tp + tx + wx;  // window row 0 of this column
       const uint32_t *lcol = slab + ty * tp + tx + wx;
@@ -202,13 +230,17 @@ size_t tile_bytes(int R, int hist_stride) {
          (size_t)kTX * kTY * 2;
 }
 
+constexpr int kRFast = 15;  // the radius with an unrolled window walk (the paper's setting)
+
+template <int RT>
 __global__ void __launch_bounds__(kTX *kTY) refine_kernel(const RefineArgs a, const uint32_t *Ec, const uint32_t *Es) {
   extern __shared__ __align__(16) uint32_t smem[];
   load_vote_tables(Ec, Es, a.R, smem);
-  refine_tile(a, blockIdx.x * kTX, blockIdx.y * kTY, smem, smem + table_words(a.R));
+  refine_tile<RT>(a, blockIdx.x * kTX, blockIdx.y * kTY, smem, smem + table_words(a.R));
 }
 
 // Batched refinement: persistent CTAs take (pair, block) tickets.
+template <int RT>
 __global__ void __launch_bounds__(kTX *kTY) refine_batch_kernel(BatchHeader *hdr, const BatchPair *pairs,
                                                                const uint32_t *Ec, const uint32_t *Es,
                                                                const uint32_t *table, int tol, int R,
@@ -233,7 +265,7 @@ __global__ void __launch_bounds__(kTX *kTY) refine_batch_kernel(BatchHeader *hdr
     const int r = tk - p.ref_base, ty = r / p.ref_tx, tx = r - ty * p.ref_tx;
     RefineArgs a{p.rgb[0], p.plane[0], table, p.disp[0], p.disp[1], p.out, p.w, p.h, p.pitch, p.dmax,
                  tol, R, hist_stride, true};
-    refine_tile(a, tx * kTX, ty * kTY, smem, smem + table_words(R));
+    refine_tile<RT>(a, tx * kTX, ty * kTY, smem, smem + table_words(R));
   }
 }
 
@@ -245,20 +277,22 @@ cudaError_t launch_refine(const bsm_ctx *ctx, const uint8_t *rgb, int pitch, con
   RefineArgs a{rgb, nullptr, ctx->color_table, const_cast<int32_t *>(dL), const_cast<int32_t *>(dR), out, w, h, pitch,
                dmax, ctx->p.lr_tol, ctx->p.vote_radius, dmax, false};
   const size_t smem = table_words(a.R) * 4 + tile_bytes(a.R, dmax);
-  cudaError_t e = cudaFuncSetAttribute(refine_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  auto kern = a.R == kRFast ? refine_kernel<kRFast> : refine_kernel<0>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   dim3 grid((w + kTX - 1) / kTX, (h + kTY - 1) / kTY);
-  refine_kernel<<<grid, kTX * kTY, smem, s>>>(a, ctx->vote_ec, ctx->vote_es);
+  kern<<<grid, kTX * kTY, smem, s>>>(a, ctx->vote_ec, ctx->vote_es);
   return cudaGetLastError();
 }
 
 cudaError_t prepare_refine_batch(const bsm_ctx *ctx, int *grid) {
   const int R = ctx->p.vote_radius, hs = ctx->p.dmax;
   const size_t smem = table_words(R) * 4 + tile_bytes(R, hs);
-  cudaError_t e = cudaFuncSetAttribute(refine_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  auto kern = R == kRFast ? refine_batch_kernel<kRFast> : refine_batch_kernel<0>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, refine_batch_kernel, kTX * kTY, smem);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kTX * kTY, smem);
   *grid = max(1, per_sm) * ctx->sms;
   return e;
 }
@@ -267,8 +301,8 @@ cudaError_t launch_refine_batch(const bsm_ctx *ctx, BatchHeader *hdr, const Batc
                                 cudaStream_t s) {
   const int R = ctx->p.vote_radius, hs = ctx->p.dmax;
   const size_t smem = table_words(R) * 4 + tile_bytes(R, hs);
-  refine_batch_kernel<<<grid, kTX * kTY, smem, s>>>(hdr, pairs, ctx->vote_ec, ctx->vote_es, ctx->color_table,
-                                                    ctx->p.lr_tol, R, hs);
+  auto kern = R == kRFast ? refine_batch_kernel<kRFast> : refine_batch_kernel<0>;
+  kern<<<grid, kTX * kTY, smem, s>>>(hdr, pairs, ctx->vote_ec, ctx->vote_es, ctx->color_table, ctx->p.lr_tol, R, hs);
   return cudaGetLastError();
 }
 
