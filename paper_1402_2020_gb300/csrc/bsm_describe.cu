@@ -255,12 +255,11 @@ __device__ __forceinline__ void describe_warp_tile(const DescribeArgs &a, const 
   for (int px = 0; px < npx; ++px) {
     const uint32_t *c = row + px;  // the same for every lane
     const uint32_t cw = *c;
-    uint32_t bword = 0, w[NW];
+    uint32_t bw[NW], w[NW];  // the descriptor words are warp-wide ballots: every lane holds all of them
 #pragma unroll
     for (int j = 0; j < NW; ++j) {
       const uint32_t pw = c[op[j]], qw = c[oq[j]];
-      const uint32_t bits = __ballot_sync(0xFFFFFFFFu, pw > (qw | kLabMask));
-      bword = lane == j ? bits : bword;
+      bw[j] = __ballot_sync(0xFFFFFFFFu, pw > (qw | kLabMask));
       w[j] = max(lab_sad(cw, pw), lab_sad(cw, qw));
     }
     uint32_t wv[NH];
@@ -287,19 +286,26 @@ __device__ __forceinline__ void describe_warp_tile(const DescribeArgs &a, const 
       if (total >= a.k) hi = mid;
       else lo = mid + 1;
     }
-    const uint32_t tb = 0x6400u | lo;
-    uint32_t fword = 0;
+    const uint32_t tb = (0x6400u | lo) * 0x10001u;  // fp16 1024 + T in both halves
+    uint32_t fw[NW];
 #pragma unroll
-    for (int m = 0; m < NH; ++m) {
-      const uint32_t f0 = __ballot_sync(0xFFFFFFFFu, (wv[m] & 0xFFFFu) <= tb);
-      const uint32_t f1 = __ballot_sync(0xFFFFFFFFu, (wv[m] >> 16) <= tb);
-      fword = lane == 2 * m ? f0 : fword;
-      fword = lane == 2 * m + 1 ? f1 : fword;
-    }
-    if (lane < NW) {
-      const size_t o = ((size_t)y * a.w + x0 + px) * NW + lane;
-      a.B[o] = bword;
-      a.Phi[o] = fword;
+    for (int m = 0; m < NH; ++m)  // one fp16x2 compare sets the predicates of pairs 2 m (low) and 2 m + 1
+      asm("{\n.reg .pred p, q;\nsetp.le.f16x2 p|q, %2, %3;\nvote.sync.ballot.b32 %0, p, 0xffffffff;\n"
+          "vote.sync.ballot.b32 %1, q, 0xffffffff;\n}"
+          : "=r"(fw[2 * m]), "=r"(fw[2 * m + 1])
+          : "r"(wv[m]), "r"(tb));
+    if (lane == 0) {  // the pixel's NW words of B and of Phi as vector stores (the planes are 16-byte aligned)
+      uint32_t *ob = a.B + ((size_t)y * a.w + x0 + px) * NW, *of = a.Phi + ((size_t)y * a.w + x0 + px) * NW;
+      if constexpr (NW == 2) {
+        *reinterpret_cast<uint2 *>(ob) = make_uint2(bw[0], bw[1]);
+        *reinterpret_cast<uint2 *>(of) = make_uint2(fw[0], fw[1]);
+      } else {
+#pragma unroll
+        for (int v = 0; v < NW / 4; ++v) {
+          reinterpret_cast<uint4 *>(ob)[v] = make_uint4(bw[4 * v], bw[4 * v + 1], bw[4 * v + 2], bw[4 * v + 3]);
+          reinterpret_cast<uint4 *>(of)[v] = make_uint4(fw[4 * v], fw[4 * v + 1], fw[4 * v + 2], fw[4 * v + 3]);
+        }
+      }
     }
   }
 }

@@ -78,23 +78,47 @@ __device__ __forceinline__ void refine_tile(const RefineArgs &a, int x0, int y0,
 
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   if (threadIdx.x == 0) *s_count = 0;
-  for (int i = threadIdx.x; i < th * tp; i += blockDim.x) {
-    const int ty = i / tp, tx = i - ty * tp;
-    const int gx = x0 + tx - R, gy = y0 + ty - R;
-    int16_t dv = -1;
-    uint32_t lab = 0;
-    if (gx >= 0 && gx < a.w && gy >= 0 && gy < a.h) {
-      if (a.plane != nullptr) {
-        lab = __ldg(a.plane + (size_t)gy * a.w + gx) & kLabMask;
-      } else {
-        const uint8_t *px = a.rgb + (size_t)gy * a.pitch + 3 * gx;
-        lab = __ldg(a.table + (((uint32_t)px[0] << 16) | ((uint32_t)px[1] << 8) | (uint32_t)px[2])) & kLabMask;
+  // Staging, kSG entries per thread at a time: each level of dependent loads (colour bytes and dL, then
+  // the colour table and dR) is issued for all of them before any result is used.
+  constexpr int kSG = 4;
+  for (int i0 = threadIdx.x; i0 < th * tp; i0 += kSG * (int)blockDim.x) {
+    int gx[kSG], gy[kSG], d[kSG];
+    bool in[kSG];
+    uint32_t key[kSG];
+#pragma unroll
+    for (int u = 0; u < kSG; ++u) {
+      const int i = i0 + u * (int)blockDim.x;
+      const int ty = i / tp, tx = i - ty * tp;
+      gx[u] = x0 + tx - R;
+      gy[u] = y0 + ty - R;
+      in[u] = i < th * tp && gx[u] >= 0 && gx[u] < a.w && gy[u] >= 0 && gy[u] < a.h;
+      key[u] = 0;
+      d[u] = a.dmax;
+      if (in[u]) {
+        const size_t o = (size_t)gy[u] * a.w + gx[u];
+        if (a.plane != nullptr) {
+          key[u] = __ldg(a.plane + o);
+        } else {
+          const uint8_t *px = a.rgb + (size_t)gy[u] * a.pitch + 3 * gx[u];
+          key[u] = ((uint32_t)px[0] << 16) | ((uint32_t)px[1] << 8) | (uint32_t)px[2];
+        }
+        d[u] = disp_at(a.dL, o);
       }
-      const int d = disp_at(a.dL, (size_t)gy * a.w + gx);
-      if (d < a.dmax && lr_valid(a, gx, gy, d)) dv = (int16_t)d;
     }
-    slab[i] = lab;
-    sd[i] = dv;
+    bool ok[kSG];
+#pragma unroll
+    for (int u = 0; u < kSG; ++u) {
+      ok[u] = in[u] && d[u] < a.dmax && lr_valid(a, gx[u], gy[u], d[u]);
+      if (in[u] && a.plane == nullptr) key[u] = __ldg(a.table + key[u]);
+    }
+#pragma unroll
+    for (int u = 0; u < kSG; ++u) {
+      const int i = i0 + u * (int)blockDim.x;
+      if (i < th * tp) {
+        slab[i] = key[u] & kLabMask;
+        sd[i] = ok[u] ? (int16_t)d[u] : (int16_t)-1;
+      }
+    }
   }
   __syncthreads();
 
