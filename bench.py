@@ -43,6 +43,7 @@ PAIR_SEED = 11
 METRIC = "Gpix*disp/s"
 L2_FLUSH_BYTES = 256 << 20
 POPC_PER_CLK_SM = 16  # measured integer-pipe rate of POPC on sm_103a
+ALU_PER_CLK_SM = 64   # measured rate of LOP3, VABSDIFF4, DP4A, MAX and SETP on sm_103a (lanes per clock)
 SMS, MAX_SM_MHZ = 152, 2070
 
 
@@ -468,6 +469,30 @@ def measured_peaks():
         return {}
 
 
+def describe_kernel(tuning, nw):
+    """(kernel name, source file) of the describe stage the library runs (the dispatch of bsm_describe)."""
+    if nw > 8:
+        return "describe_wide_kernel", "bsm_long.cu"
+    v = tuning.get("describe_variant", 0)
+    if v == 2 or (v == 0 and nw == 8):
+        return "describe_warp_kernel", "bsm_describe.cu"
+    return "describe_kernel", "bsm_describe.cu"
+
+
+def describe_roofline(kname, pixels, n_bits, seconds, traffic):
+    """Eq. 2-7 at the ISA's minimum of 32-bit integer lane operations, 8 per sampling pair: Eq. 3's
+    comparison, Eq. 5's two 3-channel SADs (four-way absolute difference + four-way dot product each) and
+    their maximum, Eq. 7's comparison with T, and one comparison per pair for Eq. 6's k-th smallest weight
+    (a linear-time selection). Peak: the ALU pipe's lanes per clock x SMs x the maximum SM clock."""
+    ops = 8 * n_bits * pixels
+    peak = SMS * ALU_PER_CLK_SM * MAX_SM_MHZ * 1e6 / 1e9
+    achieved = ops / seconds / 1e9
+    return {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": peak, "unit": "Gop/s",
+            "frac": achieved / peak, "traffic": traffic, "work_per_launch": ops,
+            "peak_basis": f"{SMS} SMs x {ALU_PER_CLK_SM} ALU lanes/clk x {MAX_SM_MHZ} MHz",
+            "note": "one view per launch; the T search's bisection and the ballots run on top of the minimum"}
+
+
 def tensor_roofline(units, n_bits, seconds, traffic):
     """Eq. 8 as a contraction: n multiply-adds per (x, d) and reference view, against the E4M3 dense
     peak (the measured bf16 GEMM rate times the nominal fp8 / bf16 ratio of 2)."""
@@ -567,13 +592,23 @@ def run_pair(args, cfg, world, rank, local, n_bits=N_BITS, window_S=WINDOW_S, si
     tuning = bsm.bsm_get_tuning(ctx)
     kname, kfile, klaunch = cost_kernel(tuning, nw, dmax)
     bad = bad_pixel_rate(out.cpu().numpy(), gt)
-    # roofline of the dominant kernel: fused cost/aggregation/WTA, both reference views per launch
+    # rooflines: the cost stage (fused cost/aggregation/WTA, both reference views per launch) and describe
+    # (one view per launch); "roofline" is the one of the two that takes more of the step
     t_k2 = float(per[:, 2].mean()) * 1e-3
     word_ops = 2 * units * nw
     achieved = word_ops / t_k2 / 1e9
     peak = SMS * POPC_PER_CLK_SM * MAX_SM_MHZ * 1e6 / 1e9
     workload_key = args.config if n_bits == N_BITS else f"{args.config}_n{n_bits}"
     traffic = profile_traffic(kfile, workload_key)
+    dname, dfile = describe_kernel(tuning, nw)
+    t_desc = float((per[:, 0] + per[:, 1]).mean()) * 1e-3  # two launches
+    roof_desc = describe_roofline(dname, w * h, n_bits, t_desc / 2, profile_traffic(dfile, workload_key))
+    roof_cost = ({"bound": "alu", "kernel": kname, "achieved": achieved, "peak": peak,
+                  "unit": "Gpopc/s", "frac": achieved / peak, "traffic": traffic,
+                  "work_per_launch": word_ops,
+                  "peak_basis": f"{SMS} SMs x {POPC_PER_CLK_SM} POPC/clk x {MAX_SM_MHZ} MHz"}
+                 if kname != "cost_tc_kernel" else tensor_roofline(units, n_bits, t_k2, traffic))
+    describe_dominant = t_desc > t_k2
     line = {
         "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_step, "higher_is_better": True, "scaling": "weak",
@@ -589,17 +624,16 @@ def run_pair(args, cfg, world, rank, local, n_bits=N_BITS, window_S=WINDOW_S, si
         "bad_pixel_rate": bad,  # |d - d_gt| > 1 against the generator's ground truth, rank 0's pair
         # colour pre-pass + describe per view, the cost stage's kernels, refine
         "gpu_launches": (4 + klaunch + 1 + (2 * sgm[2] if sgm else 0)) * args.steps,
-        "roofline": ({"bound": "alu", "kernel": kname, "achieved": achieved, "peak": peak,
-                      "unit": "Gpopc/s", "frac": achieved / peak, "traffic": traffic,
-                      "work_per_launch": word_ops,
-                      "peak_basis": f"{SMS} SMs x {POPC_PER_CLK_SM} POPC/clk x {MAX_SM_MHZ} MHz"}
-                     if kname != "cost_tc_kernel" else tensor_roofline(units, n_bits, t_k2, traffic)),
+        "roofline": roof_desc if describe_dominant else roof_cost,
+        ("roofline_cost" if describe_dominant else "roofline_describe"): roof_cost if describe_dominant else roof_desc,
         "clocks": clocks,
         "tuning": tuning,
     }
     if sgm:
         line["config"]["sgm"] = {"P1": sgm[0], "P2": sgm[1], "paths": sgm[2]}
-        line["roofline"] = None  # the cost stage also holds both views' semi-global aggregation
+        # the cost stage also holds both views' semi-global aggregation
+        line["roofline"] = roof_desc if describe_dominant else None
+        line.pop("roofline_cost", None)
     if e2e and not sgm:
         # end to end through the host-buffer C-ABI call (H2D of both views and D2H of the map inside)
         hl = torch.from_numpy(left).pin_memory()
