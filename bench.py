@@ -453,7 +453,7 @@ def cost_kernel(tuning, nw, dmax):
         return "cost_long_kernel", "bsm_long.cu", 1
     v = tuning["cost_variant"]
     if v == 3:
-        return "cost_tc_kernel", "bsm_cost_tc.cu", 2  # + the E4M3 operand-plane pass
+        return "cost_tc_kernel", "bsm_cost_tc.cu", 1
     if v == 2 or (v == 0 and nw in (4, 8)):
         need = (dmax + 7) // 8
         split = (need + min(16, need) - 1) // min(16, need) > 1
@@ -502,8 +502,8 @@ def tensor_roofline(units, n_bits, seconds, traffic):
     achieved = flops / seconds / 1e12
     return {"bound": "tensor", "kernel": "cost_tc_kernel", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
             "frac": achieved / peak, "traffic": traffic, "work_per_launch": flops, "peak_basis": basis,
-            "note": "stage time including the E4M3 operand-plane pass; the MMAs also run the window's entering "
-                    "and leaving rows and the band around the disparity range"}
+            "note": "one launch covers both reference views; the MMAs also run the window's entering and leaving "
+                    "rows and the band around the disparity range"}
 
 
 def run_pair(args, cfg, world, rank, local, n_bits=N_BITS, window_S=WINDOW_S, sigma=None, agg=AGG, e2e=True,

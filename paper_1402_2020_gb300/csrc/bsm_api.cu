@@ -35,18 +35,6 @@ void srgb_linear_table(double *lin) {
 
 // Grow the context's colour-plane scratch to at least `pixels` words. Growing waits for all work on
 // the device, because earlier calls may still read the old plane.
-// Scratch of the tensor-core cost kernel for a w x h pair (grown on demand; synchronous when it grows).
-cudaError_t ensure_tc(bsm_ctx *ctx, int w, int h) {
-  if (ctx->cost_variant != 3 || !bsm::cost_tc_supported(ctx)) return cudaSuccess;
-  const size_t need = bsm::cost_tc_scratch_bytes(w, h);
-  if (ctx->tc_ws_bytes >= need) return cudaSuccess;
-  cudaFree(ctx->tc_ws);
-  ctx->tc_ws = nullptr;
-  ctx->tc_ws_bytes = 0;
-  const cudaError_t e = cudaMalloc(&ctx->tc_ws, need);
-  if (e == cudaSuccess) ctx->tc_ws_bytes = need;
-  return e;
-}
 
 cudaError_t ensure_plane(bsm_ctx *ctx, size_t pixels) {
   if (ctx->plane_px >= pixels) return cudaSuccess;
@@ -124,7 +112,6 @@ void bsm_destroy(bsm_ctx *ctx) {
   cudaFree(ctx->status);
   cudaFree(ctx->wide_offs);
   cudaFree(ctx->ws);
-  cudaFree(ctx->tc_ws);
   cudaFree(ctx->plane);
   if (ctx->batch_graph) cudaGraphExecDestroy(ctx->batch_graph);
   if (ctx->batch_copied) cudaEventDestroy(ctx->batch_copied);
@@ -218,8 +205,6 @@ bsm_status bsm_cost_aggregate_wta(bsm_ctx *ctx, const uint32_t *BL, const uint32
     return BSM_ERR_INVALID_ARG;
   if (!size_ok(w, h) || dmax < 1 || dmax > ctx->p.dmax) return BSM_ERR_INVALID_ARG;
   if (!aligned16(BL) || !aligned16(PhiL) || !aligned16(BR) || !aligned16(PhiR)) return BSM_ERR_INVALID_ARG;
-  const cudaError_t e = ensure_tc(ctx, w, h);
-  if (e != cudaSuccess) return from_cuda(ctx, e);
   return from_cuda(ctx, bsm::launch_cost_wta(ctx, BL, PhiL, BR, PhiR, w, h, dmax, dispL, dispR, costL_or_null,
                                              nullptr, (cudaStream_t)stream));
 }
@@ -232,8 +217,6 @@ bsm_status bsm_cost_volumes(bsm_ctx *ctx, const uint32_t *BL, const uint32_t *Ph
     return BSM_ERR_INVALID_ARG;
   if (!size_ok(w, h) || dmax < 1 || dmax > ctx->p.dmax) return BSM_ERR_INVALID_ARG;
   if (!aligned16(BL) || !aligned16(PhiL) || !aligned16(BR) || !aligned16(PhiR)) return BSM_ERR_INVALID_ARG;
-  const cudaError_t e = ensure_tc(ctx, w, h);
-  if (e != cudaSuccess) return from_cuda(ctx, e);
   return from_cuda(ctx, bsm::launch_cost_wta(ctx, BL, PhiL, BR, PhiR, w, h, dmax, dispL, dispR, costL, costR,
                                              (cudaStream_t)stream));
 }
@@ -266,7 +249,6 @@ bsm_status bsm_match_host(bsm_ctx *ctx, const uint8_t *rgbL_host, const uint8_t 
   const size_t need = 2 * img + 4 * plane + 3 * map;
   cudaStream_t s = (cudaStream_t)stream;
   cudaError_t e = ensure_plane(ctx, (size_t)w * h);
-  if (e == cudaSuccess) e = ensure_tc(ctx, w, h);
   if (e != cudaSuccess) return from_cuda(e);
   if (ctx->ws_bytes < need) {
     e = cudaStreamSynchronize(s);

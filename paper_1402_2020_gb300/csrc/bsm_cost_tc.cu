@@ -9,25 +9,25 @@
 // E4M3 operands +-2^-6 and 2^-6, fp32 accumulation in TMEM: every value is an integer times 2^-12
 // below 2^11, so the products and sums are exact.
 //
-// 1. tc_expand_kernel writes, per view, the E4M3 plane S of the s bytes in a K-group-major layout
-//    [y][16 groups of 16 K bytes][x][16 bytes], and popcount(Phi AND B) per pixel. The K order within a
-//    32-bit word is a fixed permutation of its bits (byte k of output word q is bit 8k + q), the same
-//    for both operands.
-// 2. cost_tc_kernel, one CTA per (128 reference columns, band of rows, reference view), 18 warps:
+// One launch, cost_tc_kernel, one CTA per (128 reference columns, band of rows, reference view), 20 warps;
+// the K order within a 32-bit descriptor word is a fixed permutation of its bits (byte k of operand word
+// q is bit 8k + q), the same for both operands:
 //    - warp 0 (producer) loads, by TMA, the other view's descriptor words of the entering and the
-//      leaving row (32 bytes per band column) and, per 64-byte K chunk, the A operand (4 groups x 128
-//      columns of S); the tensor maps fill columns outside the image with zeros;
-//    - warps 2..5 build each chunk's B operand (4 groups x up to 384 band columns of o bytes, 2^-6
-//      where the bit is set) from those words in shared memory;
+//      leaving row (32 bytes per band column); the tensor maps fill columns outside the image with zeros;
+//    - warps 2..7 (builders) form each 64-byte K chunk's operands in shared memory: A (4 groups x 128
+//      reference columns of s bytes, +-2^-6 where the mask bit is set, from the reference view's B and
+//      Phi words, read from global memory one row half ahead) and B (4 groups x up to 384 band columns
+//      of o bytes, 2^-6 where the bit is set, from the TMA'd words); they also keep each column's window
+//      popcount(Phi AND B) and publish it per input row in a small ring;
 //    - warp 1 owns the TMEM accumulator and issues the MMAs (2 k-steps x 2 N-blocks per chunk), commits
 //      each chunk to its buffer's "empty" barrier and each finished output row to "acc_full"; before the
 //      next row's MMAs it waits until the epilogue has read the accumulator;
-//    - warps 6..17 (epilogue) read their lane quadrant of the accumulator (tcgen05.ld 32x32b.x32) and
-//      write term(x, d) = V(x, x_d) + the window's popcount(Phi AND B) of column x (or the sentinel n
-//      per in-image row when the match leaves the image) into a shared [x][d] table, release the
-//      accumulator, then slide the horizontal box sum along x on packed 16-bit pairs and reduce
-//      (A << 3 | d % 8) keys with min.u16x2 and one warp-wide minimum of (A << 8 | d): Eq. 1's
-//      smallest d. This pass overlaps the next row's MMAs.
+//    - warps 8..19 (epilogue) read their lane quadrant of the accumulator (tcgen05.ld 32x32b.x32) into
+//      registers as 16-bit term(x, d) = V(x, x_d) + the window's popcount(Phi AND B) of column x (or the
+//      sentinel n per in-image row when the match leaves the image), release the accumulator, write the
+//      terms into a shared [x][d] table, then slide the horizontal box sum along x on packed 16-bit pairs
+//      and reduce (A << 3 | d % 8) keys with min.u16x2 and one warp-wide minimum of (A << 8 | d): Eq. 1's
+//      smallest d. This overlaps the next row's MMAs.
 // Every wait is bounded; a wait that gives up latches BSM_ERR_TIMEOUT and the CTA winds down.
 #include <cuda.h>
 #include <cudaTypedefs.h>
@@ -41,10 +41,14 @@ constexpr int kTM = 128;          // reference columns per CTA: MMA M, TMEM lane
 constexpr int kNB = 384;          // B operand rows: the band of 128 + 256 - 1 other-view columns
 constexpr int kChunk = 64;        // K bytes per operand chunk: 4 K groups of 16 bytes (2 descriptor words)
 constexpr int kBuf = 3;           // operand buffers
-constexpr int kWarps = 18;        // producer, MMA, 4 B-operand builders, 12 epilogue warps
+constexpr int kBW = 6;            // operand builder warps (warps 2 .. kBW + 1)
+constexpr int kE0 = 2 + kBW;      // first epilogue warp
+constexpr int kWarps = kE0 + 12;  // producer, MMA, builders, 12 epilogue warps (3 per TMEM lane quadrant)
 constexpr int kThreads = 32 * kWarps;
-constexpr int kXpd = 4 * 32;      // B-operand builder threads (warps 2..5)
-constexpr int kEpi = 12 * 32;     // epilogue threads (warps 6..17)
+constexpr int kXpd = kBW * 32;    // operand builder threads
+constexpr int kBC = (kNB + kXpd - 1) / kXpd;  // B-operand band columns per builder thread
+static_assert(kXpd >= kTM, "one builder thread per A row");
+constexpr int kEpi = 12 * 32;     // epilogue threads (warps kE0 .. kE0 + 11)
 constexpr int kTP = 288;          // u16 pitch of the term table T[x][d] (rows 16-byte aligned)
 constexpr int kTPad = 32;         // u16 in front of row 0; row r's band terms past d = 255 land in row r + 1's first 32
 constexpr int kAB = kTM * kChunk;         // A chunk: 4 groups x 128 rows x 16 bytes
@@ -55,8 +59,10 @@ constexpr int kOffOp = 0;
 constexpr int kOffRaw = kOffOp + kBuf * kOpB;          // 2 slots x (entering, leaving) rows
 constexpr int kOffT = kOffRaw + 2 * 2 * kRawRow;
 constexpr int kOffC0 = kOffT + (kTM * kTP + kTPad) * 2;
-constexpr int kOffMisc = kOffC0 + kTM * 4;
-constexpr int kSmem = kOffMisc + 128;
+constexpr int kC0Ring = 8;        // rows of window popcounts in flight between builders and epilogue
+constexpr int kOffRing = kOffC0 + kTM * 4;
+constexpr int kOffMisc = kOffRing + kC0Ring * kTM * 4;
+constexpr int kSmem = kOffMisc + 256;
 static_assert(kSmem <= 232448, "shared memory of one CTA");
 static_assert(kOffRaw % 1024 == 0 && kOffT % 1024 == 0 && kOffC0 % 16 == 0 && kOffMisc % 16 == 0 && (kTP * 2) % 16 == 0 &&
                   (kTPad * 2) % 16 == 0 && kTP >= 256 + kTPad,
@@ -64,10 +70,10 @@ static_assert(kOffRaw % 1024 == 0 && kOffT % 1024 == 0 && kOffC0 % 16 == 0 && kO
 constexpr long long kWait = 1LL << 31;  // about one second at the GB300 clock
 
 struct TcArgs {
-  CUtensorMap smap[2];    // S planes (A operand), box 16 bytes x 128 columns x 4 groups; per reference view
   CUtensorMap bmap0[2];   // descriptor plane of the other view, box 32 bytes x 256 columns x 1 row
   CUtensorMap bmap1[2];   // the same, box 32 bytes x 128 columns x 1 row
-  const uint16_t *c0[2];  // popcount(Phi AND B) per pixel of the reference view
+  const uint32_t *Bv[2];  // descriptor plane of the reference view, [h][w][8], per reference view
+  const uint32_t *Pv[2];  // mask plane of the reference view
   int32_t *disp[2];
   uint16_t *cost[2];
   uint32_t *status;
@@ -173,39 +179,6 @@ __device__ __forceinline__ uint32_t spread(uint32_t w) {
   else return (w >> (-sh)) & mask;
 }
 
-// ---------------------------------------------------------------- operand planes
-
-// One thread per pixel: S bytes of the 16 K groups (2 per descriptor word) and popcount(Phi AND B).
-// s = +-2^-6 (0x08 / 0x88) where the mask bit is set, signed by the descriptor bit.
-__global__ void __launch_bounds__(128) tc_expand_kernel(const uint32_t *__restrict__ B0, const uint32_t *__restrict__ P0,
-                                                        const uint32_t *__restrict__ B1, const uint32_t *__restrict__ P1,
-                                                        uint4 *S0, uint16_t *c00, uint4 *S1, uint16_t *c01, int w, int h) {
-  const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y, v = blockIdx.z;
-  if (x >= w) return;
-  const uint32_t *Bp = v ? B1 : B0, *Pp = v ? P1 : P0;
-  uint4 *S = v ? S1 : S0;
-  uint16_t *c0 = v ? c01 : c00;
-  const size_t pix = (size_t)y * w + x;
-  const uint4 b01 = __ldg(reinterpret_cast<const uint4 *>(Bp + pix * 8));
-  const uint4 b23 = __ldg(reinterpret_cast<const uint4 *>(Bp + pix * 8 + 4));
-  const uint4 m01 = __ldg(reinterpret_cast<const uint4 *>(Pp + pix * 8));
-  const uint4 m23 = __ldg(reinterpret_cast<const uint4 *>(Pp + pix * 8 + 4));
-  const uint32_t bw[8] = {b01.x, b01.y, b01.z, b01.w, b23.x, b23.y, b23.z, b23.w};
-  const uint32_t mw[8] = {m01.x, m01.y, m01.z, m01.w, m23.x, m23.y, m23.z, m23.w};
-  int pc = 0;
-#pragma unroll
-  for (int j = 0; j < 8; ++j) {
-    const uint32_t m = mw[j], sb = m & bw[j];
-    pc += __popc(sb);
-    const size_t g0 = ((size_t)y * 16 + 2 * j) * w + x, g1 = g0 + w;  // K groups 2j, 2j + 1
-    S[g0] = make_uint4(spread<0, 3>(m) | spread<0, 7>(sb), spread<1, 3>(m) | spread<1, 7>(sb),
-                       spread<2, 3>(m) | spread<2, 7>(sb), spread<3, 3>(m) | spread<3, 7>(sb));
-    S[g1] = make_uint4(spread<4, 3>(m) | spread<4, 7>(sb), spread<5, 3>(m) | spread<5, 7>(sb),
-                       spread<6, 3>(m) | spread<6, 7>(sb), spread<7, 3>(m) | spread<7, 7>(sb));
-  }
-  c0[pix] = (uint16_t)pc;
-}
-
 // 32 K bytes of the B operand from one other-view word: 2^-6 (0x08) where the bit is set.
 __device__ __forceinline__ void expand_b(uint32_t o, uint8_t *dst_g0, uint8_t *dst_g1) {
   *reinterpret_cast<uint4 *>(dst_g0) =
@@ -214,15 +187,27 @@ __device__ __forceinline__ void expand_b(uint32_t o, uint8_t *dst_g0, uint8_t *d
       make_uint4(spread<4, 3>(o), spread<5, 3>(o), spread<6, 3>(o), spread<7, 3>(o));
 }
 
+// 32 K bytes of the A operand from one descriptor word b and mask word m of the reference column:
+// s = +-2^-6 (0x08, sign bit 0x80 where b is set) where m is set, 0 elsewhere.
+__device__ __forceinline__ void expand_a(uint32_t b, uint32_t m, uint8_t *dst_g0, uint8_t *dst_g1) {
+  const uint32_t sb = m & b;
+  *reinterpret_cast<uint4 *>(dst_g0) = make_uint4(spread<0, 3>(m) | spread<0, 7>(sb), spread<1, 3>(m) | spread<1, 7>(sb),
+                                                  spread<2, 3>(m) | spread<2, 7>(sb), spread<3, 3>(m) | spread<3, 7>(sb));
+  *reinterpret_cast<uint4 *>(dst_g1) = make_uint4(spread<4, 3>(m) | spread<4, 7>(sb), spread<5, 3>(m) | spread<5, 7>(sb),
+                                                  spread<6, 3>(m) | spread<6, 7>(sb), spread<7, 3>(m) | spread<7, 7>(sb));
+}
+
 // ---------------------------------------------------------------- cost kernel
 
 template <int WIN, int DIR>
 __device__ __forceinline__ void cost_tc_body(const TcArgs &a, uint8_t *smem) {
   constexpr int R = WIN / 2, OUTC = kTM - 2 * R;
   constexpr bool PK = 256 * WIN * WIN < 8192;  // aggregated costs below 2^13: 16-bit (A << 3 | dd) keys
+  static_assert(WIN + 1 <= kC0Ring, "the popcount ring holds the rows the builders may run ahead");
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const CUtensorMap *smap = &a.smap[DIR], *bmap0 = &a.bmap0[DIR], *bmap1 = &a.bmap1[DIR];
-  const uint16_t *__restrict__ c0p = DIR ? a.c0[1] : a.c0[0];
+  const CUtensorMap *bmap0 = &a.bmap0[DIR], *bmap1 = &a.bmap1[DIR];
+  const uint32_t *__restrict__ Bref = DIR ? a.Bv[1] : a.Bv[0];
+  const uint32_t *__restrict__ Pref = DIR ? a.Pv[1] : a.Pv[0];
   int32_t *__restrict__ disp = DIR ? a.disp[1] : a.disp[0];
   uint16_t *cost = DIR ? a.cost[1] : a.cost[0];
   const int w = a.w, h = a.h, dmax = a.dmax;
@@ -241,14 +226,16 @@ __device__ __forceinline__ void cost_tc_body(const TcArgs &a, uint8_t *smem) {
   uint64_t *empty = full + kBuf;                                    // [kBuf]
   uint64_t *raw_full = empty + kBuf, *raw_empty = raw_full + 2;     // [2] each
   uint64_t *acc_full = raw_empty + 2, *acc_empty = acc_full + 1;
-  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(acc_empty + 1);
+  uint64_t *c0_full = acc_empty + 1;                                // [kC0Ring]
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(c0_full + kC0Ring);
   uint32_t *abort_flag = tmem_slot + 1;
   uint16_t *T = reinterpret_cast<uint16_t *>(smem + kOffT) + kTPad;
   int32_t *c0v = reinterpret_cast<int32_t *>(smem + kOffC0);
+  int32_t *ring = reinterpret_cast<int32_t *>(smem + kOffRing);  // [kC0Ring][kTM]
 
   if (tid == 0) {
     for (int b = 0; b < kBuf; ++b) {
-      mbar_init(&full[b], 1 + kXpd / 32);  // the A copy's arrival and every builder warp
+      mbar_init(&full[b], kXpd / 32);  // every builder warp
       mbar_init(&empty[b], 1);
     }
     for (int k = 0; k < 2; ++k) {
@@ -257,6 +244,7 @@ __device__ __forceinline__ void cost_tc_body(const TcArgs &a, uint8_t *smem) {
     }
     mbar_init(acc_full, 1);
     mbar_init(acc_empty, kEpi / 32);
+    for (int k = 0; k < kC0Ring; ++k) mbar_init(&c0_full[k], kXpd / 32);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -276,9 +264,9 @@ __device__ __forceinline__ void cost_tc_body(const TcArgs &a, uint8_t *smem) {
   if (warp == 0) {
     // ---- producer: per input row the other view's words, per chunk the A operand, in order
     if (lane == 0) {
-      uint32_t slot = 0;
       const uint32_t rowbytes = (uint32_t)(256 * 32 + (nb1 > 0 ? 128 * 32 : 0));
       bool ok = true;
+      int last = -1;  // the last input row whose copies were issued
       for (int i = 0; i < n_it && ok; ++i) {
         const int rs = i & 1;
         if (i >= 2) ok = mbar_wait(&raw_empty[rs], ((i >> 1) - 1) & 1u);
@@ -293,23 +281,13 @@ __device__ __forceinline__ void cost_tc_body(const TcArgs &a, uint8_t *smem) {
             tma_load3(raw + k * kRawRow, bmap0, xb0, y, &raw_full[rs]);
             if (nb1 > 0) tma_load3(raw + k * kRawRow + 256 * 32, bmap1, xb0 + 256, y, &raw_full[rs]);
           }
+          last = i;
         } else {
           mbar_arrive(&raw_full[rs]);
         }
-        for (int c = 0; c < 8 && ok; ++c) {
-          const bool is_new = c < 4;
-          if (!(is_new ? hn : ho)) continue;
-          const int y = is_new ? y_first + i : y_first + i - (2 * R + 1);
-          const int b = (int)(slot % kBuf);
-          if (slot >= kBuf) ok = mbar_wait(&empty[b], ((slot / kBuf) - 1) & 1u);
-          if (!ok) break;
-          mbar_expect_tx(&full[b], (uint32_t)kAB);
-          tma_load3(smem + kOffOp + b * kOpB, smap, X0, y * 16 + 4 * (c & 3), &full[b]);
-          ++slot;
-        }
       }
       if (!ok) atomicExch(abort_flag, 1u);
-      if (!ok && slot > 0) mbar_wait(&full[(slot - 1) % kBuf], ((slot - 1) / kBuf) & 1u);  // let copies land
+      if (!ok && last >= 0) mbar_wait(&raw_full[last & 1], (last >> 1) & 1u);  // let the copies land
     }
   } else if (warp == 1) {
     // ---- MMA issuer
@@ -351,9 +329,36 @@ __device__ __forceinline__ void cost_tc_body(const TcArgs &a, uint8_t *smem) {
       }
       if (!ok) atomicExch(abort_flag, 1u);
     }
-  } else if (warp < 2 + kXpd / 32) {
-    // ---- B-operand builders: band column r, r + 128, r + 256 of each chunk
-    const int t = tid - 64;
+  } else if (warp < kE0) {
+    // ---- operand builders: per chunk, the A operand's row t < 128 (the s bytes of reference column X0 + t,
+    // from its descriptor and mask words) and the B operand's band columns t + kXpd j
+    const int t = tid - 64, xa = X0 + t;
+    const bool has_a = t < kTM, a_in = has_a && xa >= 0 && xa < w;
+    auto present = [&](int ii, int hh) { return hh == 0 ? row_new(ii) : row_old(ii); };
+    // the reference words of the next (row, half) with an image row are loaded one half ahead
+    auto load_ref = [&](int ii, int hh, uint4(&q)[4]) {
+      if (a_in) {
+        const int y = hh == 0 ? y_first + ii : y_first + ii - (2 * R + 1);
+        const size_t o = ((size_t)y * w + xa) * 8;
+        q[0] = __ldg(reinterpret_cast<const uint4 *>(Bref + o));
+        q[1] = __ldg(reinterpret_cast<const uint4 *>(Bref + o + 4));
+        q[2] = __ldg(reinterpret_cast<const uint4 *>(Pref + o));
+        q[3] = __ldg(reinterpret_cast<const uint4 *>(Pref + o + 4));
+      } else {
+        q[0] = q[1] = q[2] = q[3] = make_uint4(0u, 0u, 0u, 0u);  // columns off the image: s = 0
+      }
+    };
+    int ni = 0, nh = 0;
+    auto advance = [&]() {
+      do {
+        nh ^= 1;
+        if (nh == 0) ++ni;
+      } while (ni < n_it && !present(ni, nh));
+    };
+    if (!present(0, 0)) advance();
+    int c0run = 0;  // the window's popcount(Phi AND B) of column X0 + t
+    uint4 nxt[4];
+    if (ni < n_it) load_ref(ni, nh, nxt);
     uint32_t slot = 0;
     bool ok = true;
     for (int i = 0; i < n_it && ok; ++i) {
@@ -366,30 +371,45 @@ __device__ __forceinline__ void cost_tc_body(const TcArgs &a, uint8_t *smem) {
 #pragma unroll
       for (int half = 0; half < 2; ++half) {
         if (!ok || !(half == 0 ? hn : ho)) continue;
-        const uint32_t *rw = reinterpret_cast<const uint32_t *>(raw + half * kRawRow);
-        uint4 qw[3][2];
+        uint4 cur[4];  // this half's reference words: B 0..3, B 4..7, Phi 0..3, Phi 4..7
 #pragma unroll
-        for (int k = 0; k < 3; ++k) {
-          const int r = t + 128 * k;
-          if (r < ntot) {
-            qw[k][0] = *reinterpret_cast<const uint4 *>(rw + r * 8);
-            qw[k][1] = *reinterpret_cast<const uint4 *>(rw + r * 8 + 4);
-          } else {
-            qw[k][0] = qw[k][1] = make_uint4(0u, 0u, 0u, 0u);
-          }
+        for (int k = 0; k < 4; ++k) cur[k] = nxt[k];
+        advance();
+        if (ni < n_it) load_ref(ni, nh, nxt);
+        {
+          const int pc = __popc(cur[0].x & cur[2].x) + __popc(cur[0].y & cur[2].y) + __popc(cur[0].z & cur[2].z) +
+                         __popc(cur[0].w & cur[2].w) + __popc(cur[1].x & cur[3].x) + __popc(cur[1].y & cur[3].y) +
+                         __popc(cur[1].z & cur[3].z) + __popc(cur[1].w & cur[3].w);
+          c0run += half == 0 ? pc : -pc;
         }
+        const uint32_t *rw = reinterpret_cast<const uint32_t *>(raw + half * kRawRow);
+        uint4 qw[kBC];  // words 4 (cc / 2) .. 4 (cc / 2) + 3 of each of the thread's band columns
 #pragma unroll
         for (int cc = 0; cc < 4; ++cc) {  // chunk cc: descriptor words 2 cc and 2 cc + 1
           if (!ok) break;
+          if ((cc & 1) == 0) {
+#pragma unroll
+            for (int k = 0; k < kBC; ++k) {
+              const int r = t + kXpd * k;
+              qw[k] = r < ntot ? *reinterpret_cast<const uint4 *>(rw + r * 8 + 2 * cc) : make_uint4(0u, 0u, 0u, 0u);
+            }
+          }
           const int b = (int)(slot % kBuf);
           if (slot >= kBuf) ok = mbar_wait(&empty[b], ((slot / kBuf) - 1) & 1u);
           if (!ok) break;
-          uint8_t *opB = smem + kOffOp + b * kOpB + kAB;
+          uint8_t *opA = smem + kOffOp + b * kOpB, *opB = opA + kAB;
+          if (has_a) {
+            const uint4 &bq = cur[cc >> 1], &mq = cur[2 + (cc >> 1)];
+            expand_a((cc & 1) ? bq.z : bq.x, (cc & 1) ? mq.z : mq.x, opA + 0 * (kTM * 16) + t * 16,
+                     opA + 1 * (kTM * 16) + t * 16);
+            expand_a((cc & 1) ? bq.w : bq.y, (cc & 1) ? mq.w : mq.y, opA + 2 * (kTM * 16) + t * 16,
+                     opA + 3 * (kTM * 16) + t * 16);
+          }
 #pragma unroll
-          for (int k = 0; k < 3; ++k) {
-            const int r = t + 128 * k;
+          for (int k = 0; k < kBC; ++k) {
+            const int r = t + kXpd * k;
             if (r < ntot) {
-              const uint4 &qq = qw[k][cc >> 1];
+              const uint4 &qq = qw[k];
               expand_b((cc & 1) ? qq.z : qq.x, opB + 0 * (kNB * 16) + r * 16, opB + 1 * (kNB * 16) + r * 16);
               expand_b((cc & 1) ? qq.w : qq.y, opB + 2 * (kNB * 16) + r * 16, opB + 3 * (kNB * 16) + r * 16);
             }
@@ -402,24 +422,28 @@ __device__ __forceinline__ void cost_tc_body(const TcArgs &a, uint8_t *smem) {
       }
       __syncwarp();
       if (lane == 0 && ok) mbar_arrive(&raw_empty[rs]);  // this row's words are no longer needed
+      if (ok) {  // the window's popcount after input row i, for the epilogue
+        if (has_a) ring[(i & (kC0Ring - 1)) * kTM + t] = c0run;
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&c0_full[i & (kC0Ring - 1)]);
+      }
     }
     if (!ok) atomicExch(abort_flag, 1u);
   } else {
-    // ---- epilogue: warps 6..17; lane quadrant q = warp % 4, g = its index among the quadrant's warps
-    const int q = warp & 3, g = (warp - 6) >> 2, ew = warp - 6, r = 32 * q + lane, xr = X0 + r;
+    // ---- epilogue: warps kE0 .. kE0 + 11; lane quadrant q = warp % 4, g = its index among the quadrant's warps
+    const int q = warp & 3, g = (warp - kE0) >> 2, ew = warp - kE0, r = 32 * q + lane, xr = X0 + r;
     const bool col_in = xr >= 0 && xr < w;
-    int c0run = 0;  // warps with g == 0: the window's popcount(Phi AND B) of column r
     uint32_t outs = 0;
     bool ok = true;
     for (int i = 0; i < n_it && ok; ++i) {
-      const int yn = y_first + i, yold = yn - (2 * R + 1), yout = yn - R;
-      if (g == 0 && col_in) {
-        if (row_new(i)) c0run += c0p[(size_t)yn * w + xr];
-        if (row_old(i)) c0run -= c0p[(size_t)yold * w + xr];
-      }
+      const int yout = y_first + i - R;
       if (yout < yb) continue;
-      if (g == 0) c0v[r] = c0run;
-      ok = mbar_wait(acc_full, outs & 1u);
+      bool okc = true;
+      if (g == 0) {  // the builders' window popcount of column r after input row i
+        okc = mbar_wait(&c0_full[i & (kC0Ring - 1)], (uint32_t)(i / kC0Ring) & 1u);
+        c0v[r] = col_in ? ring[(i & (kC0Ring - 1)) * kTM + r] : 0;
+      }
+      ok = mbar_wait(acc_full, outs & 1u) && okc;
       if (*reinterpret_cast<volatile uint32_t *>(abort_flag) != 0) ok = false;  // the other roles gave up
       ++outs;
       // c0v published; the previous row's horizontal pass is done with T; all agree on ok
@@ -566,7 +590,7 @@ __device__ __forceinline__ void cost_tc_body(const TcArgs &a, uint8_t *smem) {
         }
       }
     }
-    if (!ok && tid == 6 * 32) atomicCAS(a.status, 0u, (uint32_t)BSM_ERR_TIMEOUT);
+    if (!ok && tid == kE0 * 32) atomicCAS(a.status, 0u, (uint32_t)BSM_ERR_TIMEOUT);
   }
   if (tid == 0 && *abort_flag != 0) atomicCAS(a.status, 0u, (uint32_t)BSM_ERR_TIMEOUT);
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -612,19 +636,6 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   return fn;
 }
 
-// Operand plane [h][16][w][16 bytes] as a 3-D byte tensor (16, w, 16 h); box 16 x cols x 4.
-bool plane_map(CUtensorMap *map, void *base, int w, int h, int cols) {
-  auto fn = encode_fn();
-  if (fn == nullptr) return false;
-  const cuuint64_t dims[3] = {16, (cuuint64_t)w, (cuuint64_t)16 * h};
-  const cuuint64_t strides[2] = {16, (cuuint64_t)16 * w};
-  const cuuint32_t box[3] = {16, (cuuint32_t)cols, 4};
-  const cuuint32_t elem[3] = {1, 1, 1};
-  return fn(map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 3, base, dims, strides, box, elem, CU_TENSOR_MAP_INTERLEAVE_NONE,
-            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
-}
-
 // Descriptor plane [h][w][8 words] as a 3-D byte tensor (32, w, h); box 32 x cols x 1.
 bool desc_map(CUtensorMap *map, const void *base, int w, int h, int cols) {
   auto fn = encode_fn();
@@ -638,39 +649,20 @@ bool desc_map(CUtensorMap *map, const void *base, int w, int h, int cols) {
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-size_t round256(size_t b) { return (b + 255) & ~(size_t)255; }
-
 }  // namespace
 
 bool cost_tc_supported(const bsm_ctx *ctx) { return ctx->nw == 8 && ctx->p.mask_mode != BSM_MASK_BOTH; }
 
-// Scratch of one call: S planes of both views (256 bytes per pixel) and popcount planes.
-size_t cost_tc_scratch_bytes(int w, int h) {
-  const size_t px = (size_t)w * h;
-  return 2 * round256(px * 256) + 2 * round256(px * 2);
-}
-
 cudaError_t launch_cost_tc(const bsm_ctx *ctx, const uint32_t *BL, const uint32_t *PhiL, const uint32_t *BR,
                            const uint32_t *PhiR, int w, int h, int dmax, int32_t *dL, int32_t *dR, uint16_t *costL,
                            uint16_t *costR, cudaStream_t s) {
-  const size_t px = (size_t)w * h;
-  if (ctx->tc_ws == nullptr || ctx->tc_ws_bytes < cost_tc_scratch_bytes(w, h)) return cudaErrorInvalidValue;
-  uint8_t *base = static_cast<uint8_t *>(ctx->tc_ws);
-  uint8_t *SL = base, *SR = SL + round256(px * 256);
-  uint16_t *cL = reinterpret_cast<uint16_t *>(SR + round256(px * 256));
-  uint16_t *cR = reinterpret_cast<uint16_t *>(reinterpret_cast<uint8_t *>(cL) + round256(px * 2));
-  dim3 eg((w + 127) / 128, h, 2);
-  tc_expand_kernel<<<eg, 128, 0, s>>>(BL, PhiL, BR, PhiR, reinterpret_cast<uint4 *>(SL), cL,
-                                      reinterpret_cast<uint4 *>(SR), cR, w, h);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
   TcArgs a{};
-  // left reference: A = S of the left view, B from the right view's descriptors; right reference the other way
-  if (!plane_map(&a.smap[0], SL, w, h, 128) || !plane_map(&a.smap[1], SR, w, h, 128) ||
-      !desc_map(&a.bmap0[0], BR, w, h, 256) || !desc_map(&a.bmap0[1], BL, w, h, 256) ||
+  // left reference: A from the left view's planes, B from the right view's descriptors; right reference the other way
+  if (!desc_map(&a.bmap0[0], BR, w, h, 256) || !desc_map(&a.bmap0[1], BL, w, h, 256) ||
       !desc_map(&a.bmap1[0], BR, w, h, 128) || !desc_map(&a.bmap1[1], BL, w, h, 128))
     return cudaErrorInvalidValue;
-  a.c0[0] = cL; a.c0[1] = cR;
+  a.Bv[0] = BL; a.Pv[0] = PhiL;
+  a.Bv[1] = BR; a.Pv[1] = PhiR;
   a.disp[0] = dL; a.disp[1] = dR;
   a.cost[0] = costL; a.cost[1] = costR;
   a.status = ctx->status;

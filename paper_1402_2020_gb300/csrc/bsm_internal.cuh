@@ -94,8 +94,6 @@ struct bsm_ctx {
   void *ws = nullptr;
   size_t ws_bytes = 0;
   // Scratch of the tensor-core cost kernel: E4M3 operand planes and popcount(Phi AND B) of both views.
-  void *tc_ws = nullptr;
-  size_t tc_ws_bytes = 0;
 };
 
 namespace bsm {
@@ -124,7 +122,6 @@ cudaError_t launch_cost_long(const bsm_ctx *ctx, const uint32_t *BL, const uint3
                              cudaStream_t s);
 bool cost2_supported(const bsm_ctx *ctx);
 bool cost_tc_supported(const bsm_ctx *ctx);
-size_t cost_tc_scratch_bytes(int w, int h);
 cudaError_t launch_cost_tc(const bsm_ctx *ctx, const uint32_t *BL, const uint32_t *PhiL, const uint32_t *BR,
                            const uint32_t *PhiR, int w, int h, int dmax, int32_t *dL, int32_t *dR, uint16_t *costL,
                            uint16_t *costR, cudaStream_t s);
