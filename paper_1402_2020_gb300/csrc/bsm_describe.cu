@@ -251,6 +251,7 @@ __device__ __forceinline__ void describe_warp_tile(const DescribeArgs &a, const 
   if (y >= a.h) return;
   const int npx = min(32, a.w - x0);
   const uint32_t *row = tile + (warp + halo) * tp + halo;
+  const int kbr = (a.k + 31) / 32 - 1;  // the per-lane rank that brackets T (see below)
 #pragma unroll 2  // two pixels' ballot and reduction chains overlap
   for (int px = 0; px < npx; ++px) {
     const uint32_t *c = row + px;  // the same for every lane
@@ -265,15 +266,43 @@ __device__ __forceinline__ void describe_warp_tile(const DescribeArgs &a, const 
     uint32_t wv[NH];
 #pragma unroll
     for (int m = 0; m < NH; ++m) wv[m] = __byte_perm(w[2 * m], w[2 * m + 1], 0x5410) | kHalfBias;
-    __half2 mn = *reinterpret_cast<const __half2 *>(&wv[0]), mx = mn;
+    // Bracket for T: with a = ceil(k / 32) - 1 and s_a(l) lane l's a-th smallest weight (0-based), fewer
+    // than k weights lie below min_l s_a(l) (at most a per lane) and at least k at or below max_l s_a(l)
+    // (a + 1 per lane), so T is in [min_l s_a, max_l s_a]. Built for a = 0 and, at NW = 8, a = 1; other
+    // ranks bracket with the smallest and the largest weight.
+    uint32_t lo, hi;
+    if (kbr == 0 || (NW == 8 && kbr == 1)) {
+      __half2 h1, h2;  // per half (pairs 2m / 2m + 1): the smallest and the second smallest of its NW / 2 weights
+      if constexpr (NW == 8) {
+        const __half2 w0 = *reinterpret_cast<const __half2 *>(&wv[0]), w1 = *reinterpret_cast<const __half2 *>(&wv[1]);
+        const __half2 w2 = *reinterpret_cast<const __half2 *>(&wv[2]), w3 = *reinterpret_cast<const __half2 *>(&wv[3]);
+        const __half2 a = __hmin2(w0, w1), A = __hmax2(w0, w1), b = __hmin2(w2, w3), B = __hmax2(w2, w3);
+        h1 = __hmin2(a, b);
+        h2 = __hmin2(__hmax2(a, b), __hmin2(A, B));
+      } else if constexpr (NW == 4) {
+        const __half2 w0 = *reinterpret_cast<const __half2 *>(&wv[0]), w1 = *reinterpret_cast<const __half2 *>(&wv[1]);
+        h1 = __hmin2(w0, w1);
+        h2 = __hmax2(w0, w1);
+      } else {
+        h1 = h2 = *reinterpret_cast<const __half2 *>(&wv[0]);
+      }
+      const uint32_t b1 = *reinterpret_cast<const uint32_t *>(&h1), b2 = *reinterpret_cast<const uint32_t *>(&h2);
+      const uint32_t m1lo = b1 & 0xFFFFu, m1hi = b1 >> 16;
+      // a = 0: the lane's smallest weight; a = 1: its second smallest (min of the larger first and the smaller second)
+      const uint32_t sab = kbr == 0 ? min(m1lo, m1hi) : min(max(m1lo, m1hi), min(b2 & 0xFFFFu, b2 >> 16));
+      lo = __reduce_min_sync(0xFFFFFFFFu, sab) & 0x3FFu;
+      hi = __reduce_max_sync(0xFFFFFFFFu, sab) & 0x3FFu;
+    } else {
+      __half2 mn = *reinterpret_cast<const __half2 *>(&wv[0]), mx = mn;
 #pragma unroll
-    for (int m = 1; m < NH; ++m) {
-      mn = __hmin2(mn, *reinterpret_cast<const __half2 *>(&wv[m]));
-      mx = __hmax2(mx, *reinterpret_cast<const __half2 *>(&wv[m]));
+      for (int m = 1; m < NH; ++m) {
+        mn = __hmin2(mn, *reinterpret_cast<const __half2 *>(&wv[m]));
+        mx = __hmax2(mx, *reinterpret_cast<const __half2 *>(&wv[m]));
+      }
+      const uint32_t mnb = *reinterpret_cast<const uint32_t *>(&mn), mxb = *reinterpret_cast<const uint32_t *>(&mx);
+      lo = __reduce_min_sync(0xFFFFFFFFu, min(mnb & 0xFFFFu, mnb >> 16)) & 0x3FFu;
+      hi = __reduce_max_sync(0xFFFFFFFFu, max(mxb & 0xFFFFu, mxb >> 16)) & 0x3FFu;
     }
-    const uint32_t mnb = *reinterpret_cast<const uint32_t *>(&mn), mxb = *reinterpret_cast<const uint32_t *>(&mx);
-    uint32_t lo = __reduce_min_sync(0xFFFFFFFFu, min(mnb & 0xFFFFu, mnb >> 16)) & 0x3FFu;
-    uint32_t hi = __reduce_max_sync(0xFFFFFFFFu, max(mxb & 0xFFFFu, mxb >> 16)) & 0x3FFu;
     while (lo < hi) {  // T in [lo, hi] with count(w <= hi) >= k; every step halves the interval
       const uint32_t mid = (lo + hi) >> 1;
       const uint32_t tb = (0x6400u | mid) * 0x10001u;

@@ -99,7 +99,11 @@ def test_describe_bit_exact(B, orc, w, h, n, k, pad):
     c.close()
 
 
-@pytest.mark.parametrize("w,h,n,k", [(450, 375, 256, 0), (37, 23, 256, 100), (33, 2, 64, 64), (5, 7, 128, 1)])
+# k picks the bracket of T's search: k <= 32 (the lanes' smallest weights), 33..64 at n = 256 (their second
+# smallest; 64 is the default n/4), any other rank (the smallest and the largest weight)
+@pytest.mark.parametrize("w,h,n,k", [(450, 375, 256, 0), (37, 23, 256, 100), (33, 2, 64, 64), (5, 7, 128, 1),
+                                     (61, 9, 256, 32), (61, 9, 256, 33), (40, 11, 64, 16), (29, 13, 128, 64),
+                                     (70, 5, 256, 256)])
 def test_describe_warp_per_pixel_bit_exact(B, orc, w, h, n, k):
     l, _, _ = synth.stereo_pair(w, h, 16, seed=120 + w)
     pairs = synth.pair_table(n, 31, seed=w + h + 1)
