@@ -32,6 +32,8 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
+#include <type_traits>
+
 #include "bsm_internal.cuh"
 
 namespace bsm {
@@ -543,51 +545,65 @@ __device__ __forceinline__ void cost_tc_body(const TcArgs &a, uint8_t *smem) {
 #pragma unroll
         for (int j = 0; j < 4; ++j)
           inval[j] = (d8 + 2 * j < dmax ? 0u : 0xFFFFu) | (d8 + 2 * j + 1 < dmax ? 0u : 0xFFFF0000u);
-        // the next column's entering and leaving rows are loaded one column ahead
-        uint4 tn = make_uint4(0u, 0u, 0u, 0u), to = tn;
-        if (lane_on && rr0 + 1 < rr1) {
-          tn = *reinterpret_cast<const uint4 *>(T + (rr0 + 1 + R) * kTP + d8);
-          to = *reinterpret_cast<const uint4 *>(T + (rr0 - R) * kTP + d8);
-        }
+        // FULL: dmax = 256, so every lane's 8 disparities are below dmax: no invalid halves to mask, and the
+        // key needs no select
+        auto columns = [&](auto full_tag) {
+          constexpr bool FULL = decltype(full_tag)::value;
+          // the next column's entering and leaving rows are loaded one column ahead
+          uint4 tn = make_uint4(0u, 0u, 0u, 0u), to = tn;
+          if (lane_on && rr0 + 1 < rr1) {
+            tn = *reinterpret_cast<const uint4 *>(T + (rr0 + 1 + R) * kTP + d8);
+            to = *reinterpret_cast<const uint4 *>(T + (rr0 - R) * kTP + d8);
+          }
 #pragma unroll 2
-        for (int rr = rr0; rr < rr1; ++rr) {
-          if (rr > rr0) {
-            s4[0] += tn.x - to.x; s4[1] += tn.y - to.y; s4[2] += tn.z - to.z; s4[3] += tn.w - to.w;
-            if (lane_on && rr + 1 < rr1) {
-              tn = *reinterpret_cast<const uint4 *>(T + (rr + 1 + R) * kTP + d8);
-              to = *reinterpret_cast<const uint4 *>(T + (rr - R) * kTP + d8);
+          for (int rr = rr0; rr < rr1; ++rr) {
+            if (rr > rr0) {
+              s4[0] += tn.x - to.x; s4[1] += tn.y - to.y; s4[2] += tn.z - to.z; s4[3] += tn.w - to.w;
+              if (lane_on && rr + 1 < rr1) {
+                tn = *reinterpret_cast<const uint4 *>(T + (rr + 1 + R) * kTP + d8);
+                to = *reinterpret_cast<const uint4 *>(T + (rr - R) * kTP + d8);
+              }
             }
-          }
-          uint32_t key;
-          if constexpr (PK) {
-            uint32_t m = 0xFFFFFFFFu;
+            uint32_t key;
+            if constexpr (PK && FULL) {
+              uint32_t m = s4[0] * 8u + 0x00010000u;
 #pragma unroll
-            for (int j = 0; j < 4; ++j)
-              m = vmin_u16x2(m, (s4[j] * 8u + ((uint32_t)(2 * j) | ((uint32_t)(2 * j + 1) << 16))) | inval[j]);
-            const uint32_t m16 = min(m & 0xFFFFu, m >> 16);
-            key = (m16 == 0xFFFFu || !lane_on) ? 0xFFFFFFFFu : ((m16 >> 3) << 8) | (uint32_t)(d8 + (m16 & 7u));
-          } else {
-            key = 0xFFFFFFFFu;
+              for (int j = 1; j < 4; ++j)
+                m = vmin_u16x2(m, s4[j] * 8u + ((uint32_t)(2 * j) | ((uint32_t)(2 * j + 1) << 16)));
+              const uint32_t m16 = min(m & 0xFFFFu, m >> 16);  // (A << 3 | d % 8) of the lane's best
+              key = ((m16 & ~7u) << 5) | (uint32_t)d8 | (m16 & 7u);
+            } else if constexpr (PK) {
+              uint32_t m = 0xFFFFFFFFu;
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
-              if (d8 + 2 * j < dmax) key = min(key, ((s4[j] & 0xFFFFu) << 8) | (uint32_t)(d8 + 2 * j));
-              if (d8 + 2 * j + 1 < dmax) key = min(key, ((s4[j] >> 16) << 8) | (uint32_t)(d8 + 2 * j + 1));
-            }
-          }
-          key = __reduce_min_sync(0xFFFFFFFFu, key);
-          const int x = X0 + rr;
-          if (x >= 0 && x < w) {
-            if (lane == 0) disp[(size_t)yout * w + x] = (int32_t)(key & 0xFFu);
-            if (cost != nullptr && lane_on) {
-              uint16_t *cp = cost + ((size_t)yout * w + x) * dmax;
+              for (int j = 0; j < 4; ++j)
+                m = vmin_u16x2(m, (s4[j] * 8u + ((uint32_t)(2 * j) | ((uint32_t)(2 * j + 1) << 16))) | inval[j]);
+              const uint32_t m16 = min(m & 0xFFFFu, m >> 16);
+              key = (m16 == 0xFFFFu || !lane_on) ? 0xFFFFFFFFu : ((m16 >> 3) << 8) | (uint32_t)(d8 + (m16 & 7u));
+            } else {
+              key = 0xFFFFFFFFu;
 #pragma unroll
               for (int j = 0; j < 4; ++j) {
-                if (d8 + 2 * j < dmax) cp[d8 + 2 * j] = (uint16_t)(s4[j] & 0xFFFFu);
-                if (d8 + 2 * j + 1 < dmax) cp[d8 + 2 * j + 1] = (uint16_t)(s4[j] >> 16);
+                if (d8 + 2 * j < dmax) key = min(key, ((s4[j] & 0xFFFFu) << 8) | (uint32_t)(d8 + 2 * j));
+                if (d8 + 2 * j + 1 < dmax) key = min(key, ((s4[j] >> 16) << 8) | (uint32_t)(d8 + 2 * j + 1));
+              }
+            }
+            key = __reduce_min_sync(0xFFFFFFFFu, key);
+            const int x = X0 + rr;
+            if (x >= 0 && x < w) {
+              if (lane == 0) disp[(size_t)yout * w + x] = (int32_t)(key & 0xFFu);
+              if (cost != nullptr && lane_on) {
+                uint16_t *cp = cost + ((size_t)yout * w + x) * dmax;
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                  if (d8 + 2 * j < dmax) cp[d8 + 2 * j] = (uint16_t)(s4[j] & 0xFFFFu);
+                  if (d8 + 2 * j + 1 < dmax) cp[d8 + 2 * j + 1] = (uint16_t)(s4[j] >> 16);
+                }
               }
             }
           }
-        }
+        };
+        if (dmax == 256) columns(std::true_type{});
+        else columns(std::false_type{});
       }
     }
     if (!ok && tid == kE0 * 32) atomicCAS(a.status, 0u, (uint32_t)BSM_ERR_TIMEOUT);
