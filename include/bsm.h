@@ -168,8 +168,10 @@ typedef struct {
 
 /*
  * The whole method (describe both views, cost_aggregate_wta, refine) for `count` pairs of any sizes
- * and dmax in four persistent launches, replayed from one CUDA graph the context captures on its
- * first batch. Every pair's outputs are bit-identical to the per-pair calls. `pairs` is a HOST array
+ * and dmax in four persistent launches; the first three are replayed from one CUDA graph the context
+ * captures on its first batch. Pairs of at least 1280 x 720 x 128 pixel-disparities instead take the
+ * tensor-core cost kernel (one launch each, after the graph) where n_bits is 256 and the tuning's
+ * cost_variant is 0 or 3. Every pair's outputs are bit-identical to the per-pair calls. `pairs` is a HOST array
  * read before the call returns. Work is asynchronous on `stream`. The context's batch scratch (the
  * colour planes of all 2 * count views) grows here if too small (bsm_reserve_batch sizes it up
  * front); the call waits until the previous batch's ticket table has been copied to the device.

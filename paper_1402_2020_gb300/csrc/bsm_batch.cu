@@ -1,10 +1,14 @@
 // bsm_batch_run: many stereo pairs of uneven size and dmax through the whole path in four persistent
-// launches (colour pre-pass, describe, cost/aggregation/WTA, refine), replayed from one CUDA graph.
+// launches (colour pre-pass, describe, cost/aggregation/WTA, refine); the first three are replayed from
+// one CUDA graph.
 //
 // The host writes a ticket table (one BatchPair per pair plus per-stage ticket bases and totals) into
 // a pinned buffer; the graph's first node copies it to the device, and every persistent CTA then
 // takes tickets from the table's counters, which the copy resets to zero. Nothing in the graph
 // depends on the batch's shape, so one graph, captured the first time, serves every later batch.
+// Pairs of at least kTcWork pixel-disparities take no cost tickets: where the context's parameters
+// allow it they run the tensor-core cost kernel, one launch each, between the graph and the
+// persistent refine launch (for them it is faster than the batched popcount kernel).
 #include <algorithm>
 #include <cstring>
 
@@ -24,6 +28,7 @@ namespace {
 constexpr int kDescTY = 4;           // rows per describe tile (describe kernel's CTA)
 constexpr int kRefTX = 32, kRefTY = 8;
 constexpr size_t kTableBytes = sizeof(BatchHeader) + sizeof(BatchPair) * kMaxBatch;
+constexpr int64_t kTcWork = 1280LL * 720 * 128;  // pixel-disparities from which a pair uses the tensor cores
 
 bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
 
@@ -75,7 +80,6 @@ cudaError_t capture_graph(bsm_ctx *ctx) {
   if (k == cudaSuccess) k = launch_color_plane_batch(ctx, hdr, pairs, ctx->batch_grid[0], cs);
   if (k == cudaSuccess) k = launch_describe_batch(ctx, hdr, pairs, ctx->batch_grid[1], cs);
   if (k == cudaSuccess) k = launch_cost_batch(ctx, hdr, pairs, ctx->batch_grid[2], cs);
-  if (k == cudaSuccess) k = launch_refine_batch(ctx, hdr, pairs, ctx->batch_grid[3], cs);
   cudaGraph_t graph = nullptr;
   e = cudaStreamEndCapture(cs, &graph);
   if (k != cudaSuccess) {
@@ -126,6 +130,8 @@ extern "C" bsm_status bsm_batch_run(bsm_ctx *ctx, const bsm_pair_desc *descs, in
   hdr->band_rows = band;
   size_t plane_off = 0;
   int t_pre = 0, t_desc = 0, t_cost = 0, t_ref = 0;
+  // the tensor-core kernel, unless the tuning asks for a popcount form
+  const bool tc_ok = cost_tc_supported(ctx) && (ctx->cost_variant == 0 || ctx->cost_variant == 3);
   for (int i = 0; i < count; ++i) {
     const bsm_pair_desc &d = descs[i];
     BatchPair &p = pairs[i];
@@ -139,7 +145,8 @@ extern "C" bsm_status bsm_batch_run(bsm_ctx *ctx, const bsm_pair_desc *descs, in
     plane_off += 2 * (size_t)d.w * d.h;
     p.desc_tx = (d.w + 31) / 32;
     p.desc_ty = (d.h + kDescTY - 1) / kDescTY;
-    p.cost_cb = (d.w + outc - 1) / outc;
+    const bool tc = tc_ok && (int64_t)d.w * d.h * d.dmax >= kTcWork;
+    p.cost_cb = tc ? 0 : (d.w + outc - 1) / outc;  // no cost tickets: the pair's own tensor-core launch
     p.cost_bands = (d.h + band - 1) / band;
     p.cost_dr = (d.dmax + kBatchDisp - 1) / kBatchDisp;
     p.ref_tx = (d.w + kRefTX - 1) / kRefTX;
@@ -162,7 +169,16 @@ extern "C" bsm_status bsm_batch_run(bsm_ctx *ctx, const bsm_pair_desc *descs, in
     e = capture_graph(ctx);
     if (e != cudaSuccess) return fail(ctx, e);
   }
-  e = cudaGraphLaunch(ctx->batch_graph, (cudaStream_t)stream);
+  cudaStream_t s = (cudaStream_t)stream;
+  e = cudaGraphLaunch(ctx->batch_graph, s);
+  for (int i = 0; i < count && e == cudaSuccess; ++i) {
+    const bsm_pair_desc &d = descs[i];
+    if (pairs[i].cost_cb == 0)
+      e = launch_cost_tc(ctx, d.BL, d.PhiL, d.BR, d.PhiR, d.w, d.h, d.dmax, d.dispL, d.dispR, nullptr, nullptr, s);
+  }
+  BatchHeader *hdr_dev = reinterpret_cast<BatchHeader *>(ctx->batch_table_dev);
+  const BatchPair *pairs_dev = reinterpret_cast<const BatchPair *>(ctx->batch_table_dev + sizeof(BatchHeader));
+  if (e == cudaSuccess) e = launch_refine_batch(ctx, hdr_dev, pairs_dev, ctx->batch_grid[3], s);
   return e == cudaSuccess ? BSM_OK : fail(ctx, e);
 }
 

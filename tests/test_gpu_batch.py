@@ -112,3 +112,24 @@ def test_batch_argument_errors(B):
             B.bsm_batch_run(ctx, [d])
     finally:
         B.bsm_destroy(ctx)
+
+
+def test_batch_with_tensor_core_pairs(B):
+    # pairs of at least 1280 x 720 x 128 pixel-disparities run the tensor-core cost kernel inside the batch;
+    # every output equals the per-pair calls' (popcount cost kernel) bit for bit
+    pairs = synth.pair_table(256, 31, seed=1500)
+    ctx = B.bsm_create(B.make_params(pairs, agg_window=5, dmax=256))
+    try:
+        shapes = [(1280, 720, 128), (200, 90, 64), (1300, 740, 256), (97, 61, 13)]
+        ts = [make_pair(w, h, d, seed=1510 + i, nw=8) for i, (w, h, d) in enumerate(shapes)]
+        B.bsm_batch_run(ctx, [desc(B, t) for t in ts])
+        torch.cuda.synchronize()
+        B.bsm_set_tuning(ctx, 0, 0, 0, 2)  # the per-pair reference takes the two-column popcount kernel
+        for t in ts:
+            ref = per_pair(B, ctx, t, 8)
+            torch.cuda.synchronize()
+            for k in ("BL", "PhiL", "BR", "PhiR", "dispL", "dispR", "out"):
+                assert torch.equal(t[k], ref[k]), (k, t["w"], t["h"], t["dmax"])
+        assert B.bsm_last_error(ctx) == B.BSM_OK
+    finally:
+        B.bsm_destroy(ctx)
