@@ -116,6 +116,9 @@ void bsm_destroy(bsm_ctx *ctx) {
   if (ctx->batch_graph) cudaGraphExecDestroy(ctx->batch_graph);
   if (ctx->batch_copied) cudaEventDestroy(ctx->batch_copied);
   if (ctx->batch_capture) cudaStreamDestroy(ctx->batch_capture);
+  if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
+  if (ctx->copy_after) cudaEventDestroy(ctx->copy_after);
+  if (ctx->copy_done) cudaEventDestroy(ctx->copy_done);
   cudaFreeHost(ctx->batch_table_host);
   cudaFree(ctx->batch_table_dev);
   cudaFree(ctx->batch_plane);
@@ -268,9 +271,21 @@ bsm_status bsm_match_host(bsm_ctx *ctx, const uint8_t *rgbL_host, const uint8_t 
   int32_t *dispL = (int32_t *)(base + 2 * img + 4 * plane);
   int32_t *dispR = (int32_t *)(base + 2 * img + 4 * plane + map);
   int32_t *out = (int32_t *)(base + 2 * img + 4 * plane + 2 * map);
-  e = cudaMemcpyAsync(dl, rgbL_host, (size_t)h * pitch_bytes, cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(dr, rgbR_host, (size_t)h * pitch_bytes, cudaMemcpyHostToDevice, s);
+  if (ctx->copy_stream == nullptr) {
+    e = cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->copy_after, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->copy_done, cudaEventDisableTiming);
+    if (e != cudaSuccess) return from_cuda(e);
+  }
+  // the right view uploads on the context's copy stream while the left view is described
+  e = cudaEventRecord(ctx->copy_after, s);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->copy_stream, ctx->copy_after, 0);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dl, rgbL_host, (size_t)h * pitch_bytes, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(dr, rgbR_host, (size_t)h * pitch_bytes, cudaMemcpyHostToDevice, ctx->copy_stream);
+  if (e == cudaSuccess) e = cudaEventRecord(ctx->copy_done, ctx->copy_stream);
   if (e == cudaSuccess) e = bsm::launch_describe(ctx, dl, w, h, pitch_bytes, ctx->plane, BL, PhiL, s);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ctx->copy_done, 0);
   if (e == cudaSuccess) e = bsm::launch_describe(ctx, dr, w, h, pitch_bytes, ctx->plane, BR, PhiR, s);
   if (e == cudaSuccess)
     e = bsm::launch_cost_wta(ctx, BL, PhiL, BR, PhiR, w, h, dmax, dispL, dispR, nullptr, nullptr, s);

@@ -84,6 +84,9 @@ struct bsm_ctx {
   uint8_t *batch_table_dev = nullptr;
   cudaEvent_t batch_copied = nullptr;   // the graph's table copy has finished
   cudaStream_t batch_capture = nullptr; // stream the graph is captured on
+  cudaStream_t copy_stream = nullptr;   // bsm_match_host: the right view's upload beside the left's describe
+  cudaEvent_t copy_after = nullptr;     // ... ordered after the caller's earlier work
+  cudaEvent_t copy_done = nullptr;      // ... and awaited before the right view's describe
   cudaGraphExec_t batch_graph = nullptr;
   int batch_graph_variant = -1;         // popcount form and describe variant the graph was captured with
   int batch_grid[4] = {0, 0, 0, 0};     // persistent grid sizes of the four batched kernels
