@@ -23,9 +23,9 @@
  *   - A context is not thread-safe: use one context per host thread. Its calls share the
  *     context's scratch memory, so calls on one context must not overlap on the GPU: issue them on
  *     one stream, or order the streams with events.
- *   - Calls allocate nothing except where stated: bsm_describe grows the context's scratch the
- *     first time it sees an image larger than any before (bsm_reserve sizes it up front, which
- *     is required before capturing calls into a CUDA graph).
+ *   - Calls allocate nothing except where stated: bsm_describe and bsm_refine grow the context's
+ *     scratch the first time they see an image larger than any before (bsm_reserve sizes it up
+ *     front, which is required before capturing calls into a CUDA graph).
  *   - No C++ exception crosses this ABI.
  */
 #ifndef BSM_H
@@ -276,7 +276,8 @@ bsm_status bsm_describe_noalloc(bsm_ctx *ctx, const uint8_t *rgb_dev, int32_t w,
  *   If no vote is positive: the smaller of the nearest valid dL to the left and to the right on
  *   the row, the one that exists, else 0.
  *   rgbL_dev  device left RGB image (h rows of pitch_bytes); out  device int32 [h][w]
- * Every dL value must lie in [0, dmax-1].
+ * Every dL value must lie in [0, dmax-1]. Uses the context's scratch (a w * h plane; it holds each
+ * row's nearest valid disparities), grown here if too small.
  */
 bsm_status bsm_refine(bsm_ctx *ctx, const uint8_t *rgbL_dev, int32_t pitch_bytes, const int32_t *dispL,
                       const int32_t *dispR, int32_t w, int32_t h, int32_t dmax, int32_t *out, void *stream);

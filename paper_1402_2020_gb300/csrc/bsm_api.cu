@@ -238,7 +238,10 @@ bsm_status bsm_refine(bsm_ctx *ctx, const uint8_t *rgbL_dev, int32_t pitch_bytes
   if (ctx == nullptr || rgbL_dev == nullptr || dispL == nullptr || dispR == nullptr || out == nullptr)
     return BSM_ERR_INVALID_ARG;
   if (!size_ok(w, h) || pitch_bytes < 3 * w || dmax < 1 || dmax > ctx->p.dmax) return BSM_ERR_INVALID_ARG;
-  return from_cuda(ctx, bsm::launch_refine(ctx, rgbL_dev, pitch_bytes, dispL, dispR, w, h, dmax, out,
+  // the context's colour-plane scratch holds the rows' nearest valid disparities meanwhile
+  const cudaError_t e = ensure_plane(ctx, (size_t)w * h);
+  if (e != cudaSuccess) return from_cuda(ctx, e);
+  return from_cuda(ctx, bsm::launch_refine(ctx, rgbL_dev, pitch_bytes, dispL, dispR, w, h, dmax, out, ctx->plane,
                                            (cudaStream_t)stream));
 }
 
@@ -289,7 +292,7 @@ bsm_status bsm_match_host(bsm_ctx *ctx, const uint8_t *rgbL_host, const uint8_t 
   if (e == cudaSuccess) e = bsm::launch_describe(ctx, dr, w, h, pitch_bytes, ctx->plane, BR, PhiR, s);
   if (e == cudaSuccess)
     e = bsm::launch_cost_wta(ctx, BL, PhiL, BR, PhiR, w, h, dmax, dispL, dispR, nullptr, nullptr, s);
-  if (e == cudaSuccess) e = bsm::launch_refine(ctx, dl, pitch_bytes, dispL, dispR, w, h, dmax, out, s);
+  if (e == cudaSuccess) e = bsm::launch_refine(ctx, dl, pitch_bytes, dispL, dispR, w, h, dmax, out, ctx->plane, s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(out_host, out, (size_t)w * h * 4, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   return from_cuda(e);

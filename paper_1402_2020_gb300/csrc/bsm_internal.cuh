@@ -134,6 +134,6 @@ cudaError_t launch_cost2(const bsm_ctx *ctx, const uint32_t *BL, const uint32_t 
                          const uint32_t *PhiR, int w, int h, int dmax, int32_t *dL, int32_t *dR, uint16_t *costL, uint16_t *costR,
                          cudaStream_t s);
 cudaError_t launch_refine(const bsm_ctx *ctx, const uint8_t *rgb, int pitch, const int32_t *dL, const int32_t *dR,
-                          int w, int h, int dmax, int32_t *out, cudaStream_t s);
+                          int w, int h, int dmax, int32_t *out, uint32_t *near, cudaStream_t s);
 
 }  // namespace bsm

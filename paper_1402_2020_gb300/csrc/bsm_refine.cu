@@ -34,6 +34,8 @@ struct RefineArgs {
   int w, h, pitch, dmax, tol, R;
   int hist_stride;         // shared histogram bins per warp (>= dmax)
   bool finalize;           // write the masked disparities back into dL and dR
+  const uint32_t *near;    // per pixel (left + 1) | (right + 1) << 16: the nearest valid disparities on the row
+                           // on either side (0: none), or nullptr to scan the row
 };
 
 __device__ __forceinline__ uint32_t lab_sad(uint32_t a, uint32_t b) {
@@ -206,7 +208,12 @@ __device__ __forceinline__ void refine_tile(const RefineArgs &a, int x0, int y0,
     } else {
       // no positive vote: nearest valid disparities on the row
       int left = -1, right = -1;
-      for (int xs = x - 1; xs >= 0; xs -= 32) {
+      if (a.near != nullptr) {
+        const uint32_t nv = __ldg(a.near + (size_t)y * a.w + x);
+        left = (int)(nv & 0xFFFFu) - 1;
+        right = (int)(nv >> 16) - 1;
+      }
+      for (int xs = x - 1; a.near == nullptr && xs >= 0; xs -= 32) {
         const int xi = xs - lane;
         int d = -1;
         if (xi >= 0) d = disp_at(a.dL, (size_t)y * a.w + xi);
@@ -217,7 +224,7 @@ __device__ __forceinline__ void refine_tile(const RefineArgs &a, int x0, int y0,
           break;
         }
       }
-      for (int xs = x + 1; xs < a.w; xs += 32) {
+      for (int xs = x + 1; a.near == nullptr && xs < a.w; xs += 32) {
         const int xi = xs + lane;
         int d = -1;
         if (xi < a.w) d = disp_at(a.dL, (size_t)y * a.w + xi);
@@ -254,6 +261,62 @@ size_t tile_bytes(int R, int hist_stride) {
          (size_t)kTX * kTY * 2;
 }
 
+// Nearest valid disparities on each row (for the refinement's no-vote case): one warp per row walks it in
+// 32-pixel segments, left to right and then right to left, carrying the last valid disparity seen; a
+// pixel's nearest valid neighbour inside its segment comes from the ballot of the segment's valid lanes.
+// The loads (and left/right checks) of kNS segments are issued together; the left-to-right pass leaves
+// each pixel's own valid disparity + 1 (0: invalid) in the upper half for the right-to-left pass.
+constexpr int kNS = 8;
+
+__global__ void __launch_bounds__(256) near_valid_kernel(const RefineArgs a, uint32_t *near) {
+  const int lane = threadIdx.x & 31;
+  const int y = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (y >= a.h) return;
+  const size_t row = (size_t)y * a.w;
+  int carry = -1;  // the last valid disparity left of the segment
+  for (int xb = 0; xb < a.w; xb += 32 * kNS) {
+    int d[kNS];
+    bool ok[kNS];
+#pragma unroll
+    for (int u = 0; u < kNS; ++u) {
+      const int x = xb + 32 * u + lane;
+      d[u] = x < a.w ? disp_at(a.dL, row + x) : a.dmax;
+    }
+#pragma unroll
+    for (int u = 0; u < kNS; ++u) ok[u] = d[u] < a.dmax && lr_valid(a, xb + 32 * u + lane, y, d[u]);
+#pragma unroll
+    for (int u = 0; u < kNS; ++u) {
+      const int x = xb + 32 * u + lane;
+      const uint32_t m = __ballot_sync(0xFFFFFFFFu, ok[u]);
+      const uint32_t below = m & ((1u << lane) - 1u);  // valid lanes strictly left of this one
+      const int dl = __shfl_sync(0xFFFFFFFFu, d[u], below ? 31 - __clz(below) : 0);
+      const int left = below ? dl : carry;
+      if (x < a.w) near[row + x] = (uint32_t)(left + 1) | ((ok[u] ? (uint32_t)(d[u] + 1) : 0u) << 16);
+      if (m) carry = __shfl_sync(0xFFFFFFFFu, d[u], 31 - __clz(m));
+    }
+  }
+  carry = -1;  // the first valid disparity right of the segment
+  for (int xb = ((a.w - 1) / (32 * kNS)) * (32 * kNS); xb >= 0; xb -= 32 * kNS) {
+    uint32_t nv[kNS];
+#pragma unroll
+    for (int u = 0; u < kNS; ++u) {
+      const int x = xb + 32 * u + lane;
+      nv[u] = x < a.w ? near[row + x] : 0u;
+    }
+#pragma unroll
+    for (int u = kNS - 1; u >= 0; --u) {
+      const int x = xb + 32 * u + lane;
+      const int vd = (int)(nv[u] >> 16) - 1;  // this pixel's valid disparity, or -1
+      const uint32_t m = __ballot_sync(0xFFFFFFFFu, vd >= 0);
+      const uint32_t above = lane == 31 ? 0u : m & (0xFFFFFFFEu << lane);  // valid lanes strictly right
+      const int dr = __shfl_sync(0xFFFFFFFFu, vd, above ? __ffs(above) - 1 : 0);
+      const int right = above ? dr : carry;
+      if (x < a.w) near[row + x] = (nv[u] & 0xFFFFu) | ((uint32_t)(right + 1) << 16);
+      if (m) carry = __shfl_sync(0xFFFFFFFFu, vd, __ffs(m) - 1);
+    }
+  }
+}
+
 constexpr int kRFast = 15;  // the radius with an unrolled window walk (the paper's setting)
 
 template <int RT>
@@ -288,7 +351,7 @@ __global__ void __launch_bounds__(kTX *kTY) refine_batch_kernel(BatchHeader *hdr
     const BatchPair &p = pairs[lo];
     const int r = tk - p.ref_base, ty = r / p.ref_tx, tx = r - ty * p.ref_tx;
     RefineArgs a{p.rgb[0], p.plane[0], table, p.disp[0], p.disp[1], p.out, p.w, p.h, p.pitch, p.dmax,
-                 tol, R, hist_stride, true};
+                 tol, R, hist_stride, true, nullptr};
     refine_tile<RT>(a, tx * kTX, ty * kTY, smem, smem + table_words(R));
   }
 }
@@ -296,10 +359,15 @@ __global__ void __launch_bounds__(kTX *kTY) refine_batch_kernel(BatchHeader *hdr
 }  // namespace
 
 cudaError_t launch_refine(const bsm_ctx *ctx, const uint8_t *rgb, int pitch, const int32_t *dL, const int32_t *dR,
-                          int w, int h, int dmax, int32_t *out, cudaStream_t s) {
+                          int w, int h, int dmax, int32_t *out, uint32_t *near, cudaStream_t s) {
   // The plain form never writes dL or dR (finalize is off), so the const inputs stay untouched.
   RefineArgs a{rgb, nullptr, ctx->color_table, const_cast<int32_t *>(dL), const_cast<int32_t *>(dR), out, w, h, pitch,
-               dmax, ctx->p.lr_tol, ctx->p.vote_radius, dmax, false};
+               dmax, ctx->p.lr_tol, ctx->p.vote_radius, dmax, false, near};
+  if (near != nullptr) {
+    near_valid_kernel<<<(h + 7) / 8, 256, 0, s>>>(a, near);
+    const cudaError_t e0 = cudaGetLastError();
+    if (e0 != cudaSuccess) return e0;
+  }
   const size_t smem = table_words(a.R) * 4 + tile_bytes(a.R, dmax);
   auto kern = a.R == kRFast ? refine_kernel<kRFast> : refine_kernel<0>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
