@@ -301,6 +301,12 @@ def run_batch(args, cfg, world, rank, local):
     assert bsm.bsm_last_error(ctx) == bsm.BSM_OK
     t_batch, t_plain = max_over_ranks([t_batch, t_plain], world, dev)
     value = world * units / (t_batch * 1e-3) / 1e9
+    tuning = bsm.bsm_get_tuning(ctx)
+    # the batch: four persistent launches, plus one tensor-core cost launch per pair of at least
+    # 1280 x 720 x 128 pixel-disparities; the per-pair calls: colour pre-pass and describe per view, the
+    # cost stage's kernels, the nearest-valid pass and refine
+    n_tc = sum(1 for t in ts if t["w"] * t["h"] * t["dmax"] >= 1280 * 720 * 128) if tuning["cost_variant"] in (0, 3) else 0
+    plain_launches = sum(4 + cost_kernel(tuning, nw, t["dmax"])[2] + 2 for t in ts)
     line = {
         "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_batch, "higher_is_better": True, "scaling": "weak",
@@ -310,11 +316,11 @@ def run_batch(args, cfg, world, rank, local):
                    "l2": "inputs larger than L2 (all 64 pairs' planes resident, about 7 GB)"},
         "pairs_per_s": world * len(ts) / (t_batch * 1e-3),
         "plain": {"value": world * units / (t_plain * 1e-3) / 1e9, "ms_per_step": t_plain,
-                  "pairs_per_s": world * len(ts) / (t_plain * 1e-3), "launches_per_step": 6 * len(ts)},
+                  "pairs_per_s": world * len(ts) / (t_plain * 1e-3), "launches_per_step": plain_launches},
         "batched_over_plain": t_plain / t_batch,
-        "gpu_launches": 4 * args.steps,
+        "gpu_launches": (4 + n_tc) * args.steps,
         "clocks": clocks,
-        "tuning": bsm.bsm_get_tuning(ctx),
+        "tuning": tuning,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -622,8 +628,8 @@ def run_pair(args, cfg, world, rank, local, n_bits=N_BITS, window_S=WINDOW_S, si
                      "refine": float(per[:, 3].mean())},
         "pairs_per_s": world / (t_step * 1e-3),
         "bad_pixel_rate": bad,  # |d - d_gt| > 1 against the generator's ground truth, rank 0's pair
-        # colour pre-pass + describe per view, the cost stage's kernels, refine
-        "gpu_launches": (4 + klaunch + 1 + (2 * sgm[2] if sgm else 0)) * args.steps,
+        # colour pre-pass + describe per view, the cost stage's kernels, the nearest-valid pass + refine
+        "gpu_launches": (4 + klaunch + 2 + (2 * sgm[2] if sgm else 0)) * args.steps,
         "roofline": roof_desc if describe_dominant else roof_cost,
         ("roofline_cost" if describe_dominant else "roofline_describe"): roof_cost if describe_dominant else roof_desc,
         "clocks": clocks,
