@@ -40,6 +40,8 @@ def _planes(B, ctx, img, nw):
     (17, 50, 40, 5, 0),      # narrower than the disparity range
     (1, 9, 8, 3, 0),         # one column
     (126, 3, 200, 7, 0),     # fewer rows than the window
+    (4100, 9, 256, 5, 0),    # long rows: 34 column tiles, a few rows
+    (1500, 64, 200, 7, 32),  # window 7 (the popcount ring's deepest lead), bands of 32 rows
 ])
 def test_tc_cost_volumes_bit_exact(B, orc, w, h, dmax, win, rows):
     l, r, _ = synth.stereo_pair(w, h, min(dmax, max(w - 1, 1)), seed=1000 + w + h)
