@@ -306,7 +306,7 @@ def run_batch(args, cfg, world, rank, local):
     # 1280 x 720 x 128 pixel-disparities; the per-pair calls: colour pre-pass and describe per view, the
     # cost stage's kernels, the nearest-valid pass and refine
     n_tc = sum(1 for t in ts if t["w"] * t["h"] * t["dmax"] >= 1280 * 720 * 128) if tuning["cost_variant"] in (0, 3) else 0
-    plain_launches = sum(4 + cost_kernel(tuning, nw, t["dmax"])[2] + 2 for t in ts)
+    plain_launches = sum(4 + cost_kernel(tuning, nw, t["dmax"], t["w"] * t["h"])[2] + 2 for t in ts)
     line = {
         "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_batch, "higher_is_better": True, "scaling": "weak",
@@ -452,13 +452,14 @@ def torch_dist_done():
     dist.destroy_process_group()
 
 
-def cost_kernel(tuning, nw, dmax):
+def cost_kernel(tuning, nw, dmax, pixels=0, mask_mode=0):
     """(kernel name, source file, launches per call) of the cost/aggregation/WTA stage the library runs
-    for this tuning, descriptor length and disparity range (the dispatch of bsm_cost_aggregate_wta)."""
-    if nw > 8:
+    for this tuning, descriptor length, disparity range and image size (the dispatch of
+    bsm_cost_aggregate_wta)."""
+    if nw > 8 or mask_mode == 2:
         return "cost_long_kernel", "bsm_long.cu", 1
     v = tuning["cost_variant"]
-    if v == 3:
+    if nw == 8 and (v == 3 or (v == 0 and pixels * dmax >= 1280 * 720 * 128)):
         return "cost_tc_kernel", "bsm_cost_tc.cu", 1
     if v == 2 or (v == 0 and nw in (4, 8)):
         need = (dmax + 7) // 8
@@ -596,7 +597,7 @@ def run_pair(args, cfg, world, rank, local, n_bits=N_BITS, window_S=WINDOW_S, si
     value = world * units / (t_step * 1e-3) / 1e9
 
     tuning = bsm.bsm_get_tuning(ctx)
-    kname, kfile, klaunch = cost_kernel(tuning, nw, dmax)
+    kname, kfile, klaunch = cost_kernel(tuning, nw, dmax, w * h)
     bad = bad_pixel_rate(out.cpu().numpy(), gt)
     # rooflines: the cost stage (fused cost/aggregation/WTA, both reference views per launch) and describe
     # (one view per launch); "roofline" is the one of the two that takes more of the step

@@ -339,8 +339,9 @@ typedef struct {
                               0 carry-save tree over 8 words, 1 plain POPC per word, 2 two 3-word
                               carry-save adders plus 2 plain words (two-column kernel only) */
   int32_t batch_rows;      /* rows per task of bsm_batch_run's cost stage: 0 (64) or 8..512 */
-  int32_t cost_variant;    /* 0: automatic (per pair: two columns per lane for n_bits 128 and 256,
-                              else one; bsm_batch_run: tensor cores for pairs of >= 1280x720x128);
+  int32_t cost_variant;    /* 0: automatic (tensor cores for pairs of >= 1280 x 720 x 128 pixel-
+                              disparities where variant 3 is supported; else two columns per lane
+                              for n_bits 128 and 256, one otherwise);
                               1: one column per lane; 2: two columns per lane (n_bits 128 or 256);
                               3: tensor cores (Eq. 8 as an exact E4M3 product on tcgen05, n_bits 256,
                               reference or no mask) */

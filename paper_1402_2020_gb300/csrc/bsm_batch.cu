@@ -6,7 +6,7 @@
 // a pinned buffer; the graph's first node copies it to the device, and every persistent CTA then
 // takes tickets from the table's counters, which the copy resets to zero. Nothing in the graph
 // depends on the batch's shape, so one graph, captured the first time, serves every later batch.
-// Pairs of at least kTcWork pixel-disparities take no cost tickets: where the context's parameters
+// Pairs of at least kTcAutoWork pixel-disparities take no cost tickets: where the context's parameters
 // allow it they run the tensor-core cost kernel, one launch each, between the graph and the
 // persistent refine launch (for them it is faster than the batched popcount kernel).
 #include <algorithm>
@@ -28,7 +28,6 @@ namespace {
 constexpr int kDescTY = 4;           // rows per describe tile (describe kernel's CTA)
 constexpr int kRefTX = 32, kRefTY = 8;
 constexpr size_t kTableBytes = sizeof(BatchHeader) + sizeof(BatchPair) * kMaxBatch;
-constexpr int64_t kTcWork = 1280LL * 720 * 128;  // pixel-disparities from which a pair uses the tensor cores
 
 bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
 
@@ -145,7 +144,7 @@ extern "C" bsm_status bsm_batch_run(bsm_ctx *ctx, const bsm_pair_desc *descs, in
     plane_off += 2 * (size_t)d.w * d.h;
     p.desc_tx = (d.w + 31) / 32;
     p.desc_ty = (d.h + kDescTY - 1) / kDescTY;
-    const bool tc = tc_ok && (int64_t)d.w * d.h * d.dmax >= kTcWork;
+    const bool tc = tc_ok && (long long)d.w * d.h * d.dmax >= kTcAutoWork;
     p.cost_cb = tc ? 0 : (d.w + outc - 1) / outc;  // no cost tickets: the pair's own tensor-core launch
     p.cost_bands = (d.h + band - 1) / band;
     p.cost_dr = (d.dmax + kBatchDisp - 1) / kBatchDisp;

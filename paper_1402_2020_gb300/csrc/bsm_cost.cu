@@ -536,7 +536,9 @@ cudaError_t launch_cost_wta(const bsm_ctx *ctx, const uint32_t *BL, const uint32
                             uint16_t *costR, cudaStream_t s) {
   if (ctx->nw > 8 || ctx->p.mask_mode == BSM_MASK_BOTH)
     return launch_cost_long(ctx, BL, PhiL, BR, PhiR, w, h, dmax, dL, dR, costL, costR, s);
-  if (ctx->cost_variant == 3 && cost_tc_supported(ctx) && !ctx->withhold_arrivals)
+  // tensor cores when asked for, and by default for pairs large enough to fill the GPU with them
+  const bool tc = ctx->cost_variant == 3 || (ctx->cost_variant == 0 && (long long)w * h * dmax >= kTcAutoWork);
+  if (tc && cost_tc_supported(ctx) && !ctx->withhold_arrivals)
     return launch_cost_tc(ctx, BL, PhiL, BR, PhiR, w, h, dmax, dL, dR, costL, costR, s);
   // The two-column kernel has no staging wait to withhold, so the failure-detection hook keeps the
   // one-column kernel.

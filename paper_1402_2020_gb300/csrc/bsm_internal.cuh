@@ -17,6 +17,8 @@ constexpr int kMaxHalo = 31;       // largest |offset| of a sampling pair
 constexpr int kMaxVoteRadius = 31;
 constexpr int kMaxSad = 3 * 255;   // largest CIELAB SAD of Eq. 5 on 8-bit channels
 constexpr int kVoteShift = 15;     // votes are floor(Ec * Es / 2^15)
+// pixel-disparities of a pair from which the automatic cost variant takes the tensor-core kernel
+constexpr long long kTcAutoWork = 1280LL * 720 * 128;
 
 // Byte layout of a colour-table entry: L | (a + 128) << 8 | (b + 128) << 16 | I << 24.
 constexpr uint32_t kLabMask = 0x00FFFFFFu;
