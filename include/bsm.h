@@ -146,9 +146,12 @@ bsm_status bsm_cost_volumes(bsm_ctx *ctx, const uint32_t *BL, const uint32_t *Ph
  *   cost  device uint16 [h][w][dmax], e.g. bsm_cost_volumes' costL or costR (read only)
  *   S     device uint32 [h][w][dmax] output: S(p, d) = sum over the directions of L_r(p, d)
  *   disp  device int32 [h][w] output: the smallest d with the minimum S(p, d)
- * 0 <= P1 <= P2 <= 65535; paths 4 or 8; dmax <= the context's dmax. Asynchronous on `stream`
- * (one launch per direction). Errors: BSM_ERR_INVALID_ARG for a NULL or misaligned pointer or a
- * value out of range.
+ * 0 <= P1 <= P2 <= 65535; paths 4 or 8; dmax <= the context's dmax. Asynchronous on `stream`.
+ * Where the volume's largest cost + P2 < 65536 (decided on the device) every direction runs at once
+ * on the context's own streams (forked from and joined back into `stream` with events), writing
+ * 16-bit path costs into the context's SGM scratch (paths * w * h * dmax * 2 bytes, grown here if too
+ * small, synchronously); otherwise the directions run one after another on `stream`, accumulating
+ * into S. Errors: BSM_ERR_INVALID_ARG for a NULL or misaligned pointer or a value out of range.
  */
 bsm_status bsm_sgm(bsm_ctx *ctx, const uint16_t *cost, int32_t w, int32_t h, int32_t dmax, int32_t P1, int32_t P2,
                    int32_t paths, uint32_t *S, int32_t *disp, void *stream);

@@ -119,6 +119,12 @@ void bsm_destroy(bsm_ctx *ctx) {
   if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
   if (ctx->copy_after) cudaEventDestroy(ctx->copy_after);
   if (ctx->copy_done) cudaEventDestroy(ctx->copy_done);
+  cudaFree(ctx->sgm_ws);
+  for (int r = 0; r < 8; ++r) {
+    if (ctx->sgm_streams[r]) cudaStreamDestroy(ctx->sgm_streams[r]);
+    if (ctx->sgm_join[r]) cudaEventDestroy(ctx->sgm_join[r]);
+  }
+  if (ctx->sgm_fork) cudaEventDestroy(ctx->sgm_fork);
   cudaFreeHost(ctx->batch_table_host);
   cudaFree(ctx->batch_table_dev);
   cudaFree(ctx->batch_plane);
@@ -144,6 +150,7 @@ bsm_status bsm_create(const bsm_params *p, bsm_ctx **out) {
   ctx->halo = halo;
 
   cudaError_t e = cudaGetDevice(&ctx->device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->sms, cudaDevAttrMultiProcessorCount, ctx->device);
   const int ne = 2 * p->vote_radius * p->vote_radius + 1;
   double *lin_dev = nullptr;
   if (e == cudaSuccess) e = cudaMalloc(&ctx->color_table, sizeof(uint32_t) << 24);
@@ -230,7 +237,28 @@ bsm_status bsm_sgm(bsm_ctx *ctx, const uint16_t *cost, int32_t w, int32_t h, int
   if (!size_ok(w, h) || dmax < 1 || dmax > ctx->p.dmax) return BSM_ERR_INVALID_ARG;
   if (P1 < 0 || P2 < P1 || P2 > 65535 || (paths != 4 && paths != 8)) return BSM_ERR_INVALID_ARG;
   if (((uintptr_t)cost & 1) != 0 || ((uintptr_t)S & 3) != 0 || ((uintptr_t)disp & 3) != 0) return BSM_ERR_INVALID_ARG;
-  return from_cuda(ctx, bsm::launch_sgm(cost, w, h, dmax, P1, P2, paths, S, disp, (cudaStream_t)stream));
+  cudaError_t e = cudaSuccess;
+  if (ctx->sgm_fork == nullptr) {
+    e = cudaEventCreateWithFlags(&ctx->sgm_fork, cudaEventDisableTiming);
+    for (int r = 0; r < 8 && e == cudaSuccess; ++r) {
+      e = cudaStreamCreateWithFlags(&ctx->sgm_streams[r], cudaStreamNonBlocking);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->sgm_join[r], cudaEventDisableTiming);
+    }
+    if (e != cudaSuccess) return from_cuda(ctx, e);
+  }
+  const size_t need = bsm::sgm_scratch_bytes(w, h, dmax, paths);
+  if (ctx->sgm_ws_bytes < need) {  // grows: earlier calls may still use the old planes
+    e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) {
+      cudaFree(ctx->sgm_ws);
+      ctx->sgm_ws = nullptr;
+      ctx->sgm_ws_bytes = 0;
+      e = cudaMalloc(&ctx->sgm_ws, need);
+      if (e == cudaSuccess) ctx->sgm_ws_bytes = need;
+    }
+    if (e != cudaSuccess) return from_cuda(ctx, e);
+  }
+  return from_cuda(ctx, bsm::launch_sgm(ctx, cost, w, h, dmax, P1, P2, paths, S, disp, (cudaStream_t)stream));
 }
 
 bsm_status bsm_refine(bsm_ctx *ctx, const uint8_t *rgbL_dev, int32_t pitch_bytes, const int32_t *dispL,

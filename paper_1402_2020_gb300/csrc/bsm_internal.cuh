@@ -89,6 +89,10 @@ struct bsm_ctx {
   cudaStream_t copy_stream = nullptr;   // bsm_match_host: the right view's upload beside the left's describe
   cudaEvent_t copy_after = nullptr;     // ... ordered after the caller's earlier work
   cudaEvent_t copy_done = nullptr;      // ... and awaited before the right view's describe
+  uint16_t *sgm_ws = nullptr;           // bsm_sgm: 16-bit path-cost planes of every direction + the largest cost
+  size_t sgm_ws_bytes = 0;
+  cudaStream_t sgm_streams[8] = {};     // ... one per direction of the concurrent schedule
+  cudaEvent_t sgm_fork = nullptr, sgm_join[8] = {};
   cudaGraphExec_t batch_graph = nullptr;
   int batch_graph_variant = -1;         // popcount form and describe variant the graph was captured with
   int batch_grid[4] = {0, 0, 0, 0};     // persistent grid sizes of the four batched kernels
@@ -130,8 +134,9 @@ bool cost_tc_supported(const bsm_ctx *ctx);
 cudaError_t launch_cost_tc(const bsm_ctx *ctx, const uint32_t *BL, const uint32_t *PhiL, const uint32_t *BR,
                            const uint32_t *PhiR, int w, int h, int dmax, int32_t *dL, int32_t *dR, uint16_t *costL,
                            uint16_t *costR, cudaStream_t s);
-cudaError_t launch_sgm(const uint16_t *C, int w, int h, int dmax, int P1, int P2, int paths, uint32_t *S,
-                       int32_t *disp, cudaStream_t s);
+size_t sgm_scratch_bytes(int w, int h, int dmax, int paths);
+cudaError_t launch_sgm(bsm_ctx *ctx, const uint16_t *C, int w, int h, int dmax, int P1, int P2, int paths,
+                       uint32_t *S, int32_t *disp, cudaStream_t s);
 cudaError_t launch_cost2(const bsm_ctx *ctx, const uint32_t *BL, const uint32_t *PhiL, const uint32_t *BR,
                          const uint32_t *PhiR, int w, int h, int dmax, int32_t *dL, int32_t *dR, uint16_t *costL, uint16_t *costR,
                          cudaStream_t s);
