@@ -165,10 +165,10 @@ __device__ __forceinline__ void store_l(const SgmArgs &a, size_t base, int d0, c
   }
 }
 
-constexpr int kPF = 3;  // pixels of the scanline whose loads are in flight ahead of the arithmetic
-
-template <int D, bool VEC>
+// NARROW: the concurrent schedule (mode 3: 16-bit path costs out, no S, fewer registers).
+template <int D, bool VEC, bool NARROW>
 __global__ void __launch_bounds__(128) sgm_path_kernel(const SgmArgs a) {
+  constexpr int kPF = 3;  // pixels of the scanline whose loads are in flight ahead of the arithmetic
   const int lane = threadIdx.x & 31;
   const int line = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (line >= a.nlines || !gate_open(a.cmax, a.P2, a.wide)) return;
@@ -208,7 +208,7 @@ __global__ void __launch_bounds__(128) sgm_path_kernel(const SgmArgs a) {
         }
       }
       const size_t base = pixel(k);
-      if (a.mode == 3) {
+      if constexpr (NARROW) {
         store_l<D, VEC>(a, base, d0, L);
 #pragma unroll
         for (int j = 0; j < D; ++j) Lp[j] = L[j];
@@ -316,7 +316,7 @@ cudaError_t launch_paths(bsm_ctx *ctx, SgmArgs a, int paths, cudaStream_t s) {
     b.wide = 0;
     e = cudaStreamWaitEvent(ctx->sgm_streams[r], ctx->sgm_fork, 0);
     if (e == cudaSuccess)
-      sgm_path_kernel<D, VEC><<<(b.nlines + warps - 1) / warps, warps * 32, 0, ctx->sgm_streams[r]>>>(b);
+      sgm_path_kernel<D, VEC, true><<<(b.nlines + warps - 1) / warps, warps * 32, 0, ctx->sgm_streams[r]>>>(b);
     if (e == cudaSuccess) e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaEventRecord(ctx->sgm_join[r], ctx->sgm_streams[r]);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ctx->sgm_join[r], 0);
@@ -334,7 +334,7 @@ cudaError_t launch_paths(bsm_ctx *ctx, SgmArgs a, int paths, cudaStream_t s) {
     b.nlines = lines(r);
     b.mode = r == 0 ? 0 : (r == paths - 1 ? 2 : 1);
     b.wide = 1;
-    sgm_path_kernel<D, VEC><<<(b.nlines + warps - 1) / warps, warps * 32, 0, s>>>(b);
+    sgm_path_kernel<D, VEC, false><<<(b.nlines + warps - 1) / warps, warps * 32, 0, s>>>(b);
     e = cudaGetLastError();
   }
   return e;
