@@ -165,10 +165,11 @@ __device__ __forceinline__ void store_l(const SgmArgs &a, size_t base, int d0, c
   }
 }
 
-// NARROW: the concurrent schedule (mode 3: 16-bit path costs out, no S, fewer registers).
+// NARROW: the concurrent schedule (mode 3: 16-bit path costs out, no S). Its directions run side by
+// side, so scanlines resident per SM count for more than load-ahead depth: a 2-pixel ring, 56 registers.
 template <int D, bool VEC, bool NARROW>
 __global__ void __launch_bounds__(128) sgm_path_kernel(const SgmArgs a) {
-  constexpr int kPF = 3;  // pixels of the scanline whose loads are in flight ahead of the arithmetic
+  constexpr int kPF = NARROW ? 2 : 3;  // pixels of the scanline whose loads are in flight ahead of the arithmetic
   const int lane = threadIdx.x & 31;
   const int line = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (line >= a.nlines || !gate_open(a.cmax, a.P2, a.wide)) return;
