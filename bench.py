@@ -548,7 +548,7 @@ def run_pair(args, cfg, world, rank, local, n_bits=N_BITS, window_S=WINDOW_S, si
     dR = torch.empty_like(dL)
     out = torch.empty_like(dL)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
-    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(args.steps)]
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(6)] for _ in range(args.steps)]
     sgm = tuple(int(v) for v in args.sgm.split(",")) if args.sgm else None
     if sgm:  # semi-global aggregation of both views' cost volumes replaces Eq. 1 on the box sums
         cL = torch.empty((h, w, dmax), dtype=torch.int16, device=dev)
@@ -564,6 +564,7 @@ def run_pair(args, cfg, world, rank, local, n_bits=N_BITS, window_S=WINDOW_S, si
         if e: e[2].record(stream)
         if sgm:
             bsm.bsm_cost_volumes(ctx, BL, PL, BR, PR, w, h, dmax, dL, dR, cL, cR, s)
+            if e: e[5].record(stream)  # the two semi-global aggregations, timed apart
             bsm.bsm_sgm(ctx, cL, w, h, dmax, *sgm, S, sL, s)
             bsm.bsm_sgm(ctx, cR, w, h, dmax, *sgm, S, sR, s)
         else:
@@ -639,6 +640,20 @@ def run_pair(args, cfg, world, rank, local, n_bits=N_BITS, window_S=WINDOW_S, si
     }
     if sgm:
         line["config"]["sgm"] = {"P1": sgm[0], "P2": sgm[1], "paths": sgm[2]}
+        t_sgm = float(np.mean([ev[i][5].elapsed_time(ev[i][3]) for i in range(args.steps)])) * 1e-3
+        line["stage_ms"]["sgm_both_views"] = t_sgm * 1e3
+        if n_bits * agg * agg + sgm[1] < 65536:
+            # concurrent schedule, per (x, d) and view: the maximum (2 B), every direction's cost read and
+            # 16-bit path cost written (4 B), the path costs read back (2 B each) and S written (4 B)
+            bpx = 2 + 6 * sgm[2] + 4
+            hbm = measured_peaks().get("hbm_gbs") or 6800.0
+            achieved = 2 * units * bpx / t_sgm / 1e9
+            line["roofline_sgm"] = {"bound": "hbm", "kernel": "sgm_path_kernel + sgm_sum_kernel", "achieved": achieved,
+                                    "peak": hbm, "unit": "GB/s", "frac": achieved / hbm, "traffic": None,
+                                    "work_per_launch": 2 * units * bpx,
+                                    "peak_basis": "measured copy bandwidth" if measured_peaks().get("hbm_gbs")
+                                    else "fallback 6.8 TB/s",
+                                    "note": f"both views' aggregations, {bpx} B per (x, d) and view"}
         # the cost stage also holds both views' semi-global aggregation
         line["roofline"] = roof_desc if describe_dominant else None
         line.pop("roofline_cost", None)
