@@ -549,6 +549,7 @@ __device__ __forceinline__ void cost_tc_body(const TcArgs &a, uint8_t *smem) {
         // key needs no select
         auto columns = [&](auto full_tag) {
           constexpr bool FULL = decltype(full_tag)::value;
+          int32_t mydisp = 0;
           // the next column's entering and leaving rows are loaded one column ahead
           uint4 tn = make_uint4(0u, 0u, 0u, 0u), to = tn;
           if (lane_on && rr0 + 1 < rr1) {
@@ -588,19 +589,20 @@ __device__ __forceinline__ void cost_tc_body(const TcArgs &a, uint8_t *smem) {
               }
             }
             key = __reduce_min_sync(0xFFFFFFFFu, key);
+            mydisp = lane == rr - rr0 ? (int32_t)(key & 0xFFu) : mydisp;
             const int x = X0 + rr;
-            if (x >= 0 && x < w) {
-              if (lane == 0) disp[(size_t)yout * w + x] = (int32_t)(key & 0xFFu);
-              if (cost != nullptr && lane_on) {
-                uint16_t *cp = cost + ((size_t)yout * w + x) * dmax;
+            if (cost != nullptr && lane_on && x >= 0 && x < w) {
+              uint16_t *cp = cost + ((size_t)yout * w + x) * dmax;
 #pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                  if (d8 + 2 * j < dmax) cp[d8 + 2 * j] = (uint16_t)(s4[j] & 0xFFFFu);
-                  if (d8 + 2 * j + 1 < dmax) cp[d8 + 2 * j + 1] = (uint16_t)(s4[j] >> 16);
-                }
+              for (int j = 0; j < 4; ++j) {
+                if (d8 + 2 * j < dmax) cp[d8 + 2 * j] = (uint16_t)(s4[j] & 0xFFFFu);
+                if (d8 + 2 * j + 1 < dmax) cp[d8 + 2 * j + 1] = (uint16_t)(s4[j] >> 16);
               }
             }
           }
+          // lane c holds column rr0 + c's disparity: one store for the warp's columns
+          const int xo = X0 + rr0 + lane;
+          if (lane < rr1 - rr0 && xo >= 0 && xo < w) disp[(size_t)yout * w + xo] = mydisp;
         };
         if (dmax == 256) columns(std::true_type{});
         else columns(std::false_type{});
