@@ -654,8 +654,12 @@ def run_pair(args, cfg, world, rank, local, n_bits=N_BITS, window_S=WINDOW_S, si
                                     "peak_basis": "measured copy bandwidth" if measured_peaks().get("hbm_gbs")
                                     else "fallback 6.8 TB/s",
                                     "note": f"both views' aggregations, {bpx} B per (x, d) and view"}
-        # the cost stage also holds both views' semi-global aggregation
-        line["roofline"] = roof_desc if describe_dominant else None
+        # the cost stage also holds both views' semi-global aggregation, so it has no cost roofline of its
+        # own; the aggregation's roofline is the headline one where it takes more of the step than describe
+        if "roofline_sgm" in line and t_sgm > t_desc:
+            line["roofline"] = line["roofline_sgm"]
+        else:
+            line["roofline"] = roof_desc if describe_dominant else None
         line.pop("roofline_cost", None)
     if e2e and not sgm:
         # end to end through the host-buffer C-ABI call (H2D of both views and D2H of the map inside)
