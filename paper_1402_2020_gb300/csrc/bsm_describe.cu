@@ -46,6 +46,12 @@ __device__ __forceinline__ uint32_t lab_sad(uint32_t a, uint32_t b) {
   return __dp4a(__vabsdiffu4(a, b), 0x00010101u, 0u);
 }
 
+// The same SAD plus 1024 in the fp16 bit pattern (0x6400 | SAD for SAD < 1024): the weight's fp16 form
+// without a separate bias.
+__device__ __forceinline__ uint32_t lab_sad_h(uint32_t a, uint32_t b) {
+  return __dp4a(__vabsdiffu4(a, b), 0x00010101u, 0x6400u);
+}
+
 __global__ void __launch_bounds__(256) color_plane_kernel(const uint8_t *__restrict__ rgb, int w, int h, int pitch,
                                                           const uint32_t *__restrict__ table,
                                                           uint32_t *__restrict__ plane) {
@@ -261,11 +267,11 @@ __device__ __forceinline__ void describe_warp_tile(const DescribeArgs &a, const 
     for (int j = 0; j < NW; ++j) {
       const uint32_t pw = c[op[j]], qw = c[oq[j]];
       bw[j] = __ballot_sync(0xFFFFFFFFu, pw > (qw | kLabMask));
-      w[j] = max(lab_sad(cw, pw), lab_sad(cw, qw));
+      w[j] = max(lab_sad_h(cw, pw), lab_sad_h(cw, qw));  // fp16 bits of 1024 + w
     }
     uint32_t wv[NH];
 #pragma unroll
-    for (int m = 0; m < NH; ++m) wv[m] = __byte_perm(w[2 * m], w[2 * m + 1], 0x5410) | kHalfBias;
+    for (int m = 0; m < NH; ++m) wv[m] = __byte_perm(w[2 * m], w[2 * m + 1], 0x5410);
     // Bracket for T: with a = ceil(k / 32) - 1 and s_a(l) lane l's a-th smallest weight (0-based), fewer
     // than k weights lie below min_l s_a(l) (at most a per lane) and at least k at or below max_l s_a(l)
     // (a + 1 per lane), so T is in [min_l s_a, max_l s_a]. Built for a = 0 and, at NW = 8, a = 1; other
@@ -305,7 +311,7 @@ __device__ __forceinline__ void describe_warp_tile(const DescribeArgs &a, const 
     }
     while (lo < hi) {  // T in [lo, hi] with count(w <= hi) >= k; every step halves the interval
       const uint32_t mid = (lo + hi) >> 1;
-      const uint32_t tb = (0x6400u | mid) * 0x10001u;
+      const uint32_t tb = mid * 0x10001u + kHalfBias;
       const __half2 t2 = *reinterpret_cast<const __half2 *>(&tb);
       __half2 acc = __hle2(*reinterpret_cast<const __half2 *>(&wv[0]), t2);
 #pragma unroll
@@ -315,7 +321,7 @@ __device__ __forceinline__ void describe_warp_tile(const DescribeArgs &a, const 
       if (total >= a.k) hi = mid;
       else lo = mid + 1;
     }
-    const uint32_t tb = (0x6400u | lo) * 0x10001u;  // fp16 1024 + T in both halves
+    const uint32_t tb = lo * 0x10001u + kHalfBias;  // fp16 1024 + T in both halves
     uint32_t fw[NW];
 #pragma unroll
     for (int m = 0; m < NH; ++m)  // one fp16x2 compare sets the predicates of pairs 2 m (low) and 2 m + 1
