@@ -224,8 +224,10 @@ __global__ void __launch_bounds__(kTY * 32) describe_kernel(const DescribeArgs a
 // Warp per pixel for n <= 256 (NW = 2, 4, 8 words): lane l evaluates pairs l, l + 32, ..., keeping
 // their tile offsets in registers for the whole CTA. Descriptor word j is __ballot_sync of its 32 tau
 // bits (Eq. 3) and lands in lane j; the lane's NW weights (Eq. 5) are packed two per register as fp16
-// 1024 + w, T (Eq. 6) is found by bisection with one warp-wide sum per step, and Phi's words are ballots
-// of w <= T (Eq. 7). One warp covers a row of 32 pixels, one pixel at a time.
+// 1024 + w, T (Eq. 6) is found by bisection with one warp-wide sum per step (each step's per-lane count
+// from fp16x2 compares that yield 0xFFFF per true half, summed as integers), and Phi's words are ballots
+// of w <= T (Eq. 7). One warp covers a row of 32 pixels, one pixel at a time, four pixels' chains
+// interleaved.
 constexpr int kWY = 4;  // rows (warps) per CTA of describe_warp_kernel
 
 // One 32 x kWY block with top-left corner (x0, y0). Contains one CTA-wide barrier, which every thread
@@ -258,7 +260,7 @@ __device__ __forceinline__ void describe_warp_tile(const DescribeArgs &a, const 
   const int npx = min(32, a.w - x0);
   const uint32_t *row = tile + (warp + halo) * tp + halo;
   const int kbr = (a.k + 31) / 32 - 1;  // the per-lane rank that brackets T (see below)
-#pragma unroll 2  // two pixels' ballot and reduction chains overlap
+#pragma unroll 4  // four pixels' ballot and reduction chains overlap
   for (int px = 0; px < npx; ++px) {
     const uint32_t *c = row + px;  // the same for every lane
     const uint32_t cw = *c;
@@ -292,10 +294,11 @@ __device__ __forceinline__ void describe_warp_tile(const DescribeArgs &a, const 
       } else {
         h1 = h2 = *reinterpret_cast<const __half2 *>(&wv[0]);
       }
-      const uint32_t b1 = *reinterpret_cast<const uint32_t *>(&h1), b2 = *reinterpret_cast<const uint32_t *>(&h2);
-      const uint32_t m1lo = b1 & 0xFFFFu, m1hi = b1 >> 16;
-      // a = 0: the lane's smallest weight; a = 1: its second smallest (min of the larger first and the smaller second)
-      const uint32_t sab = kbr == 0 ? min(m1lo, m1hi) : min(max(m1lo, m1hi), min(b2 & 0xFFFFu, b2 >> 16));
+      // a = 0: the lane's smallest weight; a = 1: its second smallest (min of the larger first and the smaller
+      // second), both halves alike, so the u32 order of the pattern is the order of the weight
+      const __half2 h1s = __lowhigh2highlow(h1), h2s = __lowhigh2highlow(h2);
+      const __half2 s2 = kbr == 0 ? __hmin2(h1, h1s) : __hmin2(__hmax2(h1, h1s), __hmin2(h2, h2s));
+      const uint32_t sab = *reinterpret_cast<const uint32_t *>(&s2);
       lo = __reduce_min_sync(0xFFFFFFFFu, sab) & 0x3FFu;
       hi = __reduce_max_sync(0xFFFFFFFFu, sab) & 0x3FFu;
     } else {
@@ -313,12 +316,14 @@ __device__ __forceinline__ void describe_warp_tile(const DescribeArgs &a, const 
       const uint32_t mid = (lo + hi) >> 1;
       const uint32_t tb = mid * 0x10001u + kHalfBias;
       const __half2 t2 = *reinterpret_cast<const __half2 *>(&tb);
-      __half2 acc = __hle2(*reinterpret_cast<const __half2 *>(&wv[0]), t2);
+      // S = sum of the 0xFFFF-per-true-half masks = c_lo (2^16 - 1) + c_hi (2^32 - 2^16) mod 2^32, so
+      // -S (2^16 * 2 + 1) = c_lo + (c_lo + c_hi) 2^16 mod 2^32: the lane's count in the high half, below it a
+      // part under 2^16 that stays under 2^16 summed over the warp (c_lo <= NW / 2 per lane)
+      uint32_t S = 0;
 #pragma unroll
-      for (int m = 1; m < NH; ++m) acc = __hadd2(acc, __hle2(*reinterpret_cast<const __half2 *>(&wv[m]), t2));
-      const __half cnt = __hadd(__hadd(__low2half(acc), __high2half(acc)), __ushort_as_half((unsigned short)0x6400));
-      const int total = (int)__reduce_add_sync(0xFFFFFFFFu, (uint32_t)__half_as_ushort(cnt) & 0x3FFu);
-      if (total >= a.k) hi = mid;
+      for (int m = 0; m < NH; ++m) S += __hle2_mask(*reinterpret_cast<const __half2 *>(&wv[m]), t2);
+      const uint32_t tot = __reduce_add_sync(0xFFFFFFFFu, S * (0u - 0x20001u));  // count << 16 | sum of c_lo
+      if (tot >= ((uint32_t)a.k << 16)) hi = mid;
       else lo = mid + 1;
     }
     const uint32_t tb = lo * 0x10001u + kHalfBias;  // fp16 1024 + T in both halves
