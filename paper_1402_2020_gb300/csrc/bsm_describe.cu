@@ -260,7 +260,7 @@ __device__ __forceinline__ void describe_warp_tile(const DescribeArgs &a, const 
   const int npx = min(32, a.w - x0);
   const uint32_t *row = tile + (warp + halo) * tp + halo;
   const int kbr = (a.k + 31) / 32 - 1;  // the per-lane rank that brackets T (see below)
-#pragma unroll 4  // four pixels' ballot and reduction chains overlap
+#pragma unroll 8  // eight pixels' ballot and reduction chains overlap
   for (int px = 0; px < npx; ++px) {
     const uint32_t *c = row + px;  // the same for every lane
     const uint32_t cw = *c;
