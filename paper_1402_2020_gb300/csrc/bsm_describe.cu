@@ -232,18 +232,17 @@ constexpr int kWY = 4;  // rows (warps) per CTA of describe_warp_kernel
 
 // One 32 x kWY block with top-left corner (x0, y0). Contains one CTA-wide barrier, which every thread
 // of the CTA reaches.
-template <int NW>
+template <int NW, int UNR>
 __device__ __forceinline__ void describe_warp_tile(const DescribeArgs &a, const PairTable &pt, int x0, int y0,
                                                    uint32_t *smem) {
   constexpr int NH = NW / 2;
   const int halo = a.halo, tp = 32 + 2 * halo, th = kWY + 2 * halo;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   uint32_t *tile = smem;
-  for (int i = threadIdx.x; i < th * tp; i += blockDim.x) {
-    const int ty = i / tp, tx = i - ty * tp;
-    const int gx = min(max(x0 + tx - halo, 0), a.w - 1);
-    const int gy = min(max(y0 + ty - halo, 0), a.h - 1);
-    cp_async4(tile + i, a.plane + (size_t)gy * a.w + gx);
+  // tile rows by warp, columns by lane (no division in the addressing)
+  for (int ty = warp; ty < th; ty += kWY) {
+    const uint32_t *src = a.plane + (size_t)min(max(y0 + ty - halo, 0), a.h - 1) * a.w;
+    for (int tx = lane; tx < tp; tx += 32) cp_async4(tile + ty * tp + tx, src + min(max(x0 + tx - halo, 0), a.w - 1));
   }
   // The offsets differ per lane, so a constant-bank read of them is serialised across the warp: read
   // them once per tile, through an opaque move that keeps them in registers instead of re-read.
@@ -260,7 +259,7 @@ __device__ __forceinline__ void describe_warp_tile(const DescribeArgs &a, const 
   const int npx = min(32, a.w - x0);
   const uint32_t *row = tile + (warp + halo) * tp + halo;
   const int kbr = (a.k + 31) / 32 - 1;  // the per-lane rank that brackets T (see below)
-#pragma unroll 8  // eight pixels' ballot and reduction chains overlap
+#pragma unroll UNR  // UNR pixels' ballot and reduction chains overlap
   for (int px = 0; px < npx; ++px) {
     const uint32_t *c = row + px;  // the same for every lane
     const uint32_t cw = *c;
@@ -353,7 +352,7 @@ __device__ __forceinline__ void describe_warp_tile(const DescribeArgs &a, const 
 template <int NW>
 __global__ void __launch_bounds__(kWY * 32) describe_warp_kernel(const DescribeArgs a, const __grid_constant__ PairTable pt) {
   extern __shared__ __align__(16) uint32_t smem[];
-  describe_warp_tile<NW>(a, pt, blockIdx.x * 32, blockIdx.y * kWY, smem);
+  describe_warp_tile<NW, 8>(a, pt, blockIdx.x * 32, blockIdx.y * kWY, smem);
 }
 
 size_t describe_warp_smem(int halo) { return 4 * (size_t)(kWY + 2 * halo) * (32 + 2 * halo); }
@@ -444,7 +443,7 @@ __global__ void __launch_bounds__(kWY * 32) describe_warp_batch_kernel(BatchHead
     r -= view * per_view;
     const int ty = r / p.desc_tx, tx = r - ty * p.desc_tx;
     const DescribeArgs a{p.plane[view], p.B[view], p.Phi[view], p.w, p.h, k, halo};
-    describe_warp_tile<NW>(a, pt, tx * 32, ty * kWY, smem);
+    describe_warp_tile<NW, 4>(a, pt, tx * 32, ty * kWY, smem);  // 8 would spill with the ticket loop's registers
   }
 }
 
