@@ -1,0 +1,86 @@
+"""The integer and fp16 identities the describe kernels rely on, checked exhaustively on the host (no GPU).
+
+These are facts about the encodings, not about the oracle: the fp16 form of the Eq. 5 weights, the
+per-step count of the T bisection (Eq. 6) from 0xFFFF half masks, and the order-statistic bracket that
+starts the bisection."""
+import numpy as np
+import pytest
+
+M32 = (1 << 32) - 1
+
+
+def half_bits(x):
+    return int(np.array(x, dtype=np.float16).view(np.uint16))
+
+
+def test_biased_weight_is_the_fp16_of_1024_plus_w():
+    # every weight is a 3-channel SAD of 8-bit values (<= 765); 0x6400 + w must be the fp16 pattern of
+    # 1024 + w, exactly, and the pattern order must be the order of w
+    for w in range(0, 1024):
+        assert 0x6400 + w == half_bits(1024.0 + w)
+    pats = np.arange(0x6400, 0x6400 + 1024, dtype=np.uint16).view(np.float16).astype(np.float64)
+    assert (np.diff(pats) == 1.0).all()
+
+
+@pytest.mark.parametrize("nh", [1, 2, 4, 64])
+def test_mask_sum_count(nh):
+    # a lane holds nh fp16x2 registers; per register a compare yields 0xFFFF in each true half. The lane
+    # sums the nh masks as 32-bit integers and multiplies by -(2^17 + 1): the high half must be the
+    # lane's count, the low half the count of true low halves (<= nh), whatever the true halves are.
+    mul = (-0x20001) & M32
+    rng = np.random.default_rng(nh)
+    for _ in range(200):
+        lo = rng.integers(0, 2, size=nh)
+        hi = rng.integers(0, 2, size=nh)
+        S = 0
+        for a, b in zip(lo, hi):
+            S = (S + (0xFFFF if a else 0) + (0xFFFF0000 if b else 0)) & M32
+        t = (S * mul) & M32
+        assert t >> 16 == int(lo.sum() + hi.sum())
+        assert t & 0xFFFF == int(lo.sum())
+    # every (c_lo, c_hi) and the warp-wide sum of 32 such lanes: count << 16 plus a part below 2^16
+    for c_lo in range(nh + 1):
+        for c_hi in range(nh + 1):
+            S = (c_lo * 0xFFFF + c_hi * 0xFFFF0000) & M32
+            assert (S * mul) & M32 == c_lo + ((c_lo + c_hi) << 16)
+    lanes = rng.integers(0, nh + 1, size=(32, 2))
+    tot = sum(((int(a) * 0xFFFF + int(b) * 0xFFFF0000) * mul) & M32 for a, b in lanes) & M32
+    count = int(lanes.sum())
+    assert tot >> 16 == count and (tot & 0xFFFF) == int(lanes[:, 0].sum())
+    for k in (1, count, count + 1, 32 * 2 * nh):
+        assert (tot >= (k << 16)) == (count >= k)
+
+
+@pytest.mark.parametrize("nw,k", [(2, 16), (4, 32), (8, 64), (8, 33), (8, 32), (4, 1), (8, 256)])
+def test_order_statistic_bracket(nw, k):
+    # lane l holds the weights of pairs l, l + 32, ...; with a = ceil(k / 32) - 1 and s_a(l) the lane's
+    # a-th smallest (0-based), the k-th smallest weight T lies in [min_l s_a(l), max_l s_a(l)]
+    rng = np.random.default_rng(nw * 1000 + k)
+    a = (k + 31) // 32 - 1
+    for trial in range(300):
+        hi = [4, 30, 765][trial % 3]
+        w = rng.integers(0, hi + 1, size=32 * nw)
+        T = np.sort(w)[k - 1]
+        lanes = w.reshape(nw, 32).T  # [lane][j] = pair 32 j + lane
+        s = np.sort(lanes, axis=1)[:, min(a, nw - 1)]
+        assert s.min() <= T <= s.max()
+
+
+def test_bracket_statistic_from_half_pairs():
+    # at nw = 8 the lane's eight weights sit in four fp16x2 registers; the kernel takes the smallest and
+    # the second smallest per half with a min/max network, then the lane's smallest and second smallest
+    # from the two halves (and their swapped copies)
+    rng = np.random.default_rng(7)
+    for _ in range(2000):
+        w = rng.integers(0, 766, size=8)
+        lo_half, hi_half = w[0::2], w[1::2]  # pairs 2 m (low) and 2 m + 1 (high) of register m
+        def m12(v):
+            a, A = min(v[0], v[1]), max(v[0], v[1])
+            b, B = min(v[2], v[3]), max(v[2], v[3])
+            return min(a, b), min(max(a, b), min(A, B))
+        l1, l2 = m12(lo_half)
+        h1, h2 = m12(hi_half)
+        s0 = min(l1, h1)
+        s1 = min(max(l1, h1), min(l2, h2))
+        srt = np.sort(w)
+        assert s0 == srt[0] and s1 == srt[1]
