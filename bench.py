@@ -617,6 +617,11 @@ def run_pair(args, cfg, world, rank, local, n_bits=N_BITS, window_S=WINDOW_S, si
                   "peak_basis": f"{SMS} SMs x {POPC_PER_CLK_SM} POPC/clk x {MAX_SM_MHZ} MHz"}
                  if kname != "cost_tc_kernel" else tensor_roofline(units, n_bits, t_k2, traffic))
     roof_cost["xd_per_s_per_direction"] = units / t_k2  # one launch covers both reference views
+    if kname == "cost_tc_kernel":
+        # the same launch against the integer-pipe roofline of the popcount formulation of Eq. 8 (one plain
+        # POPC per masked word), the bound the popcount kernels are held to
+        roof_cost["popc_equivalent"] = {"achieved": achieved, "peak": peak, "unit": "Gpopc/s",
+                                        "frac": achieved / peak}
     describe_dominant = t_desc > t_k2
     line = {
         "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
