@@ -4,13 +4,18 @@ One step = the whole path on one stereo pair with inputs already resident in HBM
 right view), the fused cost + aggregation + WTA kernel (both reference views) and the left/right
 check + refinement. Metric: Gpix*disp/s = width * height * dmax per pair / step time.
 
-Default workload: the full-size synthetic 1390 x 1110 RGB8 pair with dmax 256 and a radiometric
-change on the right view (n = 256 bits, S = 31, aggregation window 5, k = n/4, R = 15).
+Default run (no flags): the 3840 x 2160 RGB8 pair with dmax 256 (n = 256 bits, S = 31, aggregation
+window 5, k = n/4, R = 15) is the headline line; the same JSON line carries
+  "batched": the batch of 64 uneven pairs in persistent launches against the per-pair calls, both
+             timed in this process on this build, with the launch-gap bound of the per-pair path;
+  "served":  a 10,000-request Poisson stream (rho = 0.7 of the engine's measured capacity) through the
+             continuous-batching engine against one-at-a-time processing of the same trace.
 
-  python bench.py [--gpus N --steps K --warmup W] [--config c1|c2|c4] [--impl ours|reference]
+  python bench.py [--gpus N --steps K --warmup W] [--config c1|c2|c3|c4|c5] [--impl ours|reference]
 
-Multi-GPU (torchrun, one process per GPU) runs independent replicas: every rank processes its own
-pair, nothing is exchanged, value = all ranks' pixels*disparities / max-over-ranks time.
+An explicit --config runs that configuration alone. Multi-GPU (torchrun, one process per GPU) runs
+independent replicas: every rank processes its own pair, nothing is exchanged, value = all ranks'
+pixels*disparities / max-over-ranks time.
 """
 import argparse
 import hashlib
@@ -42,9 +47,8 @@ N_BITS, WINDOW_S, AGG, VOTE_R = 256, 31, 5, 15
 PAIR_SEED = 11
 METRIC = "Gpix*disp/s"
 L2_FLUSH_BYTES = 256 << 20
-POPC_PER_CLK_SM = 16  # measured integer-pipe rate of POPC on sm_103a
-ALU_PER_CLK_SM = 64   # measured rate of LOP3, VABSDIFF4, DP4A, MAX and SETP on sm_103a (lanes per clock)
-SMS, MAX_SM_MHZ = 152, 2070
+SMS, MAX_SM_MHZ = 152, 2070  # the GB300's SM count and maximum SM clock
+ISSUE_PER_CLK_SM = 4 * 32    # four schedulers per SM, one warp instruction (32 lanes) each per clock
 
 
 def parse():
@@ -52,7 +56,10 @@ def parse():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
-    ap.add_argument("--config", default="c2", choices=sorted(CONFIGS))
+    ap.add_argument("--config", default="", choices=[""] + sorted(CONFIGS),
+                    help="run one configuration alone (default: c4 with the batched c3 and served c5 objects)")
+    ap.add_argument("--no-batched", action="store_true", help="default run without the batched (c3) object")
+    ap.add_argument("--no-served", action="store_true", help="default run without the served (c5) object")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cost-rows", type=int, default=0, help="rows per CTA of the cost kernel (0: heuristic)")
@@ -69,7 +76,7 @@ def parse():
                     help="bad-pixel rates against the generator's ground truth: mask ablation, radiometric 3x3")
     ap.add_argument("--sweep-n", action="store_true",
                     help="speed for every descriptor length 32 ... 4096 on the chosen pair config (Fig. 3b)")
-    ap.add_argument("--requests", type=int, default=2000, help="serving stream length (c5)")
+    ap.add_argument("--requests", type=int, default=10000, help="serving stream length (c5)")
     ap.add_argument("--rho", type=float, default=0.7, help="arrival rate as a fraction of measured capacity (c5)")
     ap.add_argument("--lanes", type=int, default=2, help="serving lanes (c5)")
     ap.add_argument("--max-batch", type=int, default=16, help="serving batch limit (c5)")
@@ -200,9 +207,11 @@ def dist_init(args):
 
 
 def run_reference(args, cfg, world, rank):
+    """The oracle as it stands, single-threaded on one pinned host core, on a bounded row band of the
+    workload per step (the band keeps the whole --steps K --warmup W run within a few minutes)."""
     if rank != 0:
         return
-    rows = 16
+    rows = 8 if cfg.get("w", 0) >= 3000 else 16
     if "count" in cfg:
         from paper_1402_2020_gb300 import synth
 
@@ -210,27 +219,37 @@ def run_reference(args, cfg, world, rank):
         cfg = dict(cfg, w=w0)
     elif "w" not in cfg:
         cfg = dict(cfg, w=1280)
-    times = []
-    for i in range(args.warmup + args.steps):
-        dt, units = oracle_sample(cfg, rows)
-        if i >= args.warmup:
-            times.append(dt)
+
+    def run():
+        times = []
+        for i in range(args.warmup + args.steps):
+            dt, units = oracle_sample(cfg, rows)
+            if i >= args.warmup:
+                times.append(dt)
+        return times, units
+
+    (times, units), core = pinned_to_one_core(run)
     t = float(np.mean(times))
     v = units / t / 1e9
+    nproc, model = host_cpu()
+    sample = f"{cfg['w']}x{rows} row band of the workload per step, whole oracle pipeline, single thread pinned to " \
+             f"host core {core}"
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": METRIC, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-            "config": {"workload": cfg["name"], "n_bits": N_BITS, "agg_window": AGG,
-                       "sample": f"{cfg['w']}x{rows} row band of the workload per step"},
-            "cpu_baseline": {"value": v, "unit": METRIC, "cores": 1, "kind": "oracle",
-                             "sample": f"{cfg['w']}x{rows} row band, whole oracle pipeline, single thread"},
+            "config": {"workload": cfg["name"], "n_bits": N_BITS, "agg_window": AGG, "sample": sample},
+            "cpu_baseline": {"value": v, "unit": METRIC, "cores": 1, "kind": "oracle", "sample": sample,
+                             "nproc": nproc, "cpu_model": model},
             "e2e": {"value": v, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
 def run_batch(args, cfg, world, rank, local):
     """Config 3: one bsm_batch_run per step (persistent launches from a CUDA graph) against the same 64 pairs
-    through the per-pair calls (four C-ABI calls, six launches per pair)."""
+    through the per-pair calls (four C-ABI calls per pair), both timed here on this build. The per-pair
+    path is timed twice: as issued (`plain`) and with the whole step enqueued behind a GPU-side delay so
+    that its kernels run back to back (`plain_gap_free`): the ratio bounds what removing launch gaps alone
+    can give. Returns the JSON object."""
     import torch
 
     from paper_1402_2020_gb300 import bsm, synth
@@ -293,20 +312,39 @@ def run_batch(args, cfg, world, rank, local):
             torch.cuda.synchronize()
         return float(np.mean([a.elapsed_time(b) for a, b in zip(e0, e1)]))
 
+    def gap_free(fn, reps=3):
+        # the GPU spins for a bounded time (torch's clock-based sleep kernel) while the host enqueues the
+        # whole step behind it; the step's kernels then run back to back without launch gaps
+        out = []
+        with torch.cuda.stream(stream):
+            for _ in range(reps):
+                torch.cuda.synchronize()
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                torch.cuda._sleep(int(0.2 * MAX_SM_MHZ * 1e6))
+                t0 = time.perf_counter()
+                a.record(stream)
+                fn()
+                b.record(stream)
+                host_s = time.perf_counter() - t0
+                torch.cuda.synchronize()
+                out.append((a.elapsed_time(b), host_s))
+        return float(np.mean([o[0] for o in out])), max(o[1] for o in out)
+
     clk = Clocks(local)
     clk.start()
     t_batch = timed(batched)
     clocks = clk.stop()
     t_plain = timed(plain)
+    t_free, host_enqueue_s = gap_free(plain)
     assert bsm.bsm_last_error(ctx) == bsm.BSM_OK
-    t_batch, t_plain = max_over_ranks([t_batch, t_plain], world, dev)
+    t_batch, t_plain, t_free = max_over_ranks([t_batch, t_plain, t_free], world, dev)
     value = world * units / (t_batch * 1e-3) / 1e9
     tuning = bsm.bsm_get_tuning(ctx)
     # the batch: four persistent launches, plus one tensor-core cost launch per pair of at least
     # 1280 x 720 x 128 pixel-disparities; the per-pair calls: colour pre-pass and describe per view, the
     # cost stage's kernels, the nearest-valid pass and refine
     n_tc = sum(1 for t in ts if t["w"] * t["h"] * t["dmax"] >= 1280 * 720 * 128) if tuning["cost_variant"] in (0, 3) else 0
-    plain_launches = sum(4 + cost_kernel(tuning, nw, t["dmax"], t["w"] * t["h"])[2] + 2 for t in ts)
+    plain_launches = sum(4 + bsm.bsm_cost_plan(ctx, t["w"], t["h"], t["dmax"])["launches"] + 2 for t in ts)
     line = {
         "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_batch, "higher_is_better": True, "scaling": "weak",
@@ -318,18 +356,23 @@ def run_batch(args, cfg, world, rank, local):
         "plain": {"value": world * units / (t_plain * 1e-3) / 1e9, "ms_per_step": t_plain,
                   "pairs_per_s": world * len(ts) / (t_plain * 1e-3), "launches_per_step": plain_launches},
         "batched_over_plain": t_plain / t_batch,
+        "bound": {"plain_gap_free_ms": t_free, "plain_ms": t_plain,
+                  "launch_gap_share_of_plain": 1.0 - t_free / t_plain,
+                  "plain_over_gap_free": t_plain / t_free,
+                  "host_enqueue_s": host_enqueue_s, "delay_s": 0.2,
+                  "note": "plain_gap_free: the per-pair calls enqueued behind a 0.2 s GPU-side delay so their kernels "
+                          "run back to back; valid while host_enqueue_s < delay_s"},
         "gpu_launches": (4 + n_tc) * args.steps,
         "clocks": clocks,
         "tuning": tuning,
     }
-    if rank == 0:
-        print(json.dumps(line), flush=True)
     bsm.bsm_destroy(ctx)
+    return line
 
 
 def run_serving(args, cfg, world, rank, local):
     """Config 5: a Poisson request stream through the continuous-batching engine, against the same trace
-    processed one request at a time through the host-buffer C-ABI call."""
+    processed one request at a time through the host-buffer C-ABI call. Returns the JSON object."""
     import torch
 
     from paper_1402_2020_gb300 import bsm, synth
@@ -442,8 +485,7 @@ def run_serving(args, cfg, world, rank, local):
         "p99_speedup": p_sum["p99_ms"] / s_sum["p99_ms"],
         "engine": stats, "clocks": clocks,
     }
-    if rank == 0:
-        print(json.dumps(line), flush=True)
+    return line
 
 
 def torch_dist_done():
@@ -452,28 +494,124 @@ def torch_dist_done():
     dist.destroy_process_group()
 
 
-def cost_kernel(tuning, nw, dmax, pixels=0, mask_mode=0):
-    """(kernel name, source file, launches per call) of the cost/aggregation/WTA stage the library runs
-    for this tuning, descriptor length, disparity range and image size (the dispatch of
-    bsm_cost_aggregate_wta)."""
-    if nw > 8 or mask_mode == 2:
-        return "cost_long_kernel", "bsm_long.cu", 1
-    v = tuning["cost_variant"]
-    if nw == 8 and (v == 3 or (v == 0 and pixels * dmax >= 1280 * 720 * 128)):
-        return "cost_tc_kernel", "bsm_cost_tc.cu", 1
-    if v == 2 or (v == 0 and nw in (4, 8)):
-        need = (dmax + 7) // 8
-        split = (need + min(16, need) - 1) // min(16, need) > 1
-        return "cost2_kernel", "bsm_cost2.cu", 2 if split else 1  # + keep_disparity_bits after a split
-    return "cost_wta_kernel", "bsm_cost.cu", 1
-
-
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
             return json.load(f)
     except (OSError, ValueError):
         return {}
+
+
+_INT_RATES = None
+
+
+def int_rates():
+    """Issue rates (lanes per clock per SM) of POPC and the ALU-pipe instructions: the summary the
+    issue-rate probe wrote under profiles/ while its source is unchanged, else a live run of the probe.
+    Returns (rates, basis)."""
+    global _INT_RATES
+    if _INT_RATES is None:
+        from paper_1402_2020_gb300 import peaks
+
+        rec = peaks.load()
+        if rec is not None:
+            _INT_RATES = (rec, f"issue-rate probe, {os.path.relpath(peaks.SUMMARY, ROOT)} "
+                               f"(probe source sha256 {peaks.source_hash()})")
+        else:
+            _INT_RATES = (peaks.measure(), "issue-rate probe run live (no summary for this probe source)")
+    return _INT_RATES
+
+
+def popc_peak():
+    """Masked 32-bit popcounts per second: SMs x POPC lanes per clock x the maximum SM clock (Gpopc/s)."""
+    from paper_1402_2020_gb300 import peaks
+
+    rates, basis = int_rates()
+    r = peaks.rounded(rates, "POPC")
+    return SMS * r * MAX_SM_MHZ * 1e6 / 1e9, f"{SMS} SMs x {r:.0f} POPC/clk x {MAX_SM_MHZ} MHz ({basis})"
+
+
+def alu_peak():
+    """32-bit integer lane operations per second on the ALU pipe (LOP3 / IMNMX / VABSDIFF4 rate) (Gop/s)."""
+    from paper_1402_2020_gb300 import peaks
+
+    rates, basis = int_rates()
+    r = peaks.rounded(rates, "LOP3")
+    return SMS * r * MAX_SM_MHZ * 1e6 / 1e9, f"{SMS} SMs x {r:.0f} ALU lanes/clk (LOP3) x {MAX_SM_MHZ} MHz ({basis})"
+
+
+def host_cpu():
+    """(cores the machine has, CPU model name) of the host the oracle is timed on."""
+    model = ""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.lower().startswith("model name"):
+                model = ln.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    if not model:
+        try:
+            for ln in open("/proc/cpuinfo"):
+                if ln.lower().startswith(("model name", "cpu part")):
+                    model = ln.split(":", 1)[1].strip()
+                    break
+        except OSError:
+            pass
+    return os.cpu_count() or 1, model or "unknown"
+
+
+def pinned_to_one_core(fn):
+    """Runs fn() with this process pinned to one host core (the oracle is single-threaded; pinning keeps
+    the scheduler from moving it). Returns (fn's result, the core used)."""
+    try:
+        before = os.sched_getaffinity(0)
+    except (AttributeError, OSError):
+        return fn(), None
+    core = max(before)
+    os.sched_setaffinity(0, {core})
+    try:
+        return fn(), core
+    finally:
+        os.sched_setaffinity(0, before)
+
+
+def refine_roofline(kname, dL, dR, dmax, R, lr_tol, seconds):
+    """Eq. 9-10 as instruction work: the vote window of every pixel that fails the left/right check.
+    Per window position (clipped to the image) one load and one test of the voter's validity; per valid
+    voter eight more (its colour word, the CIELAB SAD as a four-way absolute difference and a byte sum,
+    the two table reads, the product, the shift and the histogram add); per invalid pixel the histogram
+    clear and the argmax scan over dmax; per pixel the left/right check (two loads, two tests). Peak:
+    the SM's instruction issue rate (4 schedulers x 32 lanes per clock) x SMs x the maximum clock."""
+    dL = np.asarray(dL, np.int64)
+    dR = np.asarray(dR, np.int64)
+    h, w = dL.shape
+    ys, xs = np.mgrid[0:h, 0:w]
+    xr = xs - dL
+    inside = xr >= 0
+    partner = dR[ys, np.clip(xr, 0, w - 1)]
+    valid = inside & (np.abs(dL - partner) <= lr_tol)
+    invalid = ~valid
+    # window positions and valid voters per pixel: 2-D box sums over (2R+1)^2 (clipped), by cumulative sums
+    def box(a):
+        c = np.zeros((h + 1, w + 1), np.int64)
+        c[1:, 1:] = a.cumsum(0).cumsum(1)
+        y0, y1 = np.clip(np.arange(h) - R, 0, h), np.clip(np.arange(h) + R + 1, 0, h)
+        x0, x1 = np.clip(np.arange(w) - R, 0, w), np.clip(np.arange(w) + R + 1, 0, w)
+        return c[y1][:, x1] - c[y0][:, x1] - c[y1][:, x0] + c[y0][:, x0]
+    positions = int(box(np.ones((h, w), np.int64))[invalid].sum())
+    voters = int(box(valid.astype(np.int64))[invalid].sum())
+    n_inv = int(invalid.sum())
+    ops = 2 * positions + 8 * voters + 2 * dmax * n_inv + 4 * h * w
+    peak = SMS * ISSUE_PER_CLK_SM * MAX_SM_MHZ * 1e6 / 1e9
+    achieved = ops / seconds / 1e9
+    return {"bound": "issue", "kernel": kname, "achieved": achieved, "peak": peak, "unit": "Ginstr/s",
+            "frac": achieved / peak, "traffic": None, "work_per_launch": ops,
+            "peak_basis": f"{SMS} SMs x 4 schedulers x 32 lanes/clk x {MAX_SM_MHZ} MHz",
+            "invalid_pixels": n_inv, "window_positions": positions, "valid_voters": voters,
+            "note": "lane instructions of Eq. 9-10: 2 per window position, 8 per valid voter, 2 dmax per invalid "
+                    "pixel, 4 per pixel for the left/right check; the near-valid pre-pass is in the stage time"}
 
 
 def describe_kernel(tuning, nw):
@@ -492,11 +630,11 @@ def describe_roofline(kname, pixels, n_bits, seconds, traffic):
     their maximum, Eq. 7's comparison with T, and one comparison per pair for Eq. 6's k-th smallest weight
     (a linear-time selection). Peak: the ALU pipe's lanes per clock x SMs x the maximum SM clock."""
     ops = 8 * n_bits * pixels
-    peak = SMS * ALU_PER_CLK_SM * MAX_SM_MHZ * 1e6 / 1e9
+    peak, basis = alu_peak()
     achieved = ops / seconds / 1e9
     return {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": peak, "unit": "Gop/s",
             "frac": achieved / peak, "traffic": traffic, "work_per_launch": ops,
-            "peak_basis": f"{SMS} SMs x {ALU_PER_CLK_SM} ALU lanes/clk x {MAX_SM_MHZ} MHz",
+            "peak_basis": basis,
             "note": "one view per launch; the T search's bisection and the ballots run on top of the minimum"}
 
 
@@ -598,14 +736,15 @@ def run_pair(args, cfg, world, rank, local, n_bits=N_BITS, window_S=WINDOW_S, si
     value = world * units / (t_step * 1e-3) / 1e9
 
     tuning = bsm.bsm_get_tuning(ctx)
-    kname, kfile, klaunch = cost_kernel(tuning, nw, dmax, w * h)
+    plan = bsm.bsm_cost_plan(ctx, w, h, dmax)
+    kname, kfile, klaunch = plan["name"], plan["source"], plan["launches"]
     bad = bad_pixel_rate(out.cpu().numpy(), gt)
     # rooflines: the cost stage (fused cost/aggregation/WTA, both reference views per launch) and describe
     # (one view per launch); "roofline" is the one of the two that takes more of the step
     t_k2 = float(per[:, 2].mean()) * 1e-3
     word_ops = 2 * units * nw
     achieved = word_ops / t_k2 / 1e9
-    peak = SMS * POPC_PER_CLK_SM * MAX_SM_MHZ * 1e6 / 1e9
+    peak, popc_basis = popc_peak()
     workload_key = args.config if n_bits == N_BITS else f"{args.config}_n{n_bits}"
     traffic = profile_traffic(kfile, workload_key)
     dname, dfile = describe_kernel(tuning, nw)
@@ -614,7 +753,7 @@ def run_pair(args, cfg, world, rank, local, n_bits=N_BITS, window_S=WINDOW_S, si
     roof_cost = ({"bound": "alu", "kernel": kname, "achieved": achieved, "peak": peak,
                   "unit": "Gpopc/s", "frac": achieved / peak, "traffic": traffic,
                   "work_per_launch": word_ops,
-                  "peak_basis": f"{SMS} SMs x {POPC_PER_CLK_SM} POPC/clk x {MAX_SM_MHZ} MHz"}
+                  "peak_basis": popc_basis}
                  if kname != "cost_tc_kernel" else tensor_roofline(units, n_bits, t_k2, traffic))
     roof_cost["xd_per_s_per_direction"] = units / t_k2  # one launch covers both reference views
     if kname == "cost_tc_kernel":
@@ -623,6 +762,41 @@ def run_pair(args, cfg, world, rank, local, n_bits=N_BITS, window_S=WINDOW_S, si
         roof_cost["popc_equivalent"] = {"achieved": achieved, "peak": peak, "unit": "Gpopc/s",
                                         "frac": achieved / peak}
     describe_dominant = t_desc > t_k2
+    if kname == "cost_tc_kernel" and not sgm and args.cost_variant == 0:
+        # the popcount formulation of Eq. 8 (the two-column kernel) on the same planes, timed apart, against
+        # its own integer roofline: the design the tensor-core kernel replaced, reported beside it
+        saved = bsm.bsm_get_tuning(ctx)
+        try:
+            bsm.bsm_set_tuning(ctx, 0, 0, saved["batch_rows"], 2, saved["describe_variant"])
+            ep = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+            with torch.cuda.stream(stream):
+                for _ in range(2):
+                    bsm.bsm_cost_aggregate_wta(ctx, BL, PL, BR, PR, w, h, dmax, dL, dR, None, s)
+                reps = 5
+                ep[0].record(stream)
+                for _ in range(reps):
+                    bsm.bsm_cost_aggregate_wta(ctx, BL, PL, BR, PR, w, h, dmax, dL, dR, None, s)
+                ep[1].record(stream)
+                torch.cuda.synchronize()
+            t_pc = ep[0].elapsed_time(ep[1]) * 1e-3 / reps
+            pplan = bsm.bsm_cost_plan(ctx, w, h, dmax)
+            pk, pname = pplan["name"], pplan["source"]
+            roof_cost["popcount_kernel"] = {
+                "bound": "alu", "kernel": pk, "achieved": word_ops / t_pc / 1e9, "peak": peak, "unit": "Gpopc/s",
+                "frac": word_ops / t_pc / 1e9 / peak, "stage_ms": t_pc * 1e3,
+                "traffic": profile_traffic(pname, workload_key), "peak_basis": popc_basis,
+                "note": "the two-column popcount kernel timed on the same planes (not part of the step)"}
+        finally:
+            bsm.bsm_set_tuning(ctx, saved["cost_rows"], saved["cost_popc_plain"], saved["batch_rows"],
+                               saved["cost_variant"], saved["describe_variant"])
+            with torch.cuda.stream(stream):  # the maps of the last timed step again, from the step's own kernel
+                bsm.bsm_cost_aggregate_wta(ctx, BL, PL, BR, PR, w, h, dmax, dL, dR, None, s)
+            torch.cuda.synchronize()
+    rname = "refine_kernel"
+    roof_ref = None
+    if not sgm:
+        roof_ref = refine_roofline(rname, dL.cpu().numpy(), dR.cpu().numpy(), dmax, VOTE_R, 1,
+                                   float(per[:, 3].mean()) * 1e-3)
     line = {
         "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_step, "higher_is_better": True, "scaling": "weak",
@@ -642,6 +816,7 @@ def run_pair(args, cfg, world, rank, local, n_bits=N_BITS, window_S=WINDOW_S, si
         ("roofline_cost" if describe_dominant else "roofline_describe"): roof_cost if describe_dominant else roof_desc,
         "clocks": clocks,
         "tuning": tuning,
+        "cost_plan": plan,
     }
     if sgm:
         line["config"]["sgm"] = {"P1": sgm[0], "P2": sgm[1], "paths": sgm[2]}
@@ -684,10 +859,15 @@ def run_pair(args, cfg, world, rank, local, n_bits=N_BITS, window_S=WINDOW_S, si
         e2e_s = max_over_ranks([e2e_s], world, dev)[0]
         line["e2e"] = {"value": world * units / e2e_s / 1e9, "unit": METRIC, "h2d_bytes_per_step": 2 * h * pitch,
                        "d2h_bytes_per_step": 4 * w * h, "ms_per_step": e2e_s * 1e3}
+    if roof_ref is not None:
+        line["roofline_refine"] = roof_ref
     if cpu_baseline and rank == 0 and world == 1 and not args.no_cpu_baseline:
-        dt, u = oracle_sample(cfg, 32)
+        (dt, u), core = pinned_to_one_core(lambda: oracle_sample(cfg, 32))
+        nproc, model = host_cpu()
         line["cpu_baseline"] = {"value": u / dt / 1e9, "unit": METRIC, "cores": 1, "kind": "oracle",
-                                "sample": f"{w}x32 row band of the workload, whole oracle pipeline, single thread"}
+                                "sample": f"{w}x32 row band of the workload (rows {h // 2 - 16}..{h // 2 + 15}), whole "
+                                          f"oracle pipeline, single thread pinned to host core {core}",
+                                "seconds": dt, "nproc": nproc, "cpu_model": model}
     bsm.bsm_destroy(ctx)
     return line
 
@@ -776,24 +956,49 @@ def run_sweep_n(args, cfg, world, rank, local):
             print(json.dumps(line), flush=True)
 
 
+def run_default(args, world, rank, local):
+    """The headline: the 3840 x 2160 pair (the largest single-GPU configuration, the one the fused cost
+    kernel's roofline is judged on), with the batched (c3) and served (c5) objects in the same line."""
+    args.config = "c4"
+    line = run_pair(args, CONFIGS["c4"], world, rank, local)
+    if not args.no_batched:
+        b = run_batch(args, CONFIGS["c3"], world, rank, local)
+        b["workload"] = CONFIGS["c3"]["name"]
+        line["batched"] = b
+    if not args.no_served:
+        sv = run_serving(args, CONFIGS["c5"], world, rank, local)
+        sv["workload"] = CONFIGS["c5"]["name"]
+        line["served"] = sv
+    return line
+
+
 def main():
     args = parse()
-    cfg = CONFIGS[args.config]
     world, rank, local = dist_init(args)
     if args.impl == "reference":
-        run_reference(args, cfg, world, rank)
+        run_reference(args, CONFIGS[args.config or "c4"], world, rank)
         return
-    if args.config in ("c3", "c5"):
-        (run_batch if args.config == "c3" else run_serving)(args, cfg, world, rank, local)
-    elif args.sweep_n:
-        run_sweep_n(args, cfg, world, rank, local)
-    elif args.quality:
-        run_quality(args, cfg, world, rank, local)
-    else:
-        agg = AGG if args.n_bits * AGG * AGG <= 65535 else 3  # the 16-bit aggregated cost bounds n * W^2
-        line = run_pair(args, cfg, world, rank, local, n_bits=args.n_bits, agg=agg)
+    cfg = CONFIGS.get(args.config)
+    if not args.config and not (args.sweep_n or args.quality):
+        line = run_default(args, world, rank, local)
         if rank == 0:
             print(json.dumps(line), flush=True)
+    elif args.config in ("c3", "c5"):
+        line = (run_batch if args.config == "c3" else run_serving)(args, cfg, world, rank, local)
+        if rank == 0:
+            print(json.dumps(line), flush=True)
+    else:
+        if not args.config:
+            args.config, cfg = "c2", CONFIGS["c2"]
+        if args.sweep_n:
+            run_sweep_n(args, cfg, world, rank, local)
+        elif args.quality:
+            run_quality(args, cfg, world, rank, local)
+        else:
+            agg = AGG if args.n_bits * AGG * AGG <= 65535 else 3  # the 16-bit aggregated cost bounds n * W^2
+            line = run_pair(args, cfg, world, rank, local, n_bits=args.n_bits, agg=agg)
+            if rank == 0:
+                print(json.dumps(line), flush=True)
     if world > 1:
         torch_dist_done()
 

@@ -205,7 +205,9 @@ typedef struct bsm_server bsm_server;
 typedef struct {
   int32_t lanes;          /* batches in flight at once, 1..8 */
   int32_t max_batch;      /* requests per batch, 1..BSM_MAX_BATCH */
-  int64_t device_budget;  /* bytes of request buffers the engine may hold; 0 selects half the free memory */
+  int64_t device_budget;  /* bytes of device memory the engine may hold for request buffers and its lanes'
+                             colour-plane scratch (4 bytes per pixel of a lane's largest batch and of its
+                             largest per-pair request, kept once reserved); 0 selects half the free memory */
   int64_t max_batch_work; /* cap on a batch's sum of w * h * dmax (a larger request still runs alone);
                              0 = no cap. Keeps large requests from holding small ones in one batch. */
 } bsm_server_config;
@@ -225,14 +227,15 @@ typedef struct {
 
 typedef struct {
   int64_t submitted, completed, failed, batches, max_batch_seen, queued, bytes_in_use, budget;
+  int64_t scratch_bytes;  /* lane scratch reserved so far, charged to the budget beside bytes_in_use */
 } bsm_server_stats;
 
 /* Start an engine (creates `lanes` contexts: synchronous, allocates). BSM_ERR_UNSUPPORTED for
  * n_bits > 256 or mask_mode BSM_MASK_BOTH, which the batched kernels do not serve. */
 bsm_status bsm_server_create(const bsm_params *params, const bsm_server_config *cfg, bsm_server **out);
 
-/* Queue a request (any thread, non-blocking). A malformed request, or one larger than the whole
- * budget, completes at once with BSM_ERR_INVALID_ARG, which is also returned here. */
+/* Queue a request (any thread, non-blocking). A malformed request, or one whose buffers and lane
+ * scratch exceed the whole budget, completes at once with BSM_ERR_INVALID_ARG, also returned here. */
 bsm_status bsm_server_submit(bsm_server *s, const bsm_request *req);
 
 /* Up to max_out completions; waits up to timeout_us for the first (0: none, < 0: forever).
@@ -258,11 +261,19 @@ void bsm_server_destroy(bsm_server *s);
  * allocation use this call instead. It computes exactly what bsm_describe computes, with the same
  * arguments, requirements and outputs, and allocates nothing:
  *   - its scratch is one fixed array of BSM_NOALLOC_MAX_PIXELS colour words (16 MiB) in the
- *     library's device code, which every GPU that loads the library holds until the process exits;
+ *     library's device code, which every GPU that loads it holds until the process exits. The CUDA
+ *     driver reserves those 16 MiB when it loads the module that holds the array: at library load
+ *     with eager module loading, or, with CUDA's default lazy loading, at this call's first use on
+ *     each device; make that first call during set-up, while memory is still free;
  *   - images with w * h > BSM_NOALLOC_MAX_PIXELS are rejected with BSM_ERR_INVALID_ARG;
  *   - the context must already exist (bsm_create allocates; create it during set-up);
- *   - the first call on a device looks up that device's address of the array (a host-side lookup,
- *     no allocation); make that first call before any stream capture;
+ *   - the first call on a device looks up that device's address of the array with the device current
+ *     and caches it (a host-side lookup; no cudaMalloc); make that first call before any stream
+ *     capture. The cached address belongs to the current CUDA context of that device: after
+ *     cudaDeviceReset do not call this function again in the same process;
+ *   - errors map as bsm_describe's do (a failed lookup or launch returns BSM_ERR_CUDA, or
+ *     BSM_ERR_OUT_OF_MEMORY when the driver could not load the module, with the CUDA error recorded
+ *     for bsm_last_cuda_error);
  *   - every call on a device shares the one array, and each call overwrites every word it reads,
  *     so nothing needs clearing between calls; two calls that overlap on the GPU (different streams
  *     without ordering) race on the array and give undefined results.
@@ -306,7 +317,11 @@ bsm_status bsm_last_error(bsm_ctx *ctx);
  * Test hooks for failure detection (off by default; every hook only withholds work, it never faults).
  *   BSM_DEBUG_WITHHOLD_ARRIVALS (1): value 1 makes the cost kernels' staging thread skip its mbarrier
  *     arrivals, so every bounded wait of the next cost launch runs out (about a second per wave of
- *     CTAs); the kernel then latches BSM_ERR_TIMEOUT and returns, and the context stays usable.
+ *     CTAs); the kernel then latches BSM_ERR_TIMEOUT and returns, and the context stays usable. It
+ *     reaches the one-column kernel (cost_variant 0, 1 or 2: the two-column kernel completes its copies
+ *     by cp.async groups and has no wait to withhold) and, with cost_variant 3, the tensor-core kernel,
+ *     whose producer then issues no copies, so its operand builders', MMA issuer's and epilogue's waits
+ *     all run out; no disparity of the launch is written.
  */
 #define BSM_DEBUG_WITHHOLD_ARRIVALS 1
 bsm_status bsm_debug_set(bsm_ctx *ctx, int32_t key, int32_t value);
@@ -357,6 +372,19 @@ typedef struct {
 /* Set / read the context's launch shapes. Synchronous, host only. */
 bsm_status bsm_set_tuning(bsm_ctx *ctx, const bsm_tuning *tuning);
 bsm_status bsm_get_tuning(bsm_ctx *ctx, bsm_tuning *tuning);
+
+/* The cost / aggregation / WTA launch that bsm_cost_aggregate_wta and bsm_cost_volumes make for a
+   w x h pair with this dmax under the context's current tuning (Eq. 8, box aggregation, Eq. 1): which
+   kernel, and the output rows per CTA row band (band b covers rows [b rows_per_band, (b + 1)
+   rows_per_band); every band reads rows_per_band + agg_window - 1 input rows). Host only, no GPU work;
+   for tests that place checks on band boundaries and for profiling. BSM_ERR_INVALID_ARG on bad sizes. */
+typedef struct {
+  int32_t kernel;         /* 1 one column per lane, 2 two columns per lane, 3 tensor cores, 4 long descriptors */
+  int32_t rows_per_band;  /* output rows per CTA band */
+  int32_t launches;       /* kernel launches per call */
+  int32_t reserved;
+} bsm_cost_plan_info;
+bsm_status bsm_cost_plan(bsm_ctx *ctx, int32_t w, int32_t h, int32_t dmax, bsm_cost_plan_info *out);
 
 /* Validate parameters without touching the GPU: the checks bsm_create performs first. */
 bsm_status bsm_validate_params(const bsm_params *params);

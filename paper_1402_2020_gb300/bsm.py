@@ -29,7 +29,7 @@ EXPORTED = (
     "bsm_abi_version", "bsm_set_tuning", "bsm_get_tuning", "bsm_reserve", "bsm_describe_noalloc",
     "bsm_batch_run", "bsm_reserve_batch", "bsm_last_cuda_error", "bsm_server_create", "bsm_server_submit",
     "bsm_server_poll", "bsm_server_drain", "bsm_server_get_stats", "bsm_server_destroy", "bsm_debug_set",
-    "bsm_cost_volumes", "bsm_sgm",
+    "bsm_cost_volumes", "bsm_sgm", "bsm_cost_plan",
 )
 BSM_DEBUG_WITHHOLD_ARRIVALS = 1
 BSM_MAX_BATCH = 1024
@@ -68,6 +68,15 @@ class bsm_tuning(ctypes.Structure):
                 ("reserved", ctypes.c_int32 * 3)]
 
 
+class bsm_cost_plan_info(ctypes.Structure):
+    _fields_ = [("kernel", ctypes.c_int32), ("rows_per_band", ctypes.c_int32), ("launches", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+COST_KERNELS = {1: ("cost_wta_kernel", "bsm_cost.cu"), 2: ("cost2_kernel", "bsm_cost2.cu"),
+                3: ("cost_tc_kernel", "bsm_cost_tc.cu"), 4: ("cost_long_kernel", "bsm_long.cu")}
+
+
 class bsm_pair_desc(ctypes.Structure):
     _fields_ = [("rgbL", ctypes.c_void_p), ("rgbR", ctypes.c_void_p), ("w", ctypes.c_int32), ("h", ctypes.c_int32),
                 ("pitch_bytes", ctypes.c_int32), ("dmax", ctypes.c_int32), ("BL", ctypes.c_void_p),
@@ -92,7 +101,7 @@ class bsm_completion(ctypes.Structure):
 
 class bsm_server_stats(ctypes.Structure):
     _fields_ = [(k, ctypes.c_int64) for k in ("submitted", "completed", "failed", "batches", "max_batch_seen",
-                                              "queued", "bytes_in_use", "budget")]
+                                              "queued", "bytes_in_use", "budget", "scratch_bytes")]
 
 
 _lib = None
@@ -152,6 +161,8 @@ def lib():
         L.bsm_server_destroy.restype = None
         L.bsm_debug_set.argtypes = [P, I, I]
         L.bsm_debug_set.restype = S
+        L.bsm_cost_plan.argtypes = [P, I, I, I, ctypes.POINTER(bsm_cost_plan_info)]
+        L.bsm_cost_plan.restype = S
         L.bsm_last_cuda_error.argtypes = [P]
         L.bsm_last_cuda_error.restype = ctypes.c_char_p
         L.bsm_batch_run.argtypes = [P, ctypes.POINTER(bsm_pair_desc), I, P]
@@ -314,6 +325,16 @@ def bsm_set_tuning(ctx: int, cost_rows: int = 0, cost_popc_plain: int = 0, batch
     t.cost_variant = cost_variant
     t.describe_variant = describe_variant
     _check(lib().bsm_set_tuning(ctx, ctypes.byref(t)), "bsm_set_tuning")
+
+
+def bsm_cost_plan(ctx: int, w: int, h: int, dmax: int) -> dict:
+    """The cost launch bsm_cost_aggregate_wta makes for this shape: kernel id (1..4), its name and source
+    file, output rows per CTA band, launches per call."""
+    p = bsm_cost_plan_info()
+    _check(lib().bsm_cost_plan(ctx, w, h, dmax, ctypes.byref(p)), "bsm_cost_plan")
+    name, src = COST_KERNELS[p.kernel]
+    return {"kernel": p.kernel, "name": name, "source": src, "rows_per_band": p.rows_per_band,
+            "launches": p.launches}
 
 
 def bsm_get_tuning(ctx: int) -> dict:

@@ -1,4 +1,5 @@
-"""Build libbsm.so in-tree for sm_103a: one nvcc process per translation unit, then one link.
+"""Build libbsm.so in-tree for sm_103a: one nvcc process per translation unit, then one link; and
+libbsm_probe.so, the instruction issue-rate probe behind the integer rooflines (probe/issue_rate.cu).
 
 Usage: python -m paper_1402_2020_gb300.build [--force] [--verbose]
 """
@@ -12,6 +13,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT, "libbsm.so")
+PROBE_SRC = os.path.join(HERE, "probe", "issue_rate.cu")
+PROBE_LIB = os.path.join(OUT, "libbsm_probe.so")
 ROOT = os.path.dirname(HERE)
 INCLUDE = os.path.join(ROOT, "include")
 
@@ -36,10 +39,23 @@ def _deps():
 
 
 def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+    if not os.path.exists(LIB) or not os.path.exists(PROBE_LIB):
         return False
     t = os.path.getmtime(LIB)
-    return all(os.path.getmtime(d) <= t for d in _deps())
+    return all(os.path.getmtime(d) <= t for d in _deps()) and os.path.getmtime(PROBE_SRC) <= os.path.getmtime(
+        PROBE_LIB)
+
+
+def _probe(verbose: bool) -> str:
+    tmp = PROBE_LIB + ".tmp"
+    cmd = [nvcc(), *ARCH, *FLAGS, "-shared", PROBE_SRC, "-o", tmp]
+    if verbose:
+        cmd += ["-Xptxas", "-v"]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(f"nvcc failed on {PROBE_SRC}:\n{r.stdout}\n{r.stderr}")
+    os.replace(tmp, PROBE_LIB)
+    return PROBE_LIB
 
 
 def _compile(src: str, verbose: bool) -> str:
@@ -60,8 +76,10 @@ def build(force: bool = False, verbose: bool = False) -> str:
         return LIB
     os.makedirs(OUT, exist_ok=True)
     srcs = sources()
-    with cf.ThreadPoolExecutor(max_workers=min(len(srcs), os.cpu_count() or 4)) as ex:
+    with cf.ThreadPoolExecutor(max_workers=min(len(srcs) + 1, os.cpu_count() or 4)) as ex:
+        probe = ex.submit(_probe, verbose)
         objs = list(ex.map(lambda s: _compile(s, verbose), srcs))
+        probe.result()
     tmp = LIB + ".tmp"
     cmd = [nvcc(), *ARCH, "-shared", "-o", tmp, *objs]
     r = subprocess.run(cmd, capture_output=True, text=True)

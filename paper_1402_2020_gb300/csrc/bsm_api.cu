@@ -52,7 +52,7 @@ cudaError_t ensure_plane(bsm_ctx *ctx, size_t pixels) {
 
 extern "C" {
 
-int32_t bsm_abi_version(void) { return 2; }
+int32_t bsm_abi_version(void) { return 3; }
 
 const char *bsm_status_string(bsm_status s) {
   switch (s) {
@@ -361,6 +361,16 @@ bsm_status bsm_get_tuning(bsm_ctx *ctx, bsm_tuning *t) {
   t->batch_rows = ctx->batch_rows;
   t->cost_variant = ctx->cost_variant;
   t->describe_variant = ctx->describe_variant;
+  return BSM_OK;
+}
+
+bsm_status bsm_cost_plan(bsm_ctx *ctx, int32_t w, int32_t h, int32_t dmax, bsm_cost_plan_info *out) {
+  if (ctx == nullptr || out == nullptr || !size_ok(w, h) || dmax < 1 || dmax > ctx->p.dmax) return BSM_ERR_INVALID_ARG;
+  const bsm::CostPlan p = bsm::cost_plan(ctx, w, h, dmax);
+  std::memset(out, 0, sizeof(*out));
+  out->kernel = p.kernel;
+  out->rows_per_band = p.rows;
+  out->launches = p.launches;
   return BSM_OK;
 }
 

@@ -531,26 +531,39 @@ int pick_rows(int w, int h, int win, int dmax) {
 
 }  // namespace
 
+int cost1_rows(const bsm_ctx *ctx, int w, int h, int dmax) {
+  return ctx->cost_rows > 0 ? ctx->cost_rows : pick_rows(w, h, ctx->p.agg_window, dmax);
+}
+
+CostPlan cost_plan(const bsm_ctx *ctx, int w, int h, int dmax) {
+  if (ctx->nw > 8 || ctx->p.mask_mode == BSM_MASK_BOTH) return {4, cost_long_rows(ctx, w, h, dmax), 1};
+  // tensor cores when asked for, and by default for pairs large enough to fill the GPU with them; the
+  // two-column kernel has no staging wait to withhold, so the failure-detection hook keeps the
+  // one-column kernel unless the tensor-core kernel was asked for
+  const bool tc = ctx->cost_variant == 3 || (ctx->cost_variant == 0 && (long long)w * h * dmax >= kTcAutoWork);
+  if (tc && cost_tc_supported(ctx) && (!ctx->withhold_arrivals || ctx->cost_variant == 3))
+    return {3, cost_tc_rows(ctx, w, h, dmax), 1};
+  if (ctx->cost_variant != 1 && cost2_supported(ctx) && !ctx->withhold_arrivals) {
+    const bool split = (dmax + 7) / 8 > 16;  // more 8-disparity groups than the two-column kernel's 16 warps
+    return {2, cost2_rows(ctx, w, h, dmax), split ? 2 : 1};
+  }
+  return {1, cost1_rows(ctx, w, h, dmax), 1};
+}
+
 cudaError_t launch_cost_wta(const bsm_ctx *ctx, const uint32_t *BL, const uint32_t *PhiL, const uint32_t *BR,
                             const uint32_t *PhiR, int w, int h, int dmax, int32_t *dL, int32_t *dR, uint16_t *costL,
                             uint16_t *costR, cudaStream_t s) {
-  if (ctx->nw > 8 || ctx->p.mask_mode == BSM_MASK_BOTH)
-    return launch_cost_long(ctx, BL, PhiL, BR, PhiR, w, h, dmax, dL, dR, costL, costR, s);
-  // tensor cores when asked for, and by default for pairs large enough to fill the GPU with them
-  const bool tc = ctx->cost_variant == 3 || (ctx->cost_variant == 0 && (long long)w * h * dmax >= kTcAutoWork);
-  if (tc && cost_tc_supported(ctx) && !ctx->withhold_arrivals)
-    return launch_cost_tc(ctx, BL, PhiL, BR, PhiR, w, h, dmax, dL, dR, costL, costR, s);
-  // The two-column kernel has no staging wait to withhold, so the failure-detection hook keeps the
-  // one-column kernel.
-  if (ctx->cost_variant != 1 && cost2_supported(ctx) && !ctx->withhold_arrivals)
-    return launch_cost2(ctx, BL, PhiL, BR, PhiR, w, h, dmax, dL, dR, costL, costR, s);
+  const CostPlan plan = cost_plan(ctx, w, h, dmax);
+  if (plan.kernel == 4) return launch_cost_long(ctx, BL, PhiL, BR, PhiR, w, h, dmax, dL, dR, costL, costR, s);
+  if (plan.kernel == 3) return launch_cost_tc(ctx, BL, PhiL, BR, PhiR, w, h, dmax, dL, dR, costL, costR, s);
+  if (plan.kernel == 2) return launch_cost2(ctx, BL, PhiL, BR, PhiR, w, h, dmax, dL, dR, costL, costR, s);
   CostArgs a{};
   a.B[0] = BL; a.Phi[0] = PhiL; a.O[0] = BR; a.disp[0] = dL;
   a.B[1] = BR; a.Phi[1] = PhiR; a.O[1] = BL; a.disp[1] = dR;
   a.cost[0] = costL; a.cost[1] = costR;
   a.status = ctx->status;
   a.w = w; a.h = h; a.dmax = dmax;
-  a.rows = ctx->cost_rows > 0 ? ctx->cost_rows : pick_rows(w, h, ctx->p.agg_window, dmax);
+  a.rows = plan.rows;
   a.withhold = ctx->withhold_arrivals;
   switch (ctx->nw) {
     case 1: return launch_win<1, false>(ctx->p.agg_window, a, s);

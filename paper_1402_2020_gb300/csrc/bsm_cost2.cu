@@ -393,6 +393,13 @@ int pick_rows2(int w, int h, int win, int ctas_z) {
 
 bool cost2_supported(const bsm_ctx *ctx) { return ctx->nw == 4 || ctx->nw == 8; }
 
+int cost2_rows(const bsm_ctx *ctx, int w, int h, int dmax) {
+  const int need = (dmax + kDC - 1) / kDC;
+  const int nwarps = min(kMaxWarps, need);
+  const int ndr = (need + nwarps - 1) / nwarps;
+  return ctx->cost_rows > 0 ? ctx->cost_rows : pick_rows2(w, h, ctx->p.agg_window, 2 * ndr);
+}
+
 cudaError_t launch_cost2(const bsm_ctx *ctx, const uint32_t *BL, const uint32_t *PhiL, const uint32_t *BR,
                          const uint32_t *PhiR, int w, int h, int dmax, int32_t *dL, int32_t *dR, uint16_t *costL,
                          uint16_t *costR, cudaStream_t s) {
@@ -404,7 +411,7 @@ cudaError_t launch_cost2(const bsm_ctx *ctx, const uint32_t *BL, const uint32_t 
   const int need = (dmax + kDC - 1) / kDC;
   const int nwarps = min(kMaxWarps, need);
   a.ndr = (need + nwarps - 1) / nwarps;
-  a.rows = ctx->cost_rows > 0 ? ctx->cost_rows : pick_rows2(w, h, ctx->p.agg_window, 2 * a.ndr);
+  a.rows = cost2_rows(ctx, w, h, dmax);
   const bool split = a.ndr > 1;
   cudaError_t e = cudaSuccess;
   if (split) {

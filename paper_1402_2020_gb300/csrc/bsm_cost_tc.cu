@@ -28,7 +28,8 @@
 //      terms into a shared [x][d] table, then slide the horizontal box sum along x on packed 16-bit pairs
 //      and reduce (A << 3 | d % 8) keys with min.u16x2 and one warp-wide minimum of (A << 8 | d): Eq. 1's
 //      smallest d. This overlaps the next row's MMAs.
-// Every wait is bounded; a wait that gives up latches BSM_ERR_TIMEOUT and the CTA winds down.
+// Every wait is bounded; a wait that gives up latches BSM_ERR_TIMEOUT and the CTA winds down. The
+// failure-detection hook (withhold) makes the producer issue no copies, so every wait runs out.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
@@ -80,6 +81,7 @@ struct TcArgs {
   uint16_t *cost[2];
   uint32_t *status;
   int w, h, dmax, rows;
+  int withhold;           // test hook: the producer issues no copies, so every wait on them runs out
 };
 
 __device__ __forceinline__ uint32_t saddr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -265,7 +267,7 @@ __device__ __forceinline__ void cost_tc_body(const TcArgs &a, uint8_t *smem) {
 
   if (warp == 0) {
     // ---- producer: per input row the other view's words, per chunk the A operand, in order
-    if (lane == 0) {
+    if (lane == 0 && !a.withhold) {
       const uint32_t rowbytes = (uint32_t)(256 * 32 + (nb1 > 0 ? 128 * 32 : 0));
       bool ok = true;
       int last = -1;  // the last input row whose copies were issued
@@ -671,6 +673,11 @@ bool desc_map(CUtensorMap *map, const void *base, int w, int h, int cols) {
 
 bool cost_tc_supported(const bsm_ctx *ctx) { return ctx->nw == 8 && ctx->p.mask_mode != BSM_MASK_BOTH; }
 
+int cost_tc_rows(const bsm_ctx *ctx, int w, int h, int dmax) {
+  (void)dmax;
+  return ctx->cost_rows > 0 ? ctx->cost_rows : pick_rows_tc(w, h, ctx->p.agg_window);
+}
+
 cudaError_t launch_cost_tc(const bsm_ctx *ctx, const uint32_t *BL, const uint32_t *PhiL, const uint32_t *BR,
                            const uint32_t *PhiR, int w, int h, int dmax, int32_t *dL, int32_t *dR, uint16_t *costL,
                            uint16_t *costR, cudaStream_t s) {
@@ -685,7 +692,8 @@ cudaError_t launch_cost_tc(const bsm_ctx *ctx, const uint32_t *BL, const uint32_
   a.cost[0] = costL; a.cost[1] = costR;
   a.status = ctx->status;
   a.w = w; a.h = h; a.dmax = dmax;
-  a.rows = ctx->cost_rows > 0 ? ctx->cost_rows : pick_rows_tc(w, h, ctx->p.agg_window);
+  a.rows = cost_tc_rows(ctx, w, h, dmax);
+  a.withhold = ctx->withhold_arrivals;
   switch (ctx->p.agg_window) {
     case 1: return launch_tc_t<1>(a, s);
     case 3: return launch_tc_t<3>(a, s);

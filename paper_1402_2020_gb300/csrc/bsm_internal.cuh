@@ -131,6 +131,18 @@ cudaError_t launch_cost_long(const bsm_ctx *ctx, const uint32_t *BL, const uint3
                              cudaStream_t s);
 bool cost2_supported(const bsm_ctx *ctx);
 bool cost_tc_supported(const bsm_ctx *ctx);
+// Output rows per CTA band of each cost kernel for a w x h pair (the context's cost_rows, else the
+// kernel's heuristic), and the plan launch_cost_wta follows.
+int cost1_rows(const bsm_ctx *ctx, int w, int h, int dmax);
+int cost2_rows(const bsm_ctx *ctx, int w, int h, int dmax);
+int cost_tc_rows(const bsm_ctx *ctx, int w, int h, int dmax);
+int cost_long_rows(const bsm_ctx *ctx, int w, int h, int dmax);
+struct CostPlan {
+  int kernel;  // 1 one column per lane, 2 two columns per lane, 3 tensor cores, 4 long descriptors
+  int rows;
+  int launches;
+};
+CostPlan cost_plan(const bsm_ctx *ctx, int w, int h, int dmax);
 cudaError_t launch_cost_tc(const bsm_ctx *ctx, const uint32_t *BL, const uint32_t *PhiL, const uint32_t *BR,
                            const uint32_t *PhiR, int w, int h, int dmax, int32_t *dL, int32_t *dR, uint16_t *costL,
                            uint16_t *costR, cudaStream_t s);

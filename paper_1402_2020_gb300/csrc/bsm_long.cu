@@ -398,6 +398,12 @@ void wide_offsets(const bsm_ctx *ctx, int32_t *out) {
   }
 }
 
+int cost_long_rows(const bsm_ctx *ctx, int w, int h, int dmax) {
+  (void)w;
+  (void)dmax;
+  return ctx->cost_rows > 0 ? ctx->cost_rows : (h >= 256 ? 64 : 16);
+}
+
 cudaError_t launch_cost_long(const bsm_ctx *ctx, const uint32_t *BL, const uint32_t *PhiL, const uint32_t *BR,
                              const uint32_t *PhiR, int w, int h, int dmax, int32_t *dL, int32_t *dR, uint16_t *costL,
                              uint16_t *costR, cudaStream_t s) {
@@ -406,7 +412,7 @@ cudaError_t launch_cost_long(const bsm_ctx *ctx, const uint32_t *BL, const uint3
   a.B[1] = BR; a.Phi[1] = PhiR; a.O[1] = BL; a.OPhi[1] = PhiL; a.disp[1] = dR;
   a.cost[0] = costL; a.cost[1] = costR;
   a.w = w; a.h = h; a.dmax = dmax; a.nw = ctx->nw;
-  a.rows = ctx->cost_rows > 0 ? ctx->cost_rows : (h >= 256 ? 64 : 16);
+  a.rows = cost_long_rows(ctx, w, h, dmax);
   if (a.nw % kChunkWords != 0) return cudaErrorInvalidValue;
   return ctx->p.mask_mode == BSM_MASK_BOTH ? launch_long_win<1>(ctx->p.agg_window, a, s)
                                            : launch_long_win<0>(ctx->p.agg_window, a, s);

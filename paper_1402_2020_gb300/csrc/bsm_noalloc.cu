@@ -6,8 +6,9 @@
 // out up front (a serving process that owns all of its device memory through its own pool), and
 // latency-bound loops where the implicit device synchronisation of cudaMalloc/cudaFree is not
 // allowed. This entry point runs the same two kernels as bsm_describe, but the scratch plane is a
-// fixed array in this file, reserved once per device when the library's device code is loaded and
-// held until the process exits. It calls no allocating routine.
+// fixed array in this file, reserved by the driver when it loads this file's module on a device (at
+// the first symbol lookup below under lazy module loading) and held until the process exits. It calls
+// no allocating routine.
 #include <mutex>
 
 #include "bsm_internal.cuh"
@@ -50,9 +51,11 @@ extern "C" bsm_status bsm_describe_noalloc(bsm_ctx *ctx, const uint8_t *rgb_dev,
   if ((int64_t)w * h > BSM_NOALLOC_MAX_PIXELS) return BSM_ERR_INVALID_ARG;  // larger than the fixed scratch
   uint32_t *plane = nullptr;
   cudaError_t e = plane_for_current_device(&plane);
-  if (e != cudaSuccess) return BSM_ERR_CUDA;
   // The pre-pass writes every plane word that the describe kernel then reads, so nothing left by an
   // earlier call leaks into this one.
-  e = bsm::launch_describe(ctx, rgb_dev, w, h, pitch_bytes, plane, B_dev, Phi_dev, (cudaStream_t)stream);
-  return e == cudaSuccess ? BSM_OK : BSM_ERR_CUDA;
+  if (e == cudaSuccess)
+    e = bsm::launch_describe(ctx, rgb_dev, w, h, pitch_bytes, plane, B_dev, Phi_dev, (cudaStream_t)stream);
+  if (e == cudaSuccess) return BSM_OK;
+  ctx->last_cuda = e;  // as bsm_describe records it, for bsm_last_cuda_error
+  return e == cudaErrorMemoryAllocation ? BSM_ERR_OUT_OF_MEMORY : BSM_ERR_CUDA;
 }

@@ -4,7 +4,9 @@
 // own stream, so the batches of different lanes overlap on the device. Requests arrive from any thread
 // (bsm_server_submit) into a FIFO queue. Whenever a lane is free, the scheduler admits queued requests
 // in arrival order while the engine's device-memory budget allows (each request needs its two views,
-// four descriptor planes, three maps and its share of the batch scratch), allocates their buffers
+// four descriptor planes and three maps; each lane keeps the colour-plane scratch its largest batch
+// and largest per-pair request needed, and that scratch is charged to the budget when it grows),
+// allocates their buffers
 // from the engine's own stream-ordered memory pool, and enqueues on the lane's stream: the host-to-
 // device copies of the views, one bsm_batch_run for the batch's small requests, the per-pair calls
 // (describe, the tensor-core cost kernel where the parameters allow it, refine) for its large ones
@@ -13,6 +15,7 @@
 // only until a lane and memory free up. Completed request ids (with a status each) are handed to
 // bsm_server_poll. A request too large for the budget completes with BSM_ERR_INVALID_ARG; a batch
 // whose launch fails completes every request of that batch with the failing status.
+#include <algorithm>
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
@@ -46,7 +49,22 @@ struct Lane {
   cudaEvent_t done = nullptr;
   uint32_t *status_host = nullptr;  // pinned copy of the context's status word, written by each batch
   std::vector<InFlight> batch;  // empty when the lane is free
-  int64_t plane_pixels = 0;     // batch scratch reserved on this lane's context
+  int64_t plane_pixels = 0;     // batch scratch reserved on this lane's context (colour words)
+  int64_t pair_pixels = 0;      // per-pair scratch reserved on this lane's context (colour words)
+};
+
+// Lane scratch a batch needs: the batch colour planes of its small requests, and the per-pair colour
+// plane of its largest large request (4 bytes per pixel each).
+struct LaneNeed {
+  int64_t batch_px = 0, pair_px = 0;
+  void add(const bsm_request &r) {
+    const int64_t px = (int64_t)r.w * r.h;
+    if ((int64_t)r.w * r.h * r.dmax < kPerPairWork) batch_px += px;
+    else pair_px = std::max(pair_px, px);
+  }
+  size_t growth(const Lane &l) const {
+    return 4 * (size_t)(std::max<int64_t>(0, batch_px - l.plane_pixels) + std::max<int64_t>(0, pair_px - l.pair_pixels));
+  }
 };
 
 }  // namespace
@@ -58,8 +76,9 @@ struct bsm_server {
   int device = 0;
   cudaMemPool_t pool = nullptr;
   std::vector<Lane> lanes;
-  size_t budget = 0;      // bytes of request buffers the engine may hold
+  size_t budget = 0;      // bytes of device memory the engine may hold (request buffers and lane scratch)
   size_t in_use = 0;      // bytes held by admitted requests
+  size_t scratch = 0;     // bytes of lane scratch reserved so far (held until the engine is destroyed)
   std::mutex mu;
   std::condition_variable cv_work;  // submissions and shutdown
   std::condition_variable cv_done;  // completions
@@ -95,12 +114,18 @@ bsm_status launch_batch(bsm_server *s, Lane &lane) {
   const int nw = s->params.n_bits / 32;
   cudaStream_t st = lane.stream;
   std::vector<bsm_pair_desc> descs(lane.batch.size());
-  int64_t pixels = 0;
-  for (auto &f : lane.batch) pixels += (int64_t)f.p.req.w * f.p.req.h;
-  if (pixels > lane.plane_pixels) {
-    const bsm_status r = bsm_reserve_batch(lane.ctx, pixels);
+  // the lane scratch the admission charged to the budget: reserved here, before any work is enqueued
+  LaneNeed need;
+  for (auto &f : lane.batch) need.add(f.p.req);
+  if (need.batch_px > lane.plane_pixels) {
+    const bsm_status r = bsm_reserve_batch(lane.ctx, need.batch_px);
     if (r != BSM_OK) return r;
-    lane.plane_pixels = pixels;
+    lane.plane_pixels = need.batch_px;
+  }
+  if (need.pair_px > lane.pair_pixels) {
+    const bsm_status r = bsm_reserve(lane.ctx, (int32_t)need.pair_px, 1);
+    if (r != BSM_OK) return r;
+    lane.pair_pixels = need.pair_px;
   }
   if (cudaMemsetAsync(lane.ctx->status, 0, sizeof(uint32_t), st) != cudaSuccess) return BSM_ERR_CUDA;
   for (size_t i = 0; i < lane.batch.size(); ++i) {
@@ -189,17 +214,25 @@ void worker_main(bsm_server *s) {
     for (Lane &lane : s->lanes) {
       if (!lane.batch.empty() || s->queue.empty()) continue;
       int64_t work = 0;
+      LaneNeed need;
+      size_t grow = 0;  // lane scratch this batch adds (charged once, kept by the lane)
       while (!s->queue.empty() && (int)lane.batch.size() < s->cfg.max_batch) {
         Pending &p = s->queue.front();
-        if (s->in_use + p.bytes > s->budget) break;  // waits for memory to free up
+        LaneNeed next = need;
+        next.add(p.req);
+        const size_t g = next.growth(lane);
+        if (s->in_use + s->scratch + g + p.bytes > s->budget) break;  // waits for memory to free up
         const int64_t wk = (int64_t)p.req.w * p.req.h * p.req.dmax;
         if (!lane.batch.empty() && s->cfg.max_batch_work > 0 && work + wk > s->cfg.max_batch_work) break;
         work += wk;
+        need = next;
+        grow = g;
         s->in_use += p.bytes;
         lane.batch.push_back(InFlight{p, nullptr});
         s->queue.pop_front();
       }
-      if (lane.batch.empty()) break;  // the head request needs memory that busy lanes still hold
+      if (lane.batch.empty()) continue;  // the head needs memory that busy lanes hold, or another lane's scratch
+      s->scratch += grow;
       ++s->stats.batches;
       s->stats.max_batch_seen = std::max<int64_t>(s->stats.max_batch_seen, (int64_t)lane.batch.size());
       lk.unlock();
@@ -220,6 +253,15 @@ void worker_main(bsm_server *s) {
     // 3. wait: briefly while batches are in flight (to retire them), else until work arrives
     bool busy = false;
     for (Lane &lane : s->lanes) busy = busy || !lane.batch.empty();
+    if (!busy && !s->queue.empty()) {
+      // every lane is idle and the head request still does not fit: the lanes' scratch leaves too
+      // little of the budget for it, so it can never run
+      Pending p = s->queue.front();
+      s->queue.pop_front();
+      complete(s, p.req.id, BSM_ERR_OUT_OF_MEMORY, p.t_submit);
+      s->cv_done.notify_all();
+      continue;
+    }
     if (busy) s->cv_work.wait_for(lk, std::chrono::microseconds(50));
     else if (s->queue.empty() && !s->stop) s->cv_work.wait(lk);
   }
@@ -302,7 +344,8 @@ bsm_status bsm_server_submit(bsm_server *s, const bsm_request *r) {
   ++s->submitted;
   ++s->stats.submitted;
   const size_t bytes = ok ? request_bytes(*r, s->params.n_bits / 32) : 0;
-  if (!ok || bytes > s->budget) {
+  // with its lane scratch (one colour word per pixel) it must fit the budget on its own
+  if (!ok || bytes + 4 * (size_t)r->w * r->h > s->budget) {
     complete(s, r->id, BSM_ERR_INVALID_ARG, t0);  // malformed, or larger than the whole budget
     s->cv_done.notify_all();
     return BSM_ERR_INVALID_ARG;
@@ -344,6 +387,7 @@ bsm_status bsm_server_get_stats(bsm_server *s, bsm_server_stats *out) {
   *out = s->stats;
   out->queued = (int64_t)s->queue.size();
   out->bytes_in_use = (int64_t)s->in_use;
+  out->scratch_bytes = (int64_t)s->scratch;
   out->budget = (int64_t)s->budget;
   return BSM_OK;
 }

@@ -41,7 +41,7 @@ def test_every_declared_symbol_is_exported(lib):
 def test_status_strings(lib):
     assert bsm.bsm_status_string(0) == "ok"
     assert "timed out" in bsm.bsm_status_string(bsm.BSM_ERR_TIMEOUT)
-    assert bsm.bsm_abi_version() == 2
+    assert bsm.bsm_abi_version() == 3
 
 
 def _params(**kw):

@@ -1,9 +1,12 @@
 """Failure detection without a GPU fault (needs a GPU).
 
-The cost kernel's staging waits are bounded. With the test hook that withholds the staging thread's
+The cost kernels' staging waits are bounded. With the test hook that withholds the staging thread's
 mbarrier arrivals (a completion that nothing signals), every wait runs out after about a second; the
 kernel latches BSM_ERR_TIMEOUT in the context's status word and returns. The host reads the status,
-and the same context then runs a normal call correctly.
+and the same context then runs a normal call correctly. Covered: the one-column popcount kernel
+(cost_variant 0 with the hook) and the tensor-core kernel (cost_variant 3), whose producer then issues
+no copies, so its operand builders, MMA issuer and epilogue all give up. The two-column kernel
+completes its copies by cp.async groups and has no wait to withhold.
 """
 import time
 
@@ -28,11 +31,16 @@ def B():
     return bsm
 
 
-def test_bounded_wait_reports_timeout_and_context_recovers(B, orc):
+@pytest.mark.parametrize("variant,kernel,shape", [(0, 1, (40, 12, 32)), (3, 3, (300, 24, 32))])
+def test_bounded_wait_reports_timeout_and_context_recovers(B, orc, variant, kernel, shape):
     pairs = synth.pair_table(256, 31, seed=3000)
     ctx = B.bsm_create(B.make_params(pairs, agg_window=5, dmax=32))
     try:
-        w, h, dmax = 40, 12, 32  # one CTA per reference view
+        w, h, dmax = shape  # one wave of CTAs
+        B.bsm_set_tuning(ctx, 0, 0, 0, variant, 0)
+        B.bsm_debug_set(ctx, B.BSM_DEBUG_WITHHOLD_ARRIVALS, 1)
+        assert B.bsm_cost_plan(ctx, w, h, dmax)["kernel"] == kernel  # the kernel the hook reaches
+        B.bsm_debug_set(ctx, B.BSM_DEBUG_WITHHOLD_ARRIVALS, 0)
         l, r, _ = synth.stereo_pair(w, h, dmax, seed=3001)
         dl, dr = torch.from_numpy(l).cuda(), torch.from_numpy(r).cuda()
         P = [torch.empty((h, w, 8), dtype=torch.int32, device="cuda") for _ in range(4)]
@@ -46,6 +54,7 @@ def test_bounded_wait_reports_timeout_and_context_recovers(B, orc):
         assert B.bsm_last_error(ctx) == B.BSM_ERR_TIMEOUT
         assert 0.5 < time.time() - t0 < 30
         assert (dL.cpu().numpy() == -9).all()  # nothing was written past the failed wait
+        assert (dR.cpu().numpy() == -9).all()
         # the status is read-and-clear, and the context keeps working
         assert B.bsm_last_error(ctx) == B.BSM_OK
         B.bsm_debug_set(ctx, B.BSM_DEBUG_WITHHOLD_ARRIVALS, 0)
@@ -54,6 +63,8 @@ def test_bounded_wait_reports_timeout_and_context_recovers(B, orc):
         oBL, oPL = orc.describe(l, pairs)
         oBR, _ = orc.describe(r, pairs)
         assert (dL.cpu().numpy() == orc.wta(oBL, oPL, oBR, dmax, 5, 0)).all()
+        oBR, oPR = orc.describe(r, pairs)
+        assert (dR.cpu().numpy() == orc.wta(oBR, oPR, oBL, dmax, 5, 1)).all()
     finally:
         B.bsm_destroy(ctx)
 

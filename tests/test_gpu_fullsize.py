@@ -1,10 +1,10 @@
 """Parity at the full workload sizes (1390x1110 and 3840x2160, dmax 256), in the launch configuration that
 bench.py times, on outputs the oracle can compute one by one (needs a GPU).
 
-The oracle computes only what each sampled output depends on: whole descriptor rows, the WTA result of
-single pixels (from the descriptor rows of their aggregation window), and the refined value of single
-pixels (from the WTA maps of their vote window, of the pixels their left/right check reads, and of
-their row for the fallback scan).
+The oracle computes only what each checked output depends on: whole descriptor rows; whole rows of both
+WTA maps (from the descriptor rows of their aggregation window), among them the rows on both sides of
+the cost kernel's row-band boundaries (every column tile of the row); the refined map over a whole row
+(from both WTA maps over its vote window's rows); and the refined value of single pixels.
 """
 import numpy as np
 import pytest
@@ -42,10 +42,11 @@ def run_gpu(B, left, right, dmax, pairs):
     B.bsm_refine(ctx, dl, 3 * w, M[0], M[1], w, h, dmax, M[2])
     torch.cuda.synchronize()
     assert B.bsm_last_error(ctx) == B.BSM_OK
+    plan = B.bsm_cost_plan(ctx, w, h, dmax)
     B.bsm_destroy(ctx)
     planes = [p.cpu().numpy().view(np.uint32) for p in P]
     maps = [m.cpu().numpy() for m in M]
-    return planes, maps
+    return planes, maps, plan
 
 
 class OracleRows:
@@ -77,14 +78,86 @@ class OracleRows:
         return self.orc.wta(BR, PR, BL, dmax, WIN, 1, x0, x1, y0, y1)
 
 
+class OracleMaps:
+    """Whole rows of the oracle's WTA maps (both views), computed on demand and kept."""
+
+    def __init__(self, rows, w, h, dmax):
+        self.rows, self.w, self.h, self.dmax = rows, w, h, dmax
+        self.maps = [np.zeros((h, w), np.int32), np.zeros((h, w), np.int32)]
+        self.done = np.zeros(h, bool)
+
+    def ensure(self, y0, y1):
+        y0, y1 = max(0, y0), min(self.h, y1)
+        todo = [y for y in range(y0, y1) if not self.done[y]]
+        if not todo:
+            return
+        a, b = min(todo), max(todo) + 1
+        for direction in (0, 1):
+            self.maps[direction][a:b] = self.rows.wta(direction, 0, self.w, a, b, self.dmax)
+        self.done[a:b] = True
+
+
+def checked_rows(workload):
+    """Rows 0, 1, h - 1, and the rows on both sides of the first two row-band boundaries of the cost kernel
+    the library ran (bands of rows_per_band output rows; every column tile is in each whole row)."""
+    h = workload["left"].shape[0]
+    rb = workload["plan"]["rows_per_band"]
+    rows = {0, 1, h - 1}
+    for k in (1, 2):
+        if k * rb < h:
+            rows |= {k * rb - 1, k * rb}
+    return sorted(rows)
+
+
 @pytest.fixture(scope="module", params=sorted(WORKLOADS))
 def workload(request, B, orc):
     w, h, dmax, seed, radio = WORKLOADS[request.param]
     left, right, _ = synth.stereo_pair(w, h, dmax, seed, radio)
     pairs = synth.pair_table(N_BITS, S, seed=11)
-    planes, maps = run_gpu(B, left, right, dmax, pairs)
+    planes, maps, plan = run_gpu(B, left, right, dmax, pairs)
+    rows = OracleRows(orc, left, right, pairs)
     return {"left": left, "right": right, "pairs": pairs, "dmax": dmax, "planes": planes, "maps": maps,
-            "rows": OracleRows(orc, left, right, pairs), "name": request.param}
+            "plan": plan, "rows": rows, "omaps": OracleMaps(rows, w, h, dmax), "name": request.param}
+
+
+def test_launch_is_the_benchmarked_one(workload):
+    # bench.py's autotuned pick on these shapes is the tensor-core kernel with the library's own bands
+    assert workload["plan"]["kernel"] == 3, workload["plan"]
+    assert 1 <= workload["plan"]["rows_per_band"] < workload["left"].shape[0]
+
+
+def test_wta_whole_rows(workload):
+    om = workload["omaps"]
+    dL, dR = workload["maps"][0], workload["maps"][1]
+    for y in checked_rows(workload):
+        om.ensure(y, y + 1)
+        for direction, got in ((0, dL), (1, dR)):
+            bad = np.nonzero(got[y] != om.maps[direction][y])[0]
+            assert bad.size == 0, (workload["name"], direction, y, bad[:8], got[y, bad[:8]],
+                                   om.maps[direction][y, bad[:8]])
+
+
+def test_refine_whole_row(workload, orc):
+    """The refined map over a whole row at the second band boundary: its vote window's rows of both WTA
+    maps from the oracle, the left/right check and Eq. 9-10 from the oracle."""
+    h, w, _ = workload["left"].shape
+    dmax = workload["dmax"]
+    rb = workload["plan"]["rows_per_band"]
+    y = min(2 * rb, h - 1)
+    om = workload["omaps"]
+    om.ensure(y - R, y + R + 1)
+    ya, yb = max(0, y - R), min(h, y + R + 1)
+    far = 10 ** 6  # rows outside the window: a disparity that fails the left/right check (x - d < 0)
+    dL = np.full((h, w), far, np.int32)
+    dR = np.zeros((h, w), np.int32)
+    dL[ya:yb] = om.maps[0][ya:yb]
+    dR[ya:yb] = om.maps[1][ya:yb]
+    # the GPU's WTA rows of the window equal the oracle's (else the refined row could not match)
+    assert (workload["maps"][0][ya:yb] == dL[ya:yb]).all() and (workload["maps"][1][ya:yb] == dR[ya:yb]).all()
+    valid = orc.lr_check(dL, dR, 1)
+    expect = orc.refine_region(workload["left"], dL, valid, dmax, 0, w, y, y + 1, R=R)[0]
+    bad = np.nonzero(workload["maps"][2][y] != expect)[0]
+    assert bad.size == 0, (workload["name"], y, bad[:8])
 
 
 def test_descriptor_rows(workload):

@@ -87,7 +87,7 @@ def test_rejects_and_small_budget(B):
     params = B.make_params(pairs, agg_window=3, dmax=64)
     ctx = B.bsm_create(params)
     # room for about one 400x300 request at a time: admission must wait for memory, not fail
-    budget = 400 * 300 * (2 * 3 + 4 * 8 + 3 * 4) + 8 * 4096
+    budget = 400 * 300 * (2 * 3 + 4 * 8 + 3 * 4 + 4) + 8 * 4096  # views, planes, maps, lane scratch
     srv = B.bsm_server_create(params, lanes=3, max_batch=4, device_budget=budget)
     try:
         l, r, _ = synth.stereo_pair(400, 300, 64, seed=2201)
@@ -108,6 +108,63 @@ def test_rejects_and_small_budget(B):
         B.bsm_server_drain(srv, 10000)
         st = B.bsm_server_get_stats(srv)
         assert st["failed"] == 2 and st["completed"] == 5 and st["max_batch_seen"] == 1
+        assert 0 < st["scratch_bytes"] <= 3 * 4 * 400 * 300  # one colour plane per lane at most, charged
+    finally:
+        B.bsm_server_destroy(srv)
+        B.bsm_destroy(ctx)
+
+
+def test_large_request_alone_in_the_mix_and_against_the_oracle(B, orc):
+    """A request of 1280 x 720 x 128 pixel-disparities takes the engine's per-pair branch (two describes,
+    the tensor-core cost kernel, refine on the lane's stream) while small requests are batched beside it:
+    its map is the same alone and in the mix, and equals the oracle on a band of rows."""
+    pairs = synth.pair_table(256, 31, seed=2300)
+    params = B.make_params(pairs, agg_window=5, dmax=256)
+    ctx = B.bsm_create(params)
+    srv = B.bsm_server_create(params, lanes=2, max_batch=8)
+    try:
+        W, H, D = 1280, 720, 128
+        assert B.bsm_cost_plan(ctx, W, H, D)["kernel"] == 3  # the automatic choice at this size
+        big_l, big_r, _ = synth.stereo_pair(W, H, D, seed=2301)
+        big = {"l": pinned(big_l), "r": pinned(big_r)}
+        outs = [torch.full((H, W), -3, dtype=torch.int32).pin_memory() for _ in range(2)]
+        assert B.bsm_server_submit(srv, 0, big["l"], big["r"], W, H, 3 * W, D, outs[0]) == B.BSM_OK
+        assert wait_all(B, srv, [0], timeout_s=120) == {0: B.BSM_OK}
+        small = []
+        for i, (w, h, d) in enumerate([(640, 480, 64), (320, 240, 128), (640, 480, 256), (200, 150, 64)] * 2):
+            l, r, _ = synth.stereo_pair(w, h, d, seed=2310 + i)
+            small.append({"w": w, "h": h, "d": d, "l": pinned(l), "r": pinned(r),
+                          "out": torch.full((h, w), -3, dtype=torch.int32).pin_memory()})
+        # the large request in the middle of the small ones, all submitted at once
+        for i, q in enumerate(small[:4]):
+            assert B.bsm_server_submit(srv, 10 + i, q["l"], q["r"], q["w"], q["h"], 3 * q["w"], q["d"],
+                                       q["out"]) == B.BSM_OK
+        assert B.bsm_server_submit(srv, 1, big["l"], big["r"], W, H, 3 * W, D, outs[1]) == B.BSM_OK
+        for i, q in enumerate(small[4:]):
+            assert B.bsm_server_submit(srv, 14 + i, q["l"], q["r"], q["w"], q["h"], 3 * q["w"], q["d"],
+                                       q["out"]) == B.BSM_OK
+        got = wait_all(B, srv, [1] + list(range(10, 18)), timeout_s=120)
+        assert all(st == B.BSM_OK for st in got.values())
+        assert (outs[1].numpy() == outs[0].numpy()).all()  # alone == in the mix
+        for q in small[:2]:
+            assert (q["out"].numpy() == reference_map(B, ctx, q["l"].numpy(), q["r"].numpy(), q["d"])).all()
+        # the oracle on rows 300 .. 303: both WTA maps over the rows their vote windows reach
+        y0, y1, R, win = 300, 304, 15, 5
+        a, b = y0 - R - win // 2, y1 + R + win // 2
+        h, w = H, W
+        planes = [np.zeros((h, w, 8), np.uint32) for _ in range(4)]
+        orc.describe(big_l, pairs, None, a, b, out=(planes[0], planes[1]))
+        orc.describe(big_r, pairs, None, a, b, out=(planes[2], planes[3]))
+        far = 10 ** 6
+        dL = np.full((h, w), far, np.int32)
+        dR = np.zeros((h, w), np.int32)
+        dL[y0 - R:y1 + R] = orc.wta(planes[0], planes[1], planes[2], D, win, 0, 0, w, y0 - R, y1 + R)
+        dR[y0 - R:y1 + R] = orc.wta(planes[2], planes[3], planes[0], D, win, 1, 0, w, y0 - R, y1 + R)
+        valid = orc.lr_check(dL, dR, 1)
+        expect = orc.refine_region(big_l, dL, valid, D, 0, w, y0, y1, R=R)
+        assert (outs[1].numpy()[y0:y1] == expect).all()
+        st = B.bsm_server_get_stats(srv)
+        assert st["failed"] == 0
     finally:
         B.bsm_server_destroy(srv)
         B.bsm_destroy(ctx)

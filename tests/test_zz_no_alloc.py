@@ -26,18 +26,25 @@ def B():
     return bsm
 
 
-def _describe(B, fn, ctx, img, nw):
+def _describe(B, fn, ctx, img, nw, pad=0):
+    """One call of fn on img, stored with a row pitch of 3 w + pad bytes."""
     h, w, _ = img.shape
-    d = torch.from_numpy(img).cuda()
+    pitch = 3 * w + pad
+    buf = np.zeros((h, pitch), np.uint8)
+    buf[:, :3 * w] = img.reshape(h, 3 * w)
+    d = torch.from_numpy(buf).cuda()
     Bp = torch.full((h, w, nw), -1, dtype=torch.int32, device="cuda")
     Pp = torch.full((h, w, nw), -1, dtype=torch.int32, device="cuda")
-    fn(ctx, d, w, h, 3 * w, Bp, Pp)
+    fn(ctx, d, w, h, pitch, Bp, Pp)
     torch.cuda.synchronize()
     return Bp.cpu().numpy(), Pp.cpu().numpy()
 
 
-def test_noalloc_matches_describe_on_consecutive_calls(B):
-    pairs = synth.pair_table(256, 31, seed=900)
+# the thread-per-pixel describe (n = 64), the warp-per-pixel one (n = 256), the long-descriptor one
+# (n = 1024); and a padded row pitch
+@pytest.mark.parametrize("n,pad", [(64, 0), (256, 0), (1024, 0), (256, 13)])
+def test_noalloc_matches_describe_on_consecutive_calls(B, n, pad):
+    pairs = synth.pair_table(n, 31, seed=900 + n)
     params = B.make_params(pairs, dmax=64)
     ctx = B.bsm_create(params)
     try:
@@ -46,8 +53,8 @@ def test_noalloc_matches_describe_on_consecutive_calls(B):
         imgs = [synth.stereo_pair(300, 170, 64, seed=901)[0], synth.stereo_pair(97, 45, 64, seed=902)[1]]
         imgs.append(imgs[0])
         for img in imgs:
-            nb, npf = _describe(B, B.bsm_describe_noalloc, ctx, img, 8)
-            rb, rpf = _describe(B, B.bsm_describe, ctx, img, 8)
+            nb, npf = _describe(B, B.bsm_describe_noalloc, ctx, img, n // 32, pad)
+            rb, rpf = _describe(B, B.bsm_describe, ctx, img, n // 32, pad)
             assert (nb == rb).all()
             assert (npf == rpf).all()
         assert B.bsm_last_error(ctx) == B.BSM_OK
