@@ -6,8 +6,8 @@
 // disparities reach (TMEM columns) are one product S O^T. The window's vertical sum is a running
 // accumulator: every input row adds s(entering row) . o(entering row) and, with the A operand negated
 // by the instruction descriptor, subtracts s(leaving row) . o(leaving row); tcgen05.mma kind::f8f6f4,
-// E4M3 operands +-2^-6 and 2^-6, fp32 accumulation in TMEM: every value is an integer times 2^-12
-// below 2^11, so the products and sums are exact.
+// E4M3 operands whose every product is 0 or +-2^-2 (the encoding is below), fp32 accumulation in
+// TMEM: every value is an integer times 2^-2 below 2^9, so the products and sums are exact.
 //
 // One launch, cost_tc_kernel, one CTA per (128 reference columns, band of rows, reference view), 20 warps;
 // the K order within a 32-bit descriptor word is a fixed permutation of its bits (byte k of operand word
@@ -15,10 +15,10 @@
 //    - warp 0 (producer) loads, by TMA, the other view's descriptor words of the entering and the
 //      leaving row (32 bytes per band column); the tensor maps fill columns outside the image with zeros;
 //    - warps 2..7 (builders) form each 64-byte K chunk's operands in shared memory: A (4 groups x 128
-//      reference columns of s bytes, +-2^-6 where the mask bit is set, from the reference view's B and
+//      reference columns of s bytes, nonzero where the mask bit is set, from the reference view's B and
 //      Phi words, read from global memory one row half ahead) and B (4 groups x up to 384 band columns
-//      of o bytes, 2^-6 where the bit is set, from the TMA'd words); they also keep each column's window
-//      popcount(Phi AND B) and publish it per input row in a small ring;
+//      of o bytes, nonzero where the bit is set, from the TMA'd words); they also keep each column's
+//      window popcount(Phi AND B) and publish it per input row in a small ring;
 //    - warp 1 owns the TMEM accumulator and issues the MMAs (2 k-steps x 2 N-blocks per chunk), commits
 //      each chunk to its buffer's "empty" barrier and each finished output row to "acc_full"; before the
 //      next row's MMAs it waits until the epilogue has read the accumulator;
@@ -49,8 +49,11 @@ constexpr int kE0 = 2 + kBW;      // first epilogue warp
 constexpr int kWarps = kE0 + 12;  // producer, MMA, builders, 12 epilogue warps (3 per TMEM lane quadrant)
 constexpr int kThreads = 32 * kWarps;
 constexpr int kXpd = kBW * 32;    // operand builder threads
-constexpr int kBC = (kNB + kXpd - 1) / kXpd;  // B-operand band columns per builder thread
-static_assert(kXpd >= kTM, "one builder thread per A row");
+// B-operand band columns: builder thread t < kTM, which also forms A row t, owns band column t; each of
+// the other kXpd - kTM threads owns kBC of the rest, so every builder warp does about the same work
+// (an A word costs about three times a B word)
+constexpr int kBC = (kNB - kTM) / (kXpd - kTM);
+static_assert(kXpd >= kTM && kTM + (kXpd - kTM) * kBC == kNB, "band columns split over the builders");
 constexpr int kEpi = 12 * 32;     // epilogue threads (warps kE0 .. kE0 + 11)
 constexpr int kTP = 288;          // u16 pitch of the term table T[x][d] (rows 16-byte aligned)
 constexpr int kTPad = 32;         // u16 in front of row 0; row r's band terms past d = 255 land in row r + 1's first 32
@@ -86,10 +89,14 @@ struct TcArgs {
 
 __device__ __forceinline__ uint32_t saddr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
+// One try of a phase wait. A thread whose phase is not complete sleeps in the barrier hardware until the
+// phase completes or about 20 microseconds pass (the suspend-time hint), so waiting warps take few issue
+// slots from the working ones.
 __device__ __forceinline__ bool mbar_try(uint64_t *bar, uint32_t parity) {
   uint32_t ok;
-  asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}"
-               : "=r"(ok) : "r"(saddr(bar)), "r"(parity) : "memory");
+  asm volatile(
+      "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\nselp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok) : "r"(saddr(bar)), "r"(parity), "r"(20000u) : "memory");
   return ok != 0;
 }
 
@@ -156,7 +163,10 @@ __device__ __forceinline__ void mma_commit(uint64_t *bar) {
                : "memory");
 }
 
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+// 32 consecutive accumulator columns of the warp's 32 TMEM lanes into r, asynchronously: the registers
+// hold the values only after tmem_wait_ld(). (Overlapping one chunk's load with the previous chunk's
+// conversion needs 32 more live registers, which spill at this kernel's 96.)
+__device__ __forceinline__ void tmem_ld32_async(uint32_t taddr, uint32_t (&r)[32]) {
   asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
                "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
@@ -164,9 +174,11 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
                  "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
                  "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
                  "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-               : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+               : "r"(taddr)
+               : "memory");
 }
+
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 __device__ __forceinline__ uint32_t vmin_u16x2(uint32_t a, uint32_t b) {
   uint32_t r;
@@ -174,31 +186,37 @@ __device__ __forceinline__ uint32_t vmin_u16x2(uint32_t a, uint32_t b) {
   return r;
 }
 
-// Byte k (k = 0..3) of output word q takes bit 8k + q of w, placed at bit `pos` of the byte.
-template <int Q, int POS>
-__device__ __forceinline__ uint32_t spread(uint32_t w) {
-  constexpr int sh = POS - Q;
-  constexpr uint32_t mask = 0x01010101u << POS;
-  if constexpr (sh >= 0) return (w << sh) & mask;
-  else return (w >> (-sh)) & mask;
-}
+// Operand bytes. Byte k (k = 0..3) of operand word q holds bit 8k + q of a descriptor word; the same K
+// permutation for both operands. The other view's bit o becomes the byte o << q as it stands (one AND
+// per word), except bit 7, which moves to 0x40 (0x80 would be E4M3's -0): so bit q of a byte carries the
+// E4M3 value v_q = 2^-9, 2^-8, 2^-7, 2^-6, 2^-5, 2^-3, 2^1, 2^1 for q = 0 .. 7 (q < 3 are subnormals).
+// The reference byte carries s = Phi (1 - 2 B) times a_q = 2^-2 / v_q = 2^7, 2^6, 2^5, 2^4, 2^3, 2^1,
+// 2^-3, 2^-3 (E4M3 codes 0x70, 0x68, 0x60, 0x58, 0x50, 0x40, 0x20, 0x20, sign 0x80), so every product is
+// s o 2^-2 exactly and the accumulator holds 2^-2 sum_i s_i o_i.
 
-// 32 K bytes of the B operand from one other-view word: 2^-6 (0x08) where the bit is set.
+// 32 K bytes of the B operand from one other-view word o.
 __device__ __forceinline__ void expand_b(uint32_t o, uint8_t *dst_g0, uint8_t *dst_g1) {
-  *reinterpret_cast<uint4 *>(dst_g0) =
-      make_uint4(spread<0, 3>(o), spread<1, 3>(o), spread<2, 3>(o), spread<3, 3>(o));
+  *reinterpret_cast<uint4 *>(dst_g0) = make_uint4(o & 0x01010101u, o & 0x02020202u, o & 0x04040404u, o & 0x08080808u);
   *reinterpret_cast<uint4 *>(dst_g1) =
-      make_uint4(spread<4, 3>(o), spread<5, 3>(o), spread<6, 3>(o), spread<7, 3>(o));
+      make_uint4(o & 0x10101010u, o & 0x20202020u, o & 0x40404040u, (o >> 1) & 0x40404040u);
 }
 
-// 32 K bytes of the A operand from one descriptor word b and mask word m of the reference column:
-// s = +-2^-6 (0x08, sign bit 0x80 where b is set) where m is set, 0 elsewhere.
+// Operand word q < 6 of the A operand: (m & M_q) (P_q / 2^q) puts the magnitude code P_q in every byte
+// whose mask bit is set, (s & M_q) 2^(7 - q) the sign where the descriptor bit is set too (s = m & b).
+template <int Q>
+__device__ __forceinline__ uint32_t a_word(uint32_t m, uint32_t sb) {
+  constexpr uint32_t M = 0x01010101u << Q;
+  constexpr uint32_t P[6] = {0x70u, 0x68u, 0x60u, 0x58u, 0x50u, 0x40u};
+  return (m & M) * (P[Q] >> Q) + (sb & M) * (0x80u >> Q);
+}
+
+// 32 K bytes of the A operand from one descriptor word b and mask word m of the reference column.
 __device__ __forceinline__ void expand_a(uint32_t b, uint32_t m, uint8_t *dst_g0, uint8_t *dst_g1) {
   const uint32_t sb = m & b;
-  *reinterpret_cast<uint4 *>(dst_g0) = make_uint4(spread<0, 3>(m) | spread<0, 7>(sb), spread<1, 3>(m) | spread<1, 7>(sb),
-                                                  spread<2, 3>(m) | spread<2, 7>(sb), spread<3, 3>(m) | spread<3, 7>(sb));
-  *reinterpret_cast<uint4 *>(dst_g1) = make_uint4(spread<4, 3>(m) | spread<4, 7>(sb), spread<5, 3>(m) | spread<5, 7>(sb),
-                                                  spread<6, 3>(m) | spread<6, 7>(sb), spread<7, 3>(m) | spread<7, 7>(sb));
+  *reinterpret_cast<uint4 *>(dst_g0) = make_uint4(a_word<0>(m, sb), a_word<1>(m, sb), a_word<2>(m, sb), a_word<3>(m, sb));
+  *reinterpret_cast<uint4 *>(dst_g1) =
+      make_uint4(a_word<4>(m, sb), a_word<5>(m, sb), ((m >> 1) & 0x20202020u) | ((sb << 1) & 0x80808080u),
+                 ((m >> 2) & 0x20202020u) | (sb & 0x80808080u));
 }
 
 // ---------------------------------------------------------------- cost kernel
@@ -335,7 +353,7 @@ __device__ __forceinline__ void cost_tc_body(const TcArgs &a, uint8_t *smem) {
     }
   } else if (warp < kE0) {
     // ---- operand builders: per chunk, the A operand's row t < 128 (the s bytes of reference column X0 + t,
-    // from its descriptor and mask words) and the B operand's band columns t + kXpd j
+    // from its descriptor and mask words) with band column t, or band columns kTM + (t - kTM) + (kXpd - kTM) j
     const int t = tid - 64, xa = X0 + t;
     const bool has_a = t < kTM, a_in = has_a && xa >= 0 && xa < w;
     auto present = [&](int ii, int hh) { return hh == 0 ? row_new(ii) : row_old(ii); };
@@ -388,14 +406,17 @@ __device__ __forceinline__ void cost_tc_body(const TcArgs &a, uint8_t *smem) {
         }
         const uint32_t *rw = reinterpret_cast<const uint32_t *>(raw + half * kRawRow);
         uint4 qw[kBC];  // words 4 (cc / 2) .. 4 (cc / 2) + 3 of each of the thread's band columns
+        const int nbc = has_a ? 1 : kBC;  // uniform in the warp
+        auto bcol = [&](int k) { return has_a ? t : kTM + (t - kTM) + (kXpd - kTM) * k; };
 #pragma unroll
         for (int cc = 0; cc < 4; ++cc) {  // chunk cc: descriptor words 2 cc and 2 cc + 1
           if (!ok) break;
           if ((cc & 1) == 0) {
 #pragma unroll
             for (int k = 0; k < kBC; ++k) {
-              const int r = t + kXpd * k;
-              qw[k] = r < ntot ? *reinterpret_cast<const uint4 *>(rw + r * 8 + 2 * cc) : make_uint4(0u, 0u, 0u, 0u);
+              const int r = bcol(k);
+              if (k < nbc)
+                qw[k] = r < ntot ? *reinterpret_cast<const uint4 *>(rw + r * 8 + 2 * cc) : make_uint4(0u, 0u, 0u, 0u);
             }
           }
           const int b = (int)(slot % kBuf);
@@ -411,8 +432,8 @@ __device__ __forceinline__ void cost_tc_body(const TcArgs &a, uint8_t *smem) {
           }
 #pragma unroll
           for (int k = 0; k < kBC; ++k) {
-            const int r = t + kXpd * k;
-            if (r < ntot) {
+            const int r = bcol(k);
+            if (k < nbc && r < ntot) {
               const uint4 &qq = qw[k];
               expand_b((cc & 1) ? qq.z : qq.x, opB + 0 * (kNB * 16) + r * 16, opB + 1 * (kNB * 16) + r * 16);
               expand_b((cc & 1) ? qq.w : qq.y, opB + 2 * (kNB * 16) + r * 16, opB + 3 * (kNB * 16) + r * 16);
@@ -483,37 +504,47 @@ __device__ __forceinline__ void cost_tc_body(const TcArgs &a, uint8_t *smem) {
         };
         auto chunk_a0 = [&](int k) { return r * kTP + (DIR == 0 ? D - 1 - 32 * k + lane : 32 * k - lane); };
         auto whole = [&](int a0) { return DIR == 0 ? (a0 & 1) != 0 : (a0 & 1) == 0; };  // 16 whole words
+        // chunk kk of this warp (k = g + 3 kk): convert to 16-bit terms and pack them as words
+        auto process = [&](uint32_t(&v)[32], int k, uint32_t(&wk)[16]) {
 #pragma unroll
-        for (int kk = 0; kk < 3; ++kk) {
-          const int k = g + 3 * kk;
-          if (k < nck) {
-            uint32_t v[32];
-            tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(32 * q + 32 * k), v);
+          for (int t = 0; t < 32; ++t) v[t] = __float_as_uint(fmaf(__uint_as_float(v[t]), 4.0f, base));
+          const int a0 = chunk_a0(k);
+          if (!fast) {  // the sentinel where the match leaves the other view; 0 for columns off the image
+            const int c = a0 - r * kTP;
+            const int cut = DIR == 0 ? (col_in ? c - xr : 64) : (col_in ? w - xr - c : -1);
 #pragma unroll
-            for (int t = 0; t < 32; ++t) v[t] = __float_as_uint(fmaf(__uint_as_float(v[t]), 4096.0f, base));
-            const int a0 = chunk_a0(k);
-            if (!fast) {  // the sentinel where the match leaves the other view; 0 for columns off the image
-              const int c = a0 - r * kTP;
-              const int cut = DIR == 0 ? (col_in ? c - xr : 64) : (col_in ? w - xr - c : -1);
+            for (int t = 0; t < 32; ++t) v[t] = (DIR == 0 ? t >= cut : t < cut) ? v[t] : sentinel;
+          }
+          const bool al = whole(a0);
+          const uint32_t sel = (al == (DIR == 0)) ? 0x5410u : 0x1054u;
 #pragma unroll
-              for (int t = 0; t < 32; ++t) v[t] = (DIR == 0 ? t >= cut : t < cut) ? v[t] : sentinel;
-            }
-            const bool al = whole(a0);
-            const uint32_t sel = (al == (DIR == 0)) ? 0x5410u : 0x1054u;
+          for (int p = 0; p < 16; ++p)
+            wk[p] = __byte_perm(v[2 * p + 1], al ? v[2 * p] : v[2 * p + 2 < 32 ? 2 * p + 2 : 31], sel);
+          if (!al) {
+            T[a0] = (uint16_t)v[0];
+            T[DIR == 0 ? a0 - 31 : a0 + 31] = (uint16_t)v[31];
+          }
+        };
+        auto col_addr = [&](int k) { return tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(32 * q + 32 * k); };
+        const int k0 = g, k1 = g + 3, k2 = g + 6;
+        {
+          uint32_t va[32];
+          if (k0 < nck) {
+            tmem_ld32_async(col_addr(k0), va);
+            tmem_wait_ld();
             uint32_t wk[16];
-#pragma unroll
-            for (int p = 0; p < 16; ++p)
-              wk[p] = __byte_perm(v[2 * p + 1], al ? v[2 * p] : v[2 * p + 2 < 32 ? 2 * p + 2 : 31], sel);
-            if (!al) {
-              T[a0] = (uint16_t)v[0];
-              T[DIR == 0 ? a0 - 31 : a0 + 31] = (uint16_t)v[31];
-            }
-            if (kk == 0) {
-              put(a0, al, wk);
-            } else {
-#pragma unroll
-              for (int p = 0; p < 16; ++p) wd[kk - 1][p] = wk[p];
-            }
+            process(va, k0, wk);
+            put(chunk_a0(k0), whole(chunk_a0(k0)), wk);
+          }
+          if (k1 < nck) {
+            tmem_ld32_async(col_addr(k1), va);
+            tmem_wait_ld();
+            process(va, k1, wd[0]);
+          }
+          if (k2 < nck) {
+            tmem_ld32_async(col_addr(k2), va);
+            tmem_wait_ld();
+            process(va, k2, wd[1]);
           }
         }
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -635,13 +666,24 @@ cudaError_t launch_tc_t(const TcArgs &a, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-// Row bands so that the grid is about three waves of one CTA per SM.
-int pick_rows_tc(int w, int h, int win) {
+// Row bands: one CTA per SM (all of TMEM), so the launch takes ceil(CTAs / SMs) waves of about
+// (band rows + the window's halo) input rows each. The band count that minimises that product.
+int pick_rows_tc(int w, int h, int win, int sms) {
   const int outc = kTM - 2 * (win / 2);
-  const int ntx = (w + outc - 1) / outc;
-  int bands = (3 * 152 + 2 * ntx - 1) / (2 * ntx);
-  bands = max(1, min(bands, h));
-  return (h + bands - 1) / bands;
+  const long ntx = (w + outc - 1) / outc;
+  long best_cost = -1;
+  int best_rows = h;
+  for (int bands = 1; bands <= h; ++bands) {
+    const int rows = (h + bands - 1) / bands;
+    if (bands > 1 && rows == (h + bands - 2) / (bands - 1)) continue;  // same rows as fewer bands
+    const long waves = (2 * ntx * bands + sms - 1) / sms;
+    const long cost = waves * (rows + 2 * (win / 2));
+    if (best_cost < 0 || cost < best_cost) {
+      best_cost = cost;
+      best_rows = rows;
+    }
+  }
+  return best_rows;
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
@@ -675,7 +717,7 @@ bool cost_tc_supported(const bsm_ctx *ctx) { return ctx->nw == 8 && ctx->p.mask_
 
 int cost_tc_rows(const bsm_ctx *ctx, int w, int h, int dmax) {
   (void)dmax;
-  return ctx->cost_rows > 0 ? ctx->cost_rows : pick_rows_tc(w, h, ctx->p.agg_window);
+  return ctx->cost_rows > 0 ? ctx->cost_rows : pick_rows_tc(w, h, ctx->p.agg_window, ctx->sms > 0 ? ctx->sms : 152);
 }
 
 cudaError_t launch_cost_tc(const bsm_ctx *ctx, const uint32_t *BL, const uint32_t *PhiL, const uint32_t *BR,

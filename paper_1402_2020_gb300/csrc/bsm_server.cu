@@ -57,10 +57,16 @@ struct Lane {
 // plane of its largest large request (4 bytes per pixel each).
 struct LaneNeed {
   int64_t batch_px = 0, pair_px = 0;
+  int32_t pair_w = 0, pair_h = 0;  // the largest per-pair request
   void add(const bsm_request &r) {
     const int64_t px = (int64_t)r.w * r.h;
-    if ((int64_t)r.w * r.h * r.dmax < kPerPairWork) batch_px += px;
-    else pair_px = std::max(pair_px, px);
+    if ((int64_t)r.w * r.h * r.dmax < kPerPairWork) {
+      batch_px += px;
+    } else if (px > pair_px) {
+      pair_px = px;
+      pair_w = r.w;
+      pair_h = r.h;
+    }
   }
   size_t growth(const Lane &l) const {
     return 4 * (size_t)(std::max<int64_t>(0, batch_px - l.plane_pixels) + std::max<int64_t>(0, pair_px - l.pair_pixels));
@@ -123,7 +129,7 @@ bsm_status launch_batch(bsm_server *s, Lane &lane) {
     lane.plane_pixels = need.batch_px;
   }
   if (need.pair_px > lane.pair_pixels) {
-    const bsm_status r = bsm_reserve(lane.ctx, (int32_t)need.pair_px, 1);
+    const bsm_status r = bsm_reserve(lane.ctx, need.pair_w, need.pair_h);
     if (r != BSM_OK) return r;
     lane.pair_pixels = need.pair_px;
   }

@@ -84,3 +84,69 @@ def test_bracket_statistic_from_half_pairs():
         s1 = min(max(l1, h1), min(l2, h2))
         srt = np.sort(w)
         assert s0 == srt[0] and s1 == srt[1]
+
+
+# ---------------------------------------------------------------- the tensor-core cost kernel's operands
+# Eq. 8 as a product: with s_i = Phi_i (1 - 2 B_i) and o_i the other view's bit, the masked Hamming cost
+# is popcount(Phi & B) + sum_i s_i o_i. The kernel stores o_i and s_i as E4M3 bytes; byte k of operand
+# word q carries bit 8k + q of a descriptor word. The checks below restate the kernel's byte formulas
+# and decode them as E4M3 values.
+
+def e4m3(byte):
+    """Value of an E4M3 byte (sign, 4 exponent bits with bias 7, 3 mantissa bits; subnormals below 2^-6)."""
+    sign = -1.0 if byte & 0x80 else 1.0
+    e, m = (byte >> 3) & 15, byte & 7
+    assert not (e == 15 and m == 7), "NaN"
+    return sign * (m / 8.0 * 2.0 ** -6 if e == 0 else (1 + m / 8.0) * 2.0 ** (e - 7))
+
+
+def b_words(o):
+    """The kernel's B operand words 0..7 of one other-view word o."""
+    return [o & 0x01010101, o & 0x02020202, o & 0x04040404, o & 0x08080808, o & 0x10101010, o & 0x20202020,
+            o & 0x40404040, (o >> 1) & 0x40404040]
+
+
+def a_words(b, m):
+    """The kernel's A operand words 0..7 of one descriptor word b and mask word m."""
+    sb = m & b
+    P = (0x70, 0x68, 0x60, 0x58, 0x50, 0x40)
+    out = [(((m & (0x01010101 << q)) * (P[q] >> q)) + ((sb & (0x01010101 << q)) * (0x80 >> q))) & M32
+           for q in range(6)]
+    out.append(((m >> 1) & 0x20202020) | ((sb << 1) & 0x80808080))
+    out.append(((m >> 2) & 0x20202020) | (sb & 0x80808080))
+    return out
+
+
+def test_tc_operand_bytes_decode_to_s_and_o():
+    rng = np.random.default_rng(5)
+    for _ in range(300):
+        b, m, o = (int(v) for v in rng.integers(0, 1 << 32, size=3, dtype=np.uint64))
+        A, Bw = a_words(b, m), b_words(o)
+        for q in range(8):
+            for k in range(4):
+                bit = 8 * k + q
+                s = ((m >> bit) & 1) * (1 - 2 * ((b >> bit) & 1))
+                ov = (o >> bit) & 1
+                ab, bb = (A[q] >> 8 * k) & 0xFF, (Bw[q] >> 8 * k) & 0xFF
+                assert e4m3(ab) * e4m3(bb) == s * ov * 0.25, (q, k, hex(ab), hex(bb))
+                if ov == 0:
+                    assert bb == 0
+                if s == 0:
+                    assert ab == 0
+
+
+def test_tc_product_equals_masked_hamming_cost():
+    # the 256-bit cost of Eq. 8 (reference mask) from the operand bytes: 4 * sum(a * o) + popcount(Phi & B)
+    rng = np.random.default_rng(6)
+    for _ in range(200):
+        B = [int(v) for v in rng.integers(0, 1 << 32, size=8, dtype=np.uint64)]
+        P = [int(v) for v in rng.integers(0, 1 << 32, size=8, dtype=np.uint64)]
+        O = [int(v) for v in rng.integers(0, 1 << 32, size=8, dtype=np.uint64)]
+        acc = 0.0
+        for j in range(8):
+            A, Bw = a_words(B[j], P[j]), b_words(O[j])
+            for q in range(8):
+                for k in range(4):
+                    acc += e4m3((A[q] >> 8 * k) & 0xFF) * e4m3((Bw[q] >> 8 * k) & 0xFF)
+        want = sum(bin((B[j] ^ O[j]) & P[j]).count("1") for j in range(8))
+        assert 4 * acc + sum(bin(P[j] & B[j]).count("1") for j in range(8)) == want
