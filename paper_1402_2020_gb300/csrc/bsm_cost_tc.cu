@@ -42,27 +42,27 @@ namespace {
 
 constexpr int kTM = 128;          // reference columns per CTA: MMA M, TMEM lanes
 constexpr int kNB = 384;          // B operand rows: the band of 128 + 256 - 1 other-view columns
-constexpr int kChunk = 64;        // K bytes per operand chunk: 4 K groups of 16 bytes (2 descriptor words)
-constexpr int kBuf = 3;           // operand buffers
-constexpr int kBW = 6;            // operand builder warps (warps 2 .. kBW + 1)
+constexpr int kChunk = 64;        // K bytes per operand chunk: 2 descriptor words (2 MMA k-steps of 32)
+constexpr int kBuf = 4;           // operand buffers: A in TMEM, B in shared memory
+constexpr int kBW = 4;            // operand builder warps (warps 2 .. kBW + 1)
 constexpr int kE0 = 2 + kBW;      // first epilogue warp
 constexpr int kWarps = kE0 + 12;  // producer, MMA, builders, 12 epilogue warps (3 per TMEM lane quadrant)
 constexpr int kThreads = 32 * kWarps;
 constexpr int kXpd = kBW * 32;    // operand builder threads
-// B-operand band columns: builder thread t < kTM, which also forms A row t, owns band column t; each of
-// the other kXpd - kTM threads owns kBC of the rest, so every builder warp does about the same work
-// (an A word costs about three times a B word)
-constexpr int kBC = (kNB - kTM) / (kXpd - kTM);
-static_assert(kXpd >= kTM && kTM + (kXpd - kTM) * kBC == kNB, "band columns split over the builders");
+// Builder warp w (2 .. 5) forms the A rows of TMEM lane quadrant w % 4 (the quadrant its tcgen05.st
+// reaches) and, with its thread index bt = tid - 64, the band columns bt + kBT j of the B operand; the
+// hardware places warps 2 .. 5 on schedulers 2, 3, 0, 1, one builder per scheduler. (Six builder
+// warps, the A rows on four of them, measured slower.)
+constexpr int kBT = kXpd;                // band-column threads
+constexpr int kBC = kNB / kBT;
+static_assert(kXpd == kTM && kBT * kBC == kNB, "one A row and kBC band columns per builder thread");
 constexpr int kEpi = 12 * 32;     // epilogue threads (warps kE0 .. kE0 + 11)
 constexpr int kTP = 288;          // u16 pitch of the term table T[x][d] (rows 16-byte aligned)
 constexpr int kTPad = 32;         // u16 in front of row 0; row r's band terms past d = 255 land in row r + 1's first 32
-constexpr int kAB = kTM * kChunk;         // A chunk: 4 groups x 128 rows x 16 bytes
-constexpr int kBB = kNB * kChunk;         // B chunk: 4 groups x 384 rows x 16 bytes
-constexpr int kOpB = kAB + kBB;           // one operand buffer (32 KB)
+constexpr int kBB = kNB * kChunk;         // B chunk: 4 groups x 384 rows x 16 bytes (24 KB)
 constexpr int kRawRow = kNB * 32;         // other-view words of one row of the band (8 words per column)
 constexpr int kOffOp = 0;
-constexpr int kOffRaw = kOffOp + kBuf * kOpB;          // 2 slots x (entering, leaving) rows
+constexpr int kOffRaw = kOffOp + kBuf * kBB;           // 2 slots x (entering, leaving) rows
 constexpr int kOffT = kOffRaw + 2 * 2 * kRawRow;
 constexpr int kOffC0 = kOffT + (kTM * kTP + kTPad) * 2;
 constexpr int kC0Ring = 8;        // rows of window popcounts in flight between builders and epilogue
@@ -73,6 +73,11 @@ static_assert(kSmem <= 232448, "shared memory of one CTA");
 static_assert(kOffRaw % 1024 == 0 && kOffT % 1024 == 0 && kOffC0 % 16 == 0 && kOffMisc % 16 == 0 && (kTP * 2) % 16 == 0 &&
                   (kTPad * 2) % 16 == 0 && kTP >= 256 + kTPad,
               "alignment");
+// TMEM: 512 columns; the accumulator takes columns 0 .. 383, A buffer b columns kACol + 16 b .. + 15
+// (16 32-bit columns hold a row's 64 E4M3 K bytes of one chunk)
+constexpr uint32_t kTmemCols = 512;
+constexpr uint32_t kACol = 384;
+static_assert(kACol + 16 * kBuf <= kTmemCols, "A buffers beside the accumulator");
 constexpr long long kWait = 1LL << 31;  // about one second at the GB300 clock
 
 struct TcArgs {
@@ -153,9 +158,18 @@ __device__ __forceinline__ uint32_t instr_desc(int n, bool neg_a) {
   return (1u << 4) | (neg_a ? (1u << 13) : 0u) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(kTM >> 4) << 24);
 }
 
-__device__ __forceinline__ void mma_f8(uint32_t tmem, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t acc) {
-  asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\ntcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}"
-               ::"r"(tmem), "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+// D (TMEM) += or = A (TMEM, K-major: row m in lane m, 4 K bytes per 32-bit column) x B^T (shared memory).
+__device__ __forceinline__ void mma_f8_ta(uint32_t tmem_d, uint32_t tmem_a, uint64_t bd, uint32_t idesc, uint32_t acc) {
+  asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\ntcgen05.mma.cta_group::1.kind::f8f6f4 [%0], [%1], %2, %3, p;\n}"
+               ::"r"(tmem_d), "r"(tmem_a), "l"(bd), "r"(idesc), "r"(acc));
+}
+
+// 16 consecutive TMEM columns of the warp's lane quadrant from 16 registers per thread.
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&r)[16]) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};"
+               ::"r"(taddr), "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]),
+                 "r"(r[8]), "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15])
+               : "memory");
 }
 
 __device__ __forceinline__ void mma_commit(uint64_t *bar) {
@@ -164,8 +178,7 @@ __device__ __forceinline__ void mma_commit(uint64_t *bar) {
 }
 
 // 32 consecutive accumulator columns of the warp's 32 TMEM lanes into r, asynchronously: the registers
-// hold the values only after tmem_wait_ld(). (Overlapping one chunk's load with the previous chunk's
-// conversion needs 32 more live registers, which spill at this kernel's 96.)
+// hold the values only after tmem_wait_ld().
 __device__ __forceinline__ void tmem_ld32_async(uint32_t taddr, uint32_t (&r)[32]) {
   asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
                "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
@@ -210,13 +223,18 @@ __device__ __forceinline__ uint32_t a_word(uint32_t m, uint32_t sb) {
   return (m & M) * (P[Q] >> Q) + (sb & M) * (0x80u >> Q);
 }
 
-// 32 K bytes of the A operand from one descriptor word b and mask word m of the reference column.
-__device__ __forceinline__ void expand_a(uint32_t b, uint32_t m, uint8_t *dst_g0, uint8_t *dst_g1) {
+// 32 K bytes (8 words, from word o of `out`) of the A operand from one descriptor word b and mask word m
+// of the reference column.
+__device__ __forceinline__ void expand_a(uint32_t b, uint32_t m, uint32_t (&out)[16], int o) {
   const uint32_t sb = m & b;
-  *reinterpret_cast<uint4 *>(dst_g0) = make_uint4(a_word<0>(m, sb), a_word<1>(m, sb), a_word<2>(m, sb), a_word<3>(m, sb));
-  *reinterpret_cast<uint4 *>(dst_g1) =
-      make_uint4(a_word<4>(m, sb), a_word<5>(m, sb), ((m >> 1) & 0x20202020u) | ((sb << 1) & 0x80808080u),
-                 ((m >> 2) & 0x20202020u) | (sb & 0x80808080u));
+  out[o + 0] = a_word<0>(m, sb);
+  out[o + 1] = a_word<1>(m, sb);
+  out[o + 2] = a_word<2>(m, sb);
+  out[o + 3] = a_word<3>(m, sb);
+  out[o + 4] = a_word<4>(m, sb);
+  out[o + 5] = a_word<5>(m, sb);
+  out[o + 6] = ((m >> 1) & 0x20202020u) | ((sb << 1) & 0x80808080u);
+  out[o + 7] = ((m >> 2) & 0x20202020u) | (sb & 0x80808080u);
 }
 
 // ---------------------------------------------------------------- cost kernel
@@ -225,6 +243,7 @@ template <int WIN, int DIR>
 __device__ __forceinline__ void cost_tc_body(const TcArgs &a, uint8_t *smem) {
   constexpr int R = WIN / 2, OUTC = kTM - 2 * R;
   constexpr bool PK = 256 * WIN * WIN < 8192;  // aggregated costs below 2^13: 16-bit (A << 3 | dd) keys
+  constexpr int kHC = (OUTC + 11) / 12;        // output columns per epilogue warp in the horizontal pass
   static_assert(WIN + 1 <= kC0Ring, "the popcount ring holds the rows the builders may run ahead");
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const CUtensorMap *bmap0 = &a.bmap0[DIR], *bmap1 = &a.bmap1[DIR];
@@ -236,7 +255,6 @@ __device__ __forceinline__ void cost_tc_body(const TcArgs &a, uint8_t *smem) {
   const int D = (dmax + 31) & ~31;             // band depth: disparities per reference column
   const int ntot = kTM + D;                    // band columns, the MMA's N in total
   const int nb0 = ntot < 256 ? ntot : 256, nb1 = ntot - nb0;
-  const uint32_t ncols = ntot <= 256 ? 256u : 512u;
   const int X0 = (int)blockIdx.x * OUTC - R;   // column of TMEM lane 0
   const int xb0 = DIR == 0 ? X0 - D + 1 : X0;  // other-view column of band column 0
   const int yb = (int)blockIdx.y * a.rows, ye = min(h, yb + a.rows);
@@ -272,7 +290,7 @@ __device__ __forceinline__ void cost_tc_body(const TcArgs &a, uint8_t *smem) {
   }
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(saddr(tmem_slot)),
-                 "r"(ncols));
+                 "r"(kTmemCols));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -329,15 +347,15 @@ __device__ __forceinline__ void cost_tc_body(const TcArgs &a, uint8_t *smem) {
           ok = mbar_wait(&full[b], (slot / kBuf) & 1u);
           if (!ok) break;
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-          const uint32_t op = saddr(smem + kOffOp + b * kOpB);
+          const uint32_t op = saddr(smem + kOffOp + b * kBB);
 #pragma unroll
           for (int ks = 0; ks < 2; ++ks) {
-            const uint64_t ad = smem_desc(op + ks * 2 * (kTM * 16), kTM * 16, 128);
+            const uint32_t ta = tmem + kACol + 16 * b + 8 * ks;  // A of this k-step: 8 columns of 4 K bytes
             const uint32_t acc = (acc_init || ks > 0) ? 1u : 0u;
-            mma_f8(tmem, ad, smem_desc(op + kAB + ks * 2 * (kNB * 16), kNB * 16, 128), instr_desc(nb0, !is_new), acc);
+            mma_f8_ta(tmem, ta, smem_desc(op + ks * 2 * (kNB * 16), kNB * 16, 128), instr_desc(nb0, !is_new), acc);
             if (nb1 > 0)
-              mma_f8(tmem + 256, ad, smem_desc(op + kAB + ks * 2 * (kNB * 16) + 256 * 16, kNB * 16, 128),
-                     instr_desc(nb1, !is_new), acc);
+              mma_f8_ta(tmem + 256, ta, smem_desc(op + ks * 2 * (kNB * 16) + 256 * 16, kNB * 16, 128),
+                        instr_desc(nb1, !is_new), acc);
           }
           mma_commit(&empty[b]);
           acc_init = true;
@@ -352,10 +370,13 @@ __device__ __forceinline__ void cost_tc_body(const TcArgs &a, uint8_t *smem) {
       if (!ok) atomicExch(abort_flag, 1u);
     }
   } else if (warp < kE0) {
-    // ---- operand builders: per chunk, the A operand's row t < 128 (the s bytes of reference column X0 + t,
-    // from its descriptor and mask words) with band column t, or band columns kTM + (t - kTM) + (kXpd - kTM) j
-    const int t = tid - 64, xa = X0 + t;
-    const bool has_a = t < kTM, a_in = has_a && xa >= 0 && xa < w;
+    // ---- operand builders: per chunk, the A operand's row ra of this warp's TMEM lane quadrant (the s
+    // bytes of reference column X0 + ra, from its descriptor and mask words), written to TMEM, and the B
+    // operand's band columns bt + kXpd j in shared memory
+    const int ra = 32 * (warp & 3) + lane, xa = X0 + ra, bt = tid - 64;
+    constexpr bool has_a = true, has_b = true;
+    const bool a_in = xa >= 0 && xa < w;
+    const uint32_t ta_lane = tmem + ((uint32_t)(32 * (warp & 3)) << 16);  // this warp's lane quadrant
     auto present = [&](int ii, int hh) { return hh == 0 ? row_new(ii) : row_old(ii); };
     // the reference words of the next (row, half) with an image row are loaded one half ahead
     auto load_ref = [&](int ii, int hh, uint4(&q)[4]) {
@@ -378,7 +399,7 @@ __device__ __forceinline__ void cost_tc_body(const TcArgs &a, uint8_t *smem) {
       } while (ni < n_it && !present(ni, nh));
     };
     if (!present(0, 0)) advance();
-    int c0run = 0;  // the window's popcount(Phi AND B) of column X0 + t
+    int c0run = 0;  // the window's popcount(Phi AND B) of column X0 + ra
     uint4 nxt[4];
     if (ni < n_it) load_ref(ni, nh, nxt);
     uint32_t slot = 0;
@@ -406,40 +427,41 @@ __device__ __forceinline__ void cost_tc_body(const TcArgs &a, uint8_t *smem) {
         }
         const uint32_t *rw = reinterpret_cast<const uint32_t *>(raw + half * kRawRow);
         uint4 qw[kBC];  // words 4 (cc / 2) .. 4 (cc / 2) + 3 of each of the thread's band columns
-        const int nbc = has_a ? 1 : kBC;  // uniform in the warp
-        auto bcol = [&](int k) { return has_a ? t : kTM + (t - kTM) + (kXpd - kTM) * k; };
 #pragma unroll
         for (int cc = 0; cc < 4; ++cc) {  // chunk cc: descriptor words 2 cc and 2 cc + 1
           if (!ok) break;
           if ((cc & 1) == 0) {
 #pragma unroll
             for (int k = 0; k < kBC; ++k) {
-              const int r = bcol(k);
-              if (k < nbc)
+              const int r = bt + kBT * k;
+              if (has_b)
                 qw[k] = r < ntot ? *reinterpret_cast<const uint4 *>(rw + r * 8 + 2 * cc) : make_uint4(0u, 0u, 0u, 0u);
             }
           }
           const int b = (int)(slot % kBuf);
           if (slot >= kBuf) ok = mbar_wait(&empty[b], ((slot / kBuf) - 1) & 1u);
           if (!ok) break;
-          uint8_t *opA = smem + kOffOp + b * kOpB, *opB = opA + kAB;
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");  // the MMAs that read buffer b are done
           if (has_a) {
             const uint4 &bq = cur[cc >> 1], &mq = cur[2 + (cc >> 1)];
-            expand_a((cc & 1) ? bq.z : bq.x, (cc & 1) ? mq.z : mq.x, opA + 0 * (kTM * 16) + t * 16,
-                     opA + 1 * (kTM * 16) + t * 16);
-            expand_a((cc & 1) ? bq.w : bq.y, (cc & 1) ? mq.w : mq.y, opA + 2 * (kTM * 16) + t * 16,
-                     opA + 3 * (kTM * 16) + t * 16);
+            uint32_t av[16];
+            expand_a((cc & 1) ? bq.z : bq.x, (cc & 1) ? mq.z : mq.x, av, 0);
+            expand_a((cc & 1) ? bq.w : bq.y, (cc & 1) ? mq.w : mq.y, av, 8);
+            tmem_st16(ta_lane + kACol + 16 * b, av);
           }
+          uint8_t *opB = smem + kOffOp + b * kBB;
 #pragma unroll
           for (int k = 0; k < kBC; ++k) {
-            const int r = bcol(k);
-            if (k < nbc && r < ntot) {
+            const int r = bt + kBT * k;
+            if (has_b && r < ntot) {
               const uint4 &qq = qw[k];
               expand_b((cc & 1) ? qq.z : qq.x, opB + 0 * (kNB * 16) + r * 16, opB + 1 * (kNB * 16) + r * 16);
               expand_b((cc & 1) ? qq.w : qq.y, opB + 2 * (kNB * 16) + r * 16, opB + 3 * (kNB * 16) + r * 16);
             }
           }
+          if (has_a) asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
           asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+          asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
           __syncwarp();
           if (lane == 0) mbar_arrive(&full[b]);
           ++slot;
@@ -448,7 +470,7 @@ __device__ __forceinline__ void cost_tc_body(const TcArgs &a, uint8_t *smem) {
       __syncwarp();
       if (lane == 0 && ok) mbar_arrive(&raw_empty[rs]);  // this row's words are no longer needed
       if (ok) {  // the window's popcount after input row i, for the epilogue
-        if (has_a) ring[(i & (kC0Ring - 1)) * kTM + t] = c0run;
+        if (has_a) ring[(i & (kC0Ring - 1)) * kTM + ra] = c0run;
         __syncwarp();
         if (lane == 0) mbar_arrive(&c0_full[i & (kC0Ring - 1)]);
       }
@@ -526,6 +548,8 @@ __device__ __forceinline__ void cost_tc_body(const TcArgs &a, uint8_t *smem) {
           }
         };
         auto col_addr = [&](int k) { return tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(32 * q + 32 * k); };
+        // one chunk at a time (two in flight need 32 more live registers: at 18 warps, five share a
+        // scheduler, which caps a thread at 96 and would spill)
         const int k0 = g, k1 = g + 3, k2 = g + 6;
         {
           uint32_t va[32];
@@ -561,18 +585,21 @@ __device__ __forceinline__ void cost_tc_body(const TcArgs &a, uint8_t *smem) {
       }
       epi_sync();  // T complete
 
-      // horizontal box sum + Eq. 1: warp ew takes output columns rr0 .. rr1 - 1, lane 8 disparities
-      const int rr0 = R + 11 * ew, rr1 = min(rr0 + 11, kTM - R);
+      // horizontal box sum + Eq. 1: warp ew takes output columns rr0 .. rr0 + ncol - 1, lane 8 disparities;
+      // the lane keeps the window's 2R + 1 rows of T in a register ring, so each column reads one new row
+      const int rr0 = R + kHC * ew, ncol = min(kHC, OUTC - kHC * ew);
       const int d8 = 8 * lane;
-      if (rr0 < rr1) {
+      if (ncol > 0) {
         const bool lane_on = d8 < D;
+        auto trow = [&](int rr) {
+          return lane_on ? *reinterpret_cast<const uint4 *>(T + rr * kTP + d8) : make_uint4(0u, 0u, 0u, 0u);
+        };
+        uint4 ring[2 * R + 1];
         uint32_t s4[4] = {0, 0, 0, 0};
-        if (lane_on) {
 #pragma unroll
-          for (int u = -R; u <= R; ++u) {
-            const uint4 t4 = *reinterpret_cast<const uint4 *>(T + (rr0 + u) * kTP + d8);
-            s4[0] += t4.x; s4[1] += t4.y; s4[2] += t4.z; s4[3] += t4.w;
-          }
+        for (int u = 0; u < 2 * R + 1; ++u) {
+          ring[u] = trow(rr0 - R + u);
+          s4[0] += ring[u].x; s4[1] += ring[u].y; s4[2] += ring[u].z; s4[3] += ring[u].w;
         }
         uint32_t inval[4];  // halves holding a disparity at or above dmax never win
 #pragma unroll
@@ -583,20 +610,16 @@ __device__ __forceinline__ void cost_tc_body(const TcArgs &a, uint8_t *smem) {
         auto columns = [&](auto full_tag) {
           constexpr bool FULL = decltype(full_tag)::value;
           int32_t mydisp = 0;
-          // the next column's entering and leaving rows are loaded one column ahead
-          uint4 tn = make_uint4(0u, 0u, 0u, 0u), to = tn;
-          if (lane_on && rr0 + 1 < rr1) {
-            tn = *reinterpret_cast<const uint4 *>(T + (rr0 + 1 + R) * kTP + d8);
-            to = *reinterpret_cast<const uint4 *>(T + (rr0 - R) * kTP + d8);
-          }
-#pragma unroll 2
-          for (int rr = rr0; rr < rr1; ++rr) {
-            if (rr > rr0) {
-              s4[0] += tn.x - to.x; s4[1] += tn.y - to.y; s4[2] += tn.z - to.z; s4[3] += tn.w - to.w;
-              if (lane_on && rr + 1 < rr1) {
-                tn = *reinterpret_cast<const uint4 *>(T + (rr + 1 + R) * kTP + d8);
-                to = *reinterpret_cast<const uint4 *>(T + (rr - R) * kTP + d8);
-              }
+          uint4 tn = ncol > 1 ? trow(rr0 + R + 1) : make_uint4(0u, 0u, 0u, 0u);  // next column's entering row
+#pragma unroll
+          for (int c = 0; c < kHC; ++c) {
+            if (c >= ncol) break;
+            const int rr = rr0 + c;
+            if (c > 0) {  // slide: the entering row replaces the leaving one in the ring
+              uint4 &old = ring[(c - 1) % (2 * R + 1)];
+              s4[0] += tn.x - old.x; s4[1] += tn.y - old.y; s4[2] += tn.z - old.z; s4[3] += tn.w - old.w;
+              old = tn;
+              if (c + 1 < ncol) tn = trow(rr + R + 1);
             }
             uint32_t key;
             if constexpr (PK && FULL) {
@@ -622,7 +645,7 @@ __device__ __forceinline__ void cost_tc_body(const TcArgs &a, uint8_t *smem) {
               }
             }
             key = __reduce_min_sync(0xFFFFFFFFu, key);
-            mydisp = lane == rr - rr0 ? (int32_t)(key & 0xFFu) : mydisp;
+            mydisp = lane == c ? (int32_t)(key & 0xFFu) : mydisp;
             const int x = X0 + rr;
             if (cost != nullptr && lane_on && x >= 0 && x < w) {
               uint16_t *cp = cost + ((size_t)yout * w + x) * dmax;
@@ -635,7 +658,7 @@ __device__ __forceinline__ void cost_tc_body(const TcArgs &a, uint8_t *smem) {
           }
           // lane c holds column rr0 + c's disparity: one store for the warp's columns
           const int xo = X0 + rr0 + lane;
-          if (lane < rr1 - rr0 && xo >= 0 && xo < w) disp[(size_t)yout * w + xo] = mydisp;
+          if (lane < ncol && xo >= 0 && xo < w) disp[(size_t)yout * w + xo] = mydisp;
         };
         if (dmax == 256) columns(std::true_type{});
         else columns(std::false_type{});
@@ -646,7 +669,7 @@ __device__ __forceinline__ void cost_tc_body(const TcArgs &a, uint8_t *smem) {
   if (tid == 0 && *abort_flag != 0) atomicCAS(a.status, 0u, (uint32_t)BSM_ERR_TIMEOUT);
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
-  if (warp == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols));
+  if (warp == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols));
 }
 
 template <int WIN>

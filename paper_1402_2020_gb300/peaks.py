@@ -21,9 +21,10 @@ PROBE_SRC = os.path.join(HERE, "probe", "issue_rate.cu")
 PROBE_LIB = os.path.join(HERE, "_lib", "libbsm_probe.so")
 SUMMARY = os.path.join(os.path.dirname(HERE), "profiles", "int_issue_rates_gb300.md")
 
-# op index in the probe -> name (the SASS-level instruction each inline-PTX form issues)
+# op index in the probe -> name (the SASS-level instruction each inline-PTX form issues; MIN16X2_LOP3 is a
+# packed 16-bit minimum followed by a LOP3, counted as one step)
 OPS = ("POPC", "LOP3", "IADD", "SHF", "PRMT", "IMAD", "VABSDIFF4", "DP4A", "IMNMX", "SHFL", "REDUX", "FFMA",
-       "HFMA2")
+       "HFMA2", "MIN16X2_LOP3")
 
 
 def source_hash() -> str:

@@ -21,7 +21,7 @@ constexpr int kChains = 8;
 
 enum Op {
   OP_POPC = 0, OP_LOP3, OP_IADD3, OP_SHF, OP_PRMT, OP_IMAD, OP_VABSDIFF4, OP_DP4A, OP_IMNMX, OP_SHFL, OP_REDUX,
-  OP_FFMA, OP_HFMA2, OP_COUNT
+  OP_FFMA, OP_HFMA2, OP_MIN16X2, OP_COUNT
 };
 
 template <int OP>
@@ -39,7 +39,8 @@ __device__ __forceinline__ void step(uint32_t &r, uint32_t k1, uint32_t k2) {
   else if constexpr (OP == OP_SHFL) asm volatile("shfl.sync.bfly.b32 %0, %0, 1, 0x1f, 0xffffffff;" : "+r"(r));
   else if constexpr (OP == OP_REDUX) asm volatile("redux.sync.min.u32 %0, %0, 0xffffffff;" : "+r"(r));
   else if constexpr (OP == OP_FFMA) asm volatile("fma.rn.f32 %0, %0, %1, %2;" : "+r"(r) : "r"(k1), "r"(k2));
-  else asm volatile("fma.rn.f16x2 %0, %0, %1, %2;" : "+r"(r) : "r"(k1), "r"(k2));
+  else if constexpr (OP == OP_HFMA2) asm volatile("fma.rn.f16x2 %0, %0, %1, %2;" : "+r"(r) : "r"(k1), "r"(k2));
+  else asm volatile("{\n.reg .b32 t;\nmin.u16x2 t, %0, %1;\nxor.b32 %0, t, %2;\n}" : "+r"(r) : "r"(k1), "r"(k2));
 }
 
 template <int OP>
@@ -107,6 +108,7 @@ cudaError_t launch_op(int op, int blocks, int iters, uint32_t *sink, long long *
     case OP_REDUX: return launch<OP_REDUX>(blocks, iters, sink, rec);
     case OP_FFMA: return launch<OP_FFMA>(blocks, iters, sink, rec);
     case OP_HFMA2: return launch<OP_HFMA2>(blocks, iters, sink, rec);
+    case OP_MIN16X2: return launch<OP_MIN16X2>(blocks, iters, sink, rec);
   }
   return cudaErrorInvalidValue;
 }
