@@ -239,18 +239,21 @@ __device__ __forceinline__ void expand_a(uint32_t b, uint32_t m, uint32_t (&out)
 
 // ---------------------------------------------------------------- cost kernel
 
-template <int WIN, int DIR>
+template <int WIN, int DIR, bool WC>
 __device__ __forceinline__ void cost_tc_body(const TcArgs &a, uint8_t *smem) {
   constexpr int R = WIN / 2, OUTC = kTM - 2 * R;
   constexpr bool PK = 256 * WIN * WIN < 8192;  // aggregated costs below 2^13: 16-bit (A << 3 | dd) keys
   constexpr int kHC = (OUTC + 11) / 12;        // output columns per epilogue warp in the horizontal pass
+  // With 16-bit keys the term table holds 8 x each term, so a column's packed window sums are directly
+  // (A << 3 | d % 8) once the disparity's low bits are added at the window's start.
+  constexpr uint32_t kTS = PK ? 8u : 1u;
   static_assert(WIN + 1 <= kC0Ring, "the popcount ring holds the rows the builders may run ahead");
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const CUtensorMap *bmap0 = &a.bmap0[DIR], *bmap1 = &a.bmap1[DIR];
   const uint32_t *__restrict__ Bref = DIR ? a.Bv[1] : a.Bv[0];
   const uint32_t *__restrict__ Pref = DIR ? a.Pv[1] : a.Pv[0];
   int32_t *__restrict__ disp = DIR ? a.disp[1] : a.disp[0];
-  uint16_t *cost = DIR ? a.cost[1] : a.cost[0];
+  uint16_t *cost = WC ? (DIR ? a.cost[1] : a.cost[0]) : nullptr;  // WC: the cost volume is written
   const int w = a.w, h = a.h, dmax = a.dmax;
   const int D = (dmax + 31) & ~31;             // band depth: disparities per reference column
   const int ntot = kTM + D;                    // band columns, the MMA's N in total
@@ -501,9 +504,9 @@ __device__ __forceinline__ void cost_tc_body(const TcArgs &a, uint8_t *smem) {
 #pragma unroll
       for (int v = -R; v <= R; ++v) nh += (yout + v >= 0 && yout + v < h) ? 1 : 0;
       {
-        const float base = (float)c0v[r] + 12582912.0f;  // 1.5 * 2^23: the sum's integer in the low bits
+        const float base = (float)(kTS * c0v[r]) + 12582912.0f;  // 1.5 * 2^23: the sum's integer in the low bits
         const int nck = D / 32 + 1;
-        const uint32_t sentinel = col_in ? (uint32_t)nh * 256u : 0u;
+        const uint32_t sentinel = col_in ? kTS * (uint32_t)nh * 256u : 0u;
         // Element t of chunk k is disparity c - t (left reference) or c + t (right); its terms are
         // consecutive 16-bit entries of row r from u16 index a0 = r kTP + c down (left) or up (right),
         // written as 32-bit words: where a0 sits mid-word, 15 whole words and two single entries. Terms
@@ -529,7 +532,7 @@ __device__ __forceinline__ void cost_tc_body(const TcArgs &a, uint8_t *smem) {
         // chunk kk of this warp (k = g + 3 kk): convert to 16-bit terms and pack them as words
         auto process = [&](uint32_t(&v)[32], int k, uint32_t(&wk)[16]) {
 #pragma unroll
-          for (int t = 0; t < 32; ++t) v[t] = __float_as_uint(fmaf(__uint_as_float(v[t]), 4.0f, base));
+          for (int t = 0; t < 32; ++t) v[t] = __float_as_uint(fmaf(__uint_as_float(v[t]), 4.0f * kTS, base));
           const int a0 = chunk_a0(k);
           if (!fast) {  // the sentinel where the match leaves the other view; 0 for columns off the image
             const int c = a0 - r * kTP;
@@ -595,7 +598,9 @@ __device__ __forceinline__ void cost_tc_body(const TcArgs &a, uint8_t *smem) {
           return lane_on ? *reinterpret_cast<const uint4 *>(T + rr * kTP + d8) : make_uint4(0u, 0u, 0u, 0u);
         };
         uint4 ring[2 * R + 1];
-        uint32_t s4[4] = {0, 0, 0, 0};
+        uint32_t s4[4];  // with 16-bit keys: 8 x the window sums of disparities d8 + 2 j (low), + 2 j + 1 (high), plus 2 j, 2 j + 1
+#pragma unroll
+        for (int j = 0; j < 4; ++j) s4[j] = PK ? ((uint32_t)(2 * j) | ((uint32_t)(2 * j + 1) << 16)) : 0u;
 #pragma unroll
         for (int u = 0; u < 2 * R + 1; ++u) {
           ring[u] = trow(rr0 - R + u);
@@ -605,8 +610,8 @@ __device__ __forceinline__ void cost_tc_body(const TcArgs &a, uint8_t *smem) {
 #pragma unroll
         for (int j = 0; j < 4; ++j)
           inval[j] = (d8 + 2 * j < dmax ? 0u : 0xFFFFu) | (d8 + 2 * j + 1 < dmax ? 0u : 0xFFFF0000u);
-        // FULL: dmax = 256, so every lane's 8 disparities are below dmax: no invalid halves to mask, and the
-        // key needs no select
+        const uint32_t lane_d = (uint32_t)d8;  // bits 3 .. 7 of every key of this lane
+        // FULL: dmax = 256, so every lane's 8 disparities are below dmax: no invalid halves to mask
         auto columns = [&](auto full_tag) {
           constexpr bool FULL = decltype(full_tag)::value;
           int32_t mydisp = 0;
@@ -622,20 +627,17 @@ __device__ __forceinline__ void cost_tc_body(const TcArgs &a, uint8_t *smem) {
               if (c + 1 < ncol) tn = trow(rr + R + 1);
             }
             uint32_t key;
-            if constexpr (PK && FULL) {
-              uint32_t m = s4[0] * 8u + 0x00010000u;
-#pragma unroll
-              for (int j = 1; j < 4; ++j)
-                m = vmin_u16x2(m, s4[j] * 8u + ((uint32_t)(2 * j) | ((uint32_t)(2 * j + 1) << 16)));
-              const uint32_t m16 = min(m & 0xFFFFu, m >> 16);  // (A << 3 | d % 8) of the lane's best
-              key = ((m16 & ~7u) << 5) | (uint32_t)d8 | (m16 & 7u);
-            } else if constexpr (PK) {
-              uint32_t m = 0xFFFFFFFFu;
-#pragma unroll
-              for (int j = 0; j < 4; ++j)
-                m = vmin_u16x2(m, (s4[j] * 8u + ((uint32_t)(2 * j) | ((uint32_t)(2 * j + 1) << 16))) | inval[j]);
-              const uint32_t m16 = min(m & 0xFFFFu, m >> 16);
-              key = (m16 == 0xFFFFu || !lane_on) ? 0xFFFFFFFFu : ((m16 >> 3) << 8) | (uint32_t)(d8 + (m16 & 7u));
+            if constexpr (PK) {
+              uint32_t m;
+              if constexpr (FULL) {
+                m = vmin_u16x2(vmin_u16x2(s4[0], s4[1]), vmin_u16x2(s4[2], s4[3]));
+              } else {
+                m = vmin_u16x2(vmin_u16x2(s4[0] | inval[0], s4[1] | inval[1]),
+                               vmin_u16x2(s4[2] | inval[2], s4[3] | inval[3]));
+              }
+              m = vmin_u16x2(m, __byte_perm(m, 0u, 0x1032));  // both halves: the lane's smallest (A << 3 | d % 8)
+              key = (((m & 0xFFF8u) << 5) | lane_d) | (m & 7u);  // A << 8 | d
+              if constexpr (!FULL) key = ((m & 0xFFFFu) == 0xFFFFu || !lane_on) ? 0xFFFFFFFFu : key;
             } else {
               key = 0xFFFFFFFFu;
 #pragma unroll
@@ -647,12 +649,12 @@ __device__ __forceinline__ void cost_tc_body(const TcArgs &a, uint8_t *smem) {
             key = __reduce_min_sync(0xFFFFFFFFu, key);
             mydisp = lane == c ? (int32_t)(key & 0xFFu) : mydisp;
             const int x = X0 + rr;
-            if (cost != nullptr && lane_on && x >= 0 && x < w) {
+            if (WC && lane_on && x >= 0 && x < w) {
               uint16_t *cp = cost + ((size_t)yout * w + x) * dmax;
 #pragma unroll
-              for (int j = 0; j < 4; ++j) {
-                if (d8 + 2 * j < dmax) cp[d8 + 2 * j] = (uint16_t)(s4[j] & 0xFFFFu);
-                if (d8 + 2 * j + 1 < dmax) cp[d8 + 2 * j + 1] = (uint16_t)(s4[j] >> 16);
+              for (int j = 0; j < 4; ++j) {  // the window sums themselves (the 16-bit keys' sums are 8 x, plus d % 8)
+                if (d8 + 2 * j < dmax) cp[d8 + 2 * j] = (uint16_t)((s4[j] & 0xFFFFu) / kTS);
+                if (d8 + 2 * j + 1 < dmax) cp[d8 + 2 * j + 1] = (uint16_t)((s4[j] >> 16) / kTS);
               }
             }
           }
@@ -675,8 +677,13 @@ __device__ __forceinline__ void cost_tc_body(const TcArgs &a, uint8_t *smem) {
 template <int WIN>
 __global__ void __launch_bounds__(kThreads, 1) cost_tc_kernel(const __grid_constant__ TcArgs a) {
   extern __shared__ __align__(1024) uint8_t smem[];
-  if (blockIdx.z == 0) cost_tc_body<WIN, 0>(a, smem);
-  else cost_tc_body<WIN, 1>(a, smem);
+  if (a.cost[0] != nullptr || a.cost[1] != nullptr) {
+    if (blockIdx.z == 0) cost_tc_body<WIN, 0, true>(a, smem);
+    else cost_tc_body<WIN, 1, true>(a, smem);
+  } else {
+    if (blockIdx.z == 0) cost_tc_body<WIN, 0, false>(a, smem);
+    else cost_tc_body<WIN, 1, false>(a, smem);
+  }
 }
 
 template <int WIN>
