@@ -26,7 +26,7 @@ cudaError_t launch_refine_batch(const bsm_ctx *ctx, BatchHeader *hdr, const Batc
 namespace {
 
 constexpr int kDescTY = 4;           // rows per describe tile (describe kernel's CTA)
-constexpr int kRefTX = 32, kRefTY = 8;
+constexpr int kRefTX = kRefineTX, kRefTY = kRefineTY;
 constexpr size_t kTableBytes = sizeof(BatchHeader) + sizeof(BatchPair) * kMaxBatch;
 
 bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }

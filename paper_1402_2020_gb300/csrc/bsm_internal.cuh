@@ -32,6 +32,7 @@ struct PairTable {
 // ---------------------------------------------------------------- batched execution
 
 constexpr int kMaxBatch = 1024;   // pairs per bsm_batch_run call
+constexpr int kRefineTX = 32, kRefineTY = 32;  // output block of one refinement CTA (per pair and batched)
 constexpr int kBatchDisp = 64;    // disparities per CTA of the batched cost kernel (8 warps)
 
 // One pair of a batch, as the batched kernels see it (built on the host, copied to the device).

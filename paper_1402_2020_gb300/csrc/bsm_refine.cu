@@ -20,8 +20,13 @@
 namespace bsm {
 namespace {
 
-constexpr int kTX = 32, kTY = 8;
-constexpr int kWarps = kTX * kTY / 32;
+// A CTA of kWarps warps refines a kTX x kTY block. Its staged tile adds the window's R-pixel halo on
+// every side, so the block is square-ish: at R = 15 a 32 x 32 block stages 3.75 entries per output pixel
+// (a 32 x 8 block staged 9.2, and the staging, with its dependent colour-table and left/right-check
+// loads, was three quarters of the kernel's time).
+constexpr int kTX = kRefineTX, kTY = kRefineTY;
+constexpr int kWarps = 8;
+constexpr int kThreadsR = 32 * kWarps;
 constexpr uint32_t kDispMask = 1023u;
 
 struct RefineArgs {
@@ -77,6 +82,10 @@ __device__ __forceinline__ void refine_tile(const RefineArgs &a, int x0, int y0,
   int16_t *sd = reinterpret_cast<int16_t *>(shist + kWarps * a.hist_stride);  // th * tp
   int *s_count = reinterpret_cast<int *>(sd + ((th * tp + 1) & ~1));
   int16_t *s_list = reinterpret_cast<int16_t *>(s_count + 1);           // kTX * kTY
+  // RT > 0: per tile row, the validity of its tp <= 64 columns as two bit words; per warp, the list of
+  // an invalid pixel's voters (window row << 5 | window column)
+  uint32_t *vbits = reinterpret_cast<uint32_t *>(s_list + kTX * kTY);  // 2 th
+  uint16_t *vlist = reinterpret_cast<uint16_t *>(vbits + 2 * th);      // kWarps * 32 * (2 RT + 1)
 
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   if (threadIdx.x == 0) *s_count = 0;
@@ -123,23 +132,32 @@ __device__ __forceinline__ void refine_tile(const RefineArgs &a, int x0, int y0,
     }
   }
   __syncthreads();
+  if constexpr (RT > 0) {  // the validity bitmaps of the tile rows (read after the next barrier)
+    static_assert(kTX + 2 * RT <= 64, "a tile row in two bit words");
+    for (int r = warp; r < th; r += kWarps) {
+      const uint32_t b0 = __ballot_sync(0xFFFFFFFFu, lane < tp && sd[r * tp + lane] >= 0);
+      const uint32_t b1 = __ballot_sync(0xFFFFFFFFu, 32 + lane < tp && sd[r * tp + 32 + lane] >= 0);
+      if (lane == 0) {
+        vbits[2 * r] = b0;
+        vbits[2 * r + 1] = b1;
+      }
+    }
+  }
 
-  {
-    const int tx = threadIdx.x & (kTX - 1), ty = threadIdx.x / kTX;
+  for (int p = threadIdx.x; p < kTX * kTY; p += blockDim.x) {
+    const int tx = p & (kTX - 1), ty = p / kTX;
     const int x = x0 + tx, y = y0 + ty;
     if (x < a.w && y < a.h) {
       const size_t i = (size_t)y * a.w + x;
       const int dv = sd[(ty + R) * tp + tx + R];
       if (dv >= 0) a.out[i] = dv;
-      else s_list[atomicAdd(s_count, 1)] = (int16_t)threadIdx.x;
+      else s_list[atomicAdd(s_count, 1)] = (int16_t)p;
     }
   }
   __syncthreads();
 
   const int count = *s_count;
   uint32_t *hist = shist + warp * a.hist_stride;
-  // Es of window column `lane`: row wy at the constant offset (wy - RT)^2
-  const uint32_t *es = sEs + (RT > 0 && lane < 2 * RT + 1 ? (lane - RT) * (lane - RT) : 0);
   for (int it = warp; it < count; it += kWarps) {
     const int t = s_list[it];
     const int tx = t & (kTX - 1), ty = t / kTX;
@@ -148,26 +166,45 @@ __device__ __forceinline__ void refine_tile(const RefineArgs &a, int x0, int y0,
     __syncwarp();
     const uint32_t labx = slab[(ty + R) * tp + tx + R];
     if constexpr (RT > 0) {
-      if (lane < 2 * RT + 1) {
-        const int16_t *dcol = sd + ty * tp + tx + lane;
-        const uint32_t *lcol = slab + ty * tp + tx + lane;
-        int run_d = -1;
-        uint32_t run = 0;
-#pragma unroll
-        for (int wy = 0; wy < 2 * RT + 1; ++wy) {
-          const int dv = dcol[wy * tp];
-          if (dv >= 0) {
-            const uint32_t v = (sEc[lab_sad(labx, lcol[wy * tp])] * es[(wy - RT) * (wy - RT)]) >> kVoteShift;
-            if (dv != run_d) {
-              if (run) atomicAdd(&hist[run_d], run);
-              run_d = dv;
-              run = 0;
-            }
-            run += v;
-          }
-        }
-        if (run) atomicAdd(&hist[run_d], run);
+      // Only valid neighbours vote, and around an invalid pixel most are invalid (they cluster): lane wy
+      // takes window row wy's validity bits from the row bitmap, a warp prefix sum of their counts lays
+      // the voters out as one list, and each lane then walks a contiguous stretch of it, so neighbouring
+      // voters (mostly the same disparity) share one histogram add.
+      constexpr int W = 2 * RT + 1;
+      uint16_t *wl = vlist + warp * (32 * W);
+      uint32_t m = 0;
+      if (lane < W) {
+        const int r = ty + lane;  // tile row of window row `lane`; window columns are tile columns tx .. tx + 2 RT
+        const uint64_t bits = ((uint64_t)vbits[2 * r + 1] << 32) | vbits[2 * r];
+        m = (uint32_t)(bits >> tx) & ((1u << W) - 1u);
       }
+      const int cnt = __popc(m);
+      int incl = cnt;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int n = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+        if (lane >= o) incl += n;
+      }
+      const int total = __shfl_sync(0xFFFFFFFFu, incl, 31);
+      for (int p = incl - cnt; m; m &= m - 1u, ++p) wl[p] = (uint16_t)((lane << 5) | (__ffs(m) - 1));
+      __syncwarp();
+      const int per = (total + 31) >> 5;
+      const int s0 = min(total, lane * per), s1 = min(total, s0 + per);
+      int run_d = -1;
+      uint32_t run = 0;
+      for (int q = s0; q < s1; ++q) {
+        const int pos = wl[q], wy = pos >> 5, wx = pos & 31;
+        const int toff = (ty + wy) * tp + tx + wx;
+        const int dv = sd[toff];
+        const uint32_t v = (sEc[lab_sad(labx, slab[toff])] * sEs[(wx - RT) * (wx - RT) + (wy - RT) * (wy - RT)]) >> kVoteShift;
+        if (dv != run_d) {
+          if (run) atomicAdd(&hist[run_d], run);
+          run_d = dv;
+          run = 0;
+        }
+        run += v;
+      }
+      if (run) atomicAdd(&hist[run_d], run);
     }
     for (int wx = lane; RT == 0 && wx < side; wx += 32) {
       const int dx2 = (wx - R) * (wx - R);
@@ -245,12 +282,14 @@ __device__ __forceinline__ void refine_tile(const RefineArgs &a, int x0, int y0,
   }
 
   if (a.finalize) {
-    const int tx = threadIdx.x & (kTX - 1), ty = threadIdx.x / kTX;
-    const int x = x0 + tx, y = y0 + ty;
-    if (x < a.w && y < a.h) {
-      const size_t i = (size_t)y * a.w + x;
-      a.dL[i] = disp_at(a.dL, i);
-      a.dR[i] = disp_at(a.dR, i);
+    for (int p = threadIdx.x; p < kTX * kTY; p += blockDim.x) {
+      const int tx = p & (kTX - 1), ty = p / kTX;
+      const int x = x0 + tx, y = y0 + ty;
+      if (x < a.w && y < a.h) {
+        const size_t i = (size_t)y * a.w + x;
+        a.dL[i] = disp_at(a.dL, i);
+        a.dR[i] = disp_at(a.dR, i);
+      }
     }
   }
 }
@@ -258,7 +297,7 @@ __device__ __forceinline__ void refine_tile(const RefineArgs &a, int x0, int y0,
 size_t tile_bytes(int R, int hist_stride) {
   const int tp = kTX + 2 * R, th = kTY + 2 * R;
   return (size_t)th * tp * 4 + (size_t)kWarps * hist_stride * 4 + (size_t)((th * tp + 1) & ~1) * 2 + 4 +
-         (size_t)kTX * kTY * 2;
+         (size_t)kTX * kTY * 2 + (size_t)2 * th * 4 + (size_t)kWarps * 32 * (2 * R + 1) * 2;
 }
 
 // Nearest valid disparities on each row (for the refinement's no-vote case): one warp per row walks it in
@@ -320,7 +359,7 @@ __global__ void __launch_bounds__(256) near_valid_kernel(const RefineArgs a, uin
 constexpr int kRFast = 15;  // the radius with an unrolled window walk (the paper's setting)
 
 template <int RT>
-__global__ void __launch_bounds__(kTX *kTY) refine_kernel(const RefineArgs a, const uint32_t *Ec, const uint32_t *Es) {
+__global__ void __launch_bounds__(kThreadsR) refine_kernel(const RefineArgs a, const uint32_t *Ec, const uint32_t *Es) {
   extern __shared__ __align__(16) uint32_t smem[];
   load_vote_tables(Ec, Es, a.R, smem);
   refine_tile<RT>(a, blockIdx.x * kTX, blockIdx.y * kTY, smem, smem + table_words(a.R));
@@ -328,7 +367,7 @@ __global__ void __launch_bounds__(kTX *kTY) refine_kernel(const RefineArgs a, co
 
 // Batched refinement: persistent CTAs take (pair, block) tickets.
 template <int RT>
-__global__ void __launch_bounds__(kTX *kTY) refine_batch_kernel(BatchHeader *hdr, const BatchPair *pairs,
+__global__ void __launch_bounds__(kThreadsR) refine_batch_kernel(BatchHeader *hdr, const BatchPair *pairs,
                                                                const uint32_t *Ec, const uint32_t *Es,
                                                                const uint32_t *table, int tol, int R,
                                                                int hist_stride) {
@@ -373,7 +412,7 @@ cudaError_t launch_refine(const bsm_ctx *ctx, const uint8_t *rgb, int pitch, con
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   dim3 grid((w + kTX - 1) / kTX, (h + kTY - 1) / kTY);
-  kern<<<grid, kTX * kTY, smem, s>>>(a, ctx->vote_ec, ctx->vote_es);
+  kern<<<grid, kThreadsR, smem, s>>>(a, ctx->vote_ec, ctx->vote_es);
   return cudaGetLastError();
 }
 
@@ -384,7 +423,7 @@ cudaError_t prepare_refine_batch(const bsm_ctx *ctx, int *grid) {
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kTX * kTY, smem);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreadsR, smem);
   *grid = max(1, per_sm) * ctx->sms;
   return e;
 }
@@ -394,7 +433,7 @@ cudaError_t launch_refine_batch(const bsm_ctx *ctx, BatchHeader *hdr, const Batc
   const int R = ctx->p.vote_radius, hs = ctx->p.dmax;
   const size_t smem = table_words(R) * 4 + tile_bytes(R, hs);
   auto kern = R == kRFast ? refine_batch_kernel<kRFast> : refine_batch_kernel<0>;
-  kern<<<grid, kTX * kTY, smem, s>>>(hdr, pairs, ctx->vote_ec, ctx->vote_es, ctx->color_table, ctx->p.lr_tol, R, hs);
+  kern<<<grid, kThreadsR, smem, s>>>(hdr, pairs, ctx->vote_ec, ctx->vote_es, ctx->color_table, ctx->p.lr_tol, R, hs);
   return cudaGetLastError();
 }
 
