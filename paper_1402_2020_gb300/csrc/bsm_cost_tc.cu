@@ -674,26 +674,28 @@ __device__ __forceinline__ void cost_tc_body(const TcArgs &a, uint8_t *smem) {
   if (warp == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols));
 }
 
-template <int WIN>
+// WC: the launch writes cost volumes (a separate instance, so that the disparity-only kernel does not
+// carry the volume path's registers).
+template <int WIN, bool WC>
 __global__ void __launch_bounds__(kThreads, 1) cost_tc_kernel(const __grid_constant__ TcArgs a) {
   extern __shared__ __align__(1024) uint8_t smem[];
-  if (a.cost[0] != nullptr || a.cost[1] != nullptr) {
-    if (blockIdx.z == 0) cost_tc_body<WIN, 0, true>(a, smem);
-    else cost_tc_body<WIN, 1, true>(a, smem);
-  } else {
-    if (blockIdx.z == 0) cost_tc_body<WIN, 0, false>(a, smem);
-    else cost_tc_body<WIN, 1, false>(a, smem);
-  }
+  if (blockIdx.z == 0) cost_tc_body<WIN, 0, WC>(a, smem);
+  else cost_tc_body<WIN, 1, WC>(a, smem);
+}
+
+template <int WIN, bool WC>
+cudaError_t launch_tc_wc(const TcArgs &a, cudaStream_t s) {
+  constexpr int OUTC = kTM - 2 * (WIN / 2);
+  cudaError_t e = cudaFuncSetAttribute(cost_tc_kernel<WIN, WC>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
+  if (e != cudaSuccess) return e;
+  dim3 grid((a.w + OUTC - 1) / OUTC, (a.h + a.rows - 1) / a.rows, 2);
+  cost_tc_kernel<WIN, WC><<<grid, kThreads, kSmem, s>>>(a);
+  return cudaGetLastError();
 }
 
 template <int WIN>
 cudaError_t launch_tc_t(const TcArgs &a, cudaStream_t s) {
-  constexpr int OUTC = kTM - 2 * (WIN / 2);
-  cudaError_t e = cudaFuncSetAttribute(cost_tc_kernel<WIN>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
-  if (e != cudaSuccess) return e;
-  dim3 grid((a.w + OUTC - 1) / OUTC, (a.h + a.rows - 1) / a.rows, 2);
-  cost_tc_kernel<WIN><<<grid, kThreads, kSmem, s>>>(a);
-  return cudaGetLastError();
+  return (a.cost[0] != nullptr || a.cost[1] != nullptr) ? launch_tc_wc<WIN, true>(a, s) : launch_tc_wc<WIN, false>(a, s);
 }
 
 // Row bands: one CTA per SM (all of TMEM), so the launch takes ceil(CTAs / SMs) waves of about
