@@ -645,10 +645,17 @@ def tensor_roofline(units, n_bits, seconds, traffic):
     bf16 = measured_peaks().get("bf16_tflops")
     peak, basis = (2 * bf16, "measured bf16 x 2 (nominal fp8/bf16)") if bf16 else (3800.0, "fallback 1.9 PF bf16 x 2")
     achieved = flops / seconds / 1e12
-    return {"bound": "tensor", "kernel": "cost_tc_kernel", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+    line = {"bound": "tensor", "kernel": "cost_tc_kernel", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
             "frac": achieved / peak, "traffic": traffic, "work_per_launch": flops, "peak_basis": basis,
             "note": "one launch covers both reference views; the MMAs also run the window's entering and leaving "
                     "rows and the band around the disparity range"}
+    from paper_1402_2020_gb300 import peaks
+
+    f8 = peaks.load_fp8()
+    if f8:  # the vendor library's dense E4M3 GEMM rate on this GPU, measured (beside the rule's bf16 x 2)
+        line["peak_e4m3_gemm_measured"] = {"peak": f8["burst_tflops"], "frac": achieved / f8["burst_tflops"],
+                                           "basis": "cuBLASLt E4M3 GEMM burst, " + os.path.relpath(peaks.FP8_SUMMARY, ROOT)}
+    return line
 
 
 def run_pair(args, cfg, world, rank, local, n_bits=N_BITS, window_S=WINDOW_S, sigma=None, agg=AGG, e2e=True,

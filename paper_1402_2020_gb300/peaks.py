@@ -95,12 +95,91 @@ def load(path: str = SUMMARY) -> dict | None:
     return out if all(n in out for n in OPS) else None
 
 
+FP8_SUMMARY = os.path.join(os.path.dirname(HERE), "profiles", "fp8_gemm_gb300.md")
+
+
+def measure_fp8_gemm(n: int = 8192, reps: int = 20) -> dict:
+    """Dense E4M3 x E4M3 -> bf16 GEMM rate of the vendor library (cuBLASLt through torch._scaled_mm), n^3,
+    best of `reps` single launches and the mean of `reps` back-to-back launches, in TFLOP/s."""
+    import torch
+
+    g = torch.Generator(device="cuda").manual_seed(7)
+    a = (torch.rand((n, n), device="cuda", generator=g) - 0.5).to(torch.float8_e4m3fn)
+    b = (torch.rand((n, n), device="cuda", generator=g) - 0.5).to(torch.float8_e4m3fn).t()  # column-major operand
+    one = torch.ones((), device="cuda", dtype=torch.float32)
+
+    def run():
+        return torch._scaled_mm(a, b, scale_a=one, scale_b=one, out_dtype=torch.bfloat16)
+
+    for _ in range(3):
+        run()
+    torch.cuda.synchronize()
+    best = float("inf")
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        run()
+        e1.record()
+        e1.synchronize()
+        best = min(best, e0.elapsed_time(e1) * 1e-3)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        run()
+    e1.record()
+    e1.synchronize()
+    mean = e0.elapsed_time(e1) * 1e-3 / reps
+    flops = 2.0 * n ** 3
+    return {"n": n, "burst_tflops": flops / best / 1e12, "loop_tflops": flops / mean / 1e12}
+
+
+def write_fp8_summary(r: dict, path: str = FP8_SUMMARY, gpu: str = "") -> None:
+    lines = [
+        "# Dense E4M3 GEMM rate on the GB300 (the tensor-core cost kernel's roofline denominator)",
+        "",
+        "Measured by `paper_1402_2020_gb300/peaks.py` (`measure_fp8_gemm`): torch._scaled_mm (cuBLASLt), E4M3 x E4M3 -> bf16,",
+        f"unit scales, {r['n']}^3 (2 n^3 flops), CUDA events; best single launch (burst) and the mean of back-to-back launches.",
+        "",
+        "Command: `python -m paper_1402_2020_gb300.peaks --fp8 --write-fp8 profiles/fp8_gemm_gb300.md`",
+        f"GPU: {gpu or 'NVIDIA GB300'}",
+        "",
+        "| quantity | TFLOP/s |",
+        "|---|---|",
+        f"| burst | {r['burst_tflops']:.1f} |",
+        f"| back to back | {r['loop_tflops']:.1f} |",
+        "",
+        f"fp8_gemm_tflops: burst {r['burst_tflops']:.1f} loop {r['loop_tflops']:.1f}",
+        "",
+    ]
+    with open(path, "w") as f:
+        f.write("\n".join(lines))
+
+
+def load_fp8(path: str = FP8_SUMMARY) -> dict | None:
+    try:
+        text = open(path).read()
+    except OSError:
+        return None
+    m = re.search(r"fp8_gemm_tflops:\s*burst\s+([0-9.]+)\s+loop\s+([0-9.]+)", text)
+    return {"burst_tflops": float(m.group(1)), "loop_tflops": float(m.group(2))} if m else None
+
+
 def rounded(rates: dict, name: str) -> float:
     """The issue rate as a whole number of lanes per clock (measurement noise removed)."""
     return float(round(rates[name]))
 
 
 if __name__ == "__main__":
+    if "--fp8" in sys.argv:
+        r = measure_fp8_gemm()
+        print(f"fp8 GEMM: burst {r['burst_tflops']:.1f} TFLOP/s, back to back {r['loop_tflops']:.1f} TFLOP/s")
+        if "--write-fp8" in sys.argv:
+            import torch
+
+            i = sys.argv.index("--write-fp8")
+            write_fp8_summary(r, sys.argv[i + 1] if i + 1 < len(sys.argv) else FP8_SUMMARY,
+                              gpu=torch.cuda.get_device_name())
+        sys.exit(0)
     rates = measure()
     gpu = ""
     try:
