@@ -291,7 +291,8 @@ bsm_status bsm_describe_noalloc(bsm_ctx *ctx, const uint8_t *rgb_dev, int32_t w,
  *   the row, the one that exists, else 0.
  *   rgbL_dev  device left RGB image (h rows of pitch_bytes); out  device int32 [h][w]
  * Every dL value must lie in [0, dmax-1]. Uses the context's scratch (a w * h plane; it holds each
- * row's nearest valid disparities), grown here if too small.
+ * pixel's CIELAB colour, check result and disparity or row fallback as one word), grown here if too
+ * small.
  */
 bsm_status bsm_refine(bsm_ctx *ctx, const uint8_t *rgbL_dev, int32_t pitch_bytes, const int32_t *dispL,
                       const int32_t *dispR, int32_t w, int32_t h, int32_t dmax, int32_t *out, void *stream);
@@ -366,7 +367,11 @@ typedef struct {
   int32_t describe_variant; /* 0: automatic (warp per pixel from n_bits 256 on, thread per pixel below);
                                1: thread per pixel (n_bits <= 256); 2: warp per pixel (n_bits / 32 even;
                                always for n_bits > 256). Results identical. */
-  int32_t reserved[3];     /* must be zero */
+  int32_t describe_copies; /* copies of the colour-plane tile the warp-per-pixel describe kernel keeps in
+                              shared memory, 0 (one) or 1..4: with more, each sample is read from the copy
+                              that keeps its load's 32 addresses in distinct banks (bsm_describe_gather_plan);
+                              fewer bank conflicts, more staging and shared memory. Results identical. */
+  int32_t reserved[2];     /* must be zero */
 } bsm_tuning;
 
 /* Set / read the context's launch shapes. Synchronous, host only. */
@@ -385,6 +390,21 @@ typedef struct {
   int32_t reserved;
 } bsm_cost_plan_info;
 bsm_status bsm_cost_plan(bsm_ctx *ctx, int32_t w, int32_t h, int32_t dmax, bsm_cost_plan_info *out);
+
+/* The shared-memory gather plan of the warp-per-pixel describe kernel for a pair table (Eq. 2-3 and 5 read
+   the two samples of every sampling pair around the pixel; bit l of descriptor word j is pair 32 j + l's,
+   so lane l of a warp reads pair 32 j + l's samples, one load per word and sample). The kernel keeps
+   `copies` copies of its colour-plane tile (row pitch *pitch words) at bases in different banks and reads
+   each sample from the copy the plan assigns, so that a load's 32 addresses share as few banks as
+   possible. Host only, no GPU work; bsm_create plans the context's table with 4 copies (fewer for a large
+   pair window). pairs: n_bits x (px, py, qx, qy) as in bsm_params; n_bits a multiple of 32 up to 256;
+   copies 1..4. Outputs (caller-owned, any may be NULL): *pitch; *copies_used (copies, or fewer when the
+   tile copies would exceed 64 KB); copy_base[copies_used] (word offsets of the copies, copy 0 at 0);
+   offsets[n_bits][2] (each sample's word offset from the pixel in copy 0: its copy's base +
+   dy * pitch + dx); wavefronts[2 n_bits / 32] (the bank-conflict degree of load 2 j + s, 1 = none).
+   BSM_ERR_INVALID_ARG on a NULL pair table, a bad n_bits or copies, or an offset beyond 31. */
+bsm_status bsm_describe_gather_plan(const int8_t *pairs, int32_t n_bits, int32_t copies, int32_t *pitch,
+                                    int32_t *copies_used, int32_t *copy_base, int32_t *offsets, int32_t *wavefronts);
 
 /* Validate parameters without touching the GPU: the checks bsm_create performs first. */
 bsm_status bsm_validate_params(const bsm_params *params);

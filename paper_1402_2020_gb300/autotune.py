@@ -70,7 +70,7 @@ def choose(candidates, measure):
 def _time_cost(ctx, planes, w, h, dmax, rows, popc, variant, dv, reps, torch):
     dL = torch.empty((h, w), dtype=torch.int32, device="cuda")
     dR = torch.empty_like(dL)
-    bsm.bsm_set_tuning(ctx, rows, popc, 0, variant, dv)
+    bsm.bsm_set_tuning(ctx, rows, popc, 0, variant, *dv)
     s = torch.cuda.current_stream()
     for _ in range(2):
         bsm.bsm_cost_aggregate_wta(ctx, *planes, w, h, dmax, dL, dR)
@@ -85,10 +85,11 @@ def _time_cost(ctx, planes, w, h, dmax, rows, popc, variant, dv, reps, torch):
 
 def tune_cost(ctx, n_bits: int, win: int, w: int, h: int, dmax: int, reps: int = 3, use_cache: bool = True) -> dict:
     """Best (cost_rows, cost_popc_plain, cost_variant) for this workload shape; applied to ctx and cached.
-    The context's describe variant is kept."""
+    The context's describe variant and tile copies are kept."""
     import torch
 
-    dv = bsm.bsm_get_tuning(ctx)["describe_variant"]
+    cur0 = bsm.bsm_get_tuning(ctx)
+    dv = (cur0["describe_variant"], cur0["describe_copies"])
     gpu = torch.cuda.get_device_name()
     k = key(gpu, n_bits, win, w, h, dmax)
     cache = load() if use_cache else {}
@@ -101,7 +102,7 @@ def tune_cost(ctx, n_bits: int, win: int, w: int, h: int, dmax: int, reps: int =
         variants = VARIANTS if nw == 8 else ((1, 2) if nw == 4 else (1,))
         if 3 in variants:  # the tensor-core kernel is refused for the both-masks ablation
             try:
-                bsm.bsm_set_tuning(ctx, 0, 0, 0, 3, dv)
+                bsm.bsm_set_tuning(ctx, 0, 0, 0, 3, *dv)
             except bsm.BsmError:
                 variants = tuple(v for v in variants if v != 3)
         cands = [(r, p, v) for v in variants if v != 3 for r in COST_ROWS if r <= max(16, 2 * h) for p in forms
@@ -116,7 +117,7 @@ def tune_cost(ctx, n_bits: int, win: int, w: int, h: int, dmax: int, reps: int =
             store(merged)
     t = cache[k]
     cur = bsm.bsm_get_tuning(ctx)
-    bsm.bsm_set_tuning(ctx, t["cost_rows"], t["cost_popc_plain"], cur["batch_rows"], t.get("cost_variant", 0), dv)
+    bsm.bsm_set_tuning(ctx, t["cost_rows"], t["cost_popc_plain"], cur["batch_rows"], t.get("cost_variant", 0), *dv)
     return t
 
 
@@ -133,7 +134,7 @@ def tune_batch(ctx, descs, n_bits: int, win: int, reps: int = 2, use_cache: bool
 
         def measure(rows):
             bsm.bsm_set_tuning(ctx, cur["cost_rows"], cur["cost_popc_plain"], rows, cur["cost_variant"],
-                               cur["describe_variant"])
+                               cur["describe_variant"], cur["describe_copies"])
             s = torch.cuda.current_stream()
             bsm.bsm_batch_run(ctx, descs)
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -153,5 +154,5 @@ def tune_batch(ctx, descs, n_bits: int, win: int, reps: int = 2, use_cache: bool
     t = cache[k]
     cur = bsm.bsm_get_tuning(ctx)
     bsm.bsm_set_tuning(ctx, cur["cost_rows"], cur["cost_popc_plain"], t["batch_rows"], cur["cost_variant"],
-                       cur["describe_variant"])
+                       cur["describe_variant"], cur["describe_copies"])
     return t

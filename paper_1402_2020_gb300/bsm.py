@@ -29,7 +29,7 @@ EXPORTED = (
     "bsm_abi_version", "bsm_set_tuning", "bsm_get_tuning", "bsm_reserve", "bsm_describe_noalloc",
     "bsm_batch_run", "bsm_reserve_batch", "bsm_last_cuda_error", "bsm_server_create", "bsm_server_submit",
     "bsm_server_poll", "bsm_server_drain", "bsm_server_get_stats", "bsm_server_destroy", "bsm_debug_set",
-    "bsm_cost_volumes", "bsm_sgm", "bsm_cost_plan",
+    "bsm_cost_volumes", "bsm_sgm", "bsm_cost_plan", "bsm_describe_gather_plan",
 )
 BSM_DEBUG_WITHHOLD_ARRIVALS = 1
 BSM_MAX_BATCH = 1024
@@ -65,7 +65,7 @@ BSM_MASK_REFERENCE, BSM_MASK_NONE, BSM_MASK_BOTH = 0, 1, 2
 class bsm_tuning(ctypes.Structure):
     _fields_ = [("cost_rows", ctypes.c_int32), ("cost_popc_plain", ctypes.c_int32), ("batch_rows", ctypes.c_int32),
                 ("cost_variant", ctypes.c_int32), ("describe_variant", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 3)]
+                ("describe_copies", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2)]
 
 
 class bsm_cost_plan_info(ctypes.Structure):
@@ -163,6 +163,9 @@ def lib():
         L.bsm_debug_set.restype = S
         L.bsm_cost_plan.argtypes = [P, I, I, I, ctypes.POINTER(bsm_cost_plan_info)]
         L.bsm_cost_plan.restype = S
+        IP = ctypes.POINTER(ctypes.c_int32)
+        L.bsm_describe_gather_plan.argtypes = [ctypes.c_void_p, I, I, IP, IP, IP, IP, IP]
+        L.bsm_describe_gather_plan.restype = S
         L.bsm_last_cuda_error.argtypes = [P]
         L.bsm_last_cuda_error.restype = ctypes.c_char_p
         L.bsm_batch_run.argtypes = [P, ctypes.POINTER(bsm_pair_desc), I, P]
@@ -317,13 +320,14 @@ def bsm_reserve(ctx: int, max_w: int, max_h: int) -> None:
 
 
 def bsm_set_tuning(ctx: int, cost_rows: int = 0, cost_popc_plain: int = 0, batch_rows: int = 0,
-                   cost_variant: int = 0, describe_variant: int = 0) -> None:
+                   cost_variant: int = 0, describe_variant: int = 0, describe_copies: int = 0) -> None:
     t = bsm_tuning()
     t.cost_rows = cost_rows
     t.cost_popc_plain = cost_popc_plain
     t.batch_rows = batch_rows
     t.cost_variant = cost_variant
     t.describe_variant = describe_variant
+    t.describe_copies = describe_copies
     _check(lib().bsm_set_tuning(ctx, ctypes.byref(t)), "bsm_set_tuning")
 
 
@@ -337,11 +341,29 @@ def bsm_cost_plan(ctx: int, w: int, h: int, dmax: int) -> dict:
             "launches": p.launches}
 
 
+def bsm_describe_gather_plan(pairs: np.ndarray, copies: int = 4) -> dict:
+    """The warp-per-pixel describe kernel's gather plan for a pair table (host only): tile pitch, copies
+    used, copy bases, each sample's word offset from the pixel (n_bits x 2) and each load's wavefronts."""
+    pr = np.ascontiguousarray(pairs, dtype=np.int8)
+    n = int(pr.shape[0])
+    nl = max(1, 2 * (n // 32))
+    pitch, used = ctypes.c_int32(), ctypes.c_int32()
+    base = np.zeros(4, np.int32)
+    offs = np.zeros((max(n, 1), 2), np.int32)
+    wf = np.zeros(nl, np.int32)
+    ip = lambda a: a.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))  # noqa: E731
+    _check(lib().bsm_describe_gather_plan(pr.ctypes.data, n, copies, ctypes.byref(pitch), ctypes.byref(used),
+                                          ip(base), ip(offs), ip(wf)), "bsm_describe_gather_plan")
+    return {"pitch": pitch.value, "copies": used.value, "copy_base": base[: used.value].copy(), "offsets": offs[:n],
+            "wavefronts": wf}
+
+
 def bsm_get_tuning(ctx: int) -> dict:
     t = bsm_tuning()
     _check(lib().bsm_get_tuning(ctx, ctypes.byref(t)), "bsm_get_tuning")
     return {"cost_rows": t.cost_rows, "cost_popc_plain": t.cost_popc_plain, "batch_rows": t.batch_rows,
-            "cost_variant": t.cost_variant, "describe_variant": t.describe_variant}
+            "cost_variant": t.cost_variant, "describe_variant": t.describe_variant,
+            "describe_copies": t.describe_copies}
 
 
 def pair_desc(rgbL, rgbR, w, h, pitch, dmax, BL, PhiL, BR, PhiR, dispL, dispR, out) -> bsm_pair_desc:

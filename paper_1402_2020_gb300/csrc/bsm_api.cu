@@ -148,6 +148,7 @@ bsm_status bsm_create(const bsm_params *p, bsm_ctx **out) {
   int halo = 0;
   for (int i = 0; i < 4 * p->n_bits; ++i) halo = std::max(halo, std::abs((int)p->pairs[i]));
   ctx->halo = halo;
+  ctx->warp_pt = bsm::warp_pair_table(ctx);
 
   cudaError_t e = cudaGetDevice(&ctx->device);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->sms, cudaDevAttrMultiProcessorCount, ctx->device);
@@ -266,7 +267,7 @@ bsm_status bsm_refine(bsm_ctx *ctx, const uint8_t *rgbL_dev, int32_t pitch_bytes
   if (ctx == nullptr || rgbL_dev == nullptr || dispL == nullptr || dispR == nullptr || out == nullptr)
     return BSM_ERR_INVALID_ARG;
   if (!size_ok(w, h) || pitch_bytes < 3 * w || dmax < 1 || dmax > ctx->p.dmax) return BSM_ERR_INVALID_ARG;
-  // the context's colour-plane scratch holds the rows' nearest valid disparities meanwhile
+  // the context's colour-plane scratch holds the refinement words of the left view meanwhile
   const cudaError_t e = ensure_plane(ctx, (size_t)w * h);
   if (e != cudaSuccess) return from_cuda(ctx, e);
   return from_cuda(ctx, bsm::launch_refine(ctx, rgbL_dev, pitch_bytes, dispL, dispR, w, h, dmax, out, ctx->plane,
@@ -333,8 +334,9 @@ bsm_status bsm_reserve(bsm_ctx *ctx, int32_t max_w, int32_t max_h) {
 
 bsm_status bsm_set_tuning(bsm_ctx *ctx, const bsm_tuning *t) {
   if (ctx == nullptr || t == nullptr) return BSM_ERR_INVALID_ARG;
-  for (int i = 0; i < 3; ++i)
+  for (int i = 0; i < 2; ++i)
     if (t->reserved[i] != 0) return BSM_ERR_INVALID_ARG;
+  if (t->describe_copies < 0 || t->describe_copies > bsm::kMaxTileCopies) return BSM_ERR_INVALID_ARG;
   if (t->describe_variant < 0 || t->describe_variant > 2) return BSM_ERR_INVALID_ARG;
   if (t->describe_variant == 1 && ctx->nw > 8) return BSM_ERR_UNSUPPORTED;
   if (t->describe_variant == 2 && ctx->nw % 2 != 0) return BSM_ERR_UNSUPPORTED;
@@ -350,6 +352,10 @@ bsm_status bsm_set_tuning(bsm_ctx *ctx, const bsm_tuning *t) {
   ctx->batch_rows = t->batch_rows;
   ctx->cost_variant = t->cost_variant;
   ctx->describe_variant = t->describe_variant;
+  if (t->describe_copies != ctx->describe_copies) {
+    ctx->describe_copies = t->describe_copies;
+    ctx->warp_pt = bsm::warp_pair_table(ctx);
+  }
   return BSM_OK;
 }
 
@@ -361,6 +367,26 @@ bsm_status bsm_get_tuning(bsm_ctx *ctx, bsm_tuning *t) {
   t->batch_rows = ctx->batch_rows;
   t->cost_variant = ctx->cost_variant;
   t->describe_variant = ctx->describe_variant;
+  t->describe_copies = ctx->describe_copies;
+  return BSM_OK;
+}
+
+bsm_status bsm_describe_gather_plan(const int8_t *pairs, int32_t n_bits, int32_t copies, int32_t *pitch,
+                                    int32_t *copies_used, int32_t *copy_base, int32_t *offsets, int32_t *wavefronts) {
+  if (pairs == nullptr || n_bits < 32 || n_bits % 32 != 0 || n_bits > bsm::kMaxShortBits || copies < 1 ||
+      copies > bsm::kMaxTileCopies)
+    return BSM_ERR_INVALID_ARG;
+  bsm::PairTable pt{};
+  int tp = 0;
+  const int used = bsm::plan_tile_gathers(pairs, n_bits, copies, &pt, &tp, wavefronts);
+  if (used == 0) return BSM_ERR_INVALID_ARG;
+  if (pitch != nullptr) *pitch = tp;
+  if (copies_used != nullptr) *copies_used = used;
+  for (int c = 0; copy_base != nullptr && c < used; ++c) copy_base[c] = pt.copy_base[c];
+  for (int i = 0; offsets != nullptr && i < n_bits; ++i) {
+    offsets[2 * i] = pt.off[i][0];
+    offsets[2 * i + 1] = pt.off[i][1];
+  }
   return BSM_OK;
 }
 

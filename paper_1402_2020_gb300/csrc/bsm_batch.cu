@@ -58,8 +58,11 @@ cudaError_t ensure_batch_buffers(bsm_ctx *ctx, size_t plane_words) {
   return e;
 }
 
-// The kernel choices baked into the captured graph: a change of either means a new capture.
-int graph_variant(const bsm_ctx *ctx) { return ctx->cost_plain_popc + 16 * ctx->describe_variant; }
+// The kernel choices and the describe tile copies baked into the captured graph: a change of any of them
+// means a new capture.
+int graph_variant(const bsm_ctx *ctx) {
+  return ctx->cost_plain_popc + 16 * ctx->describe_variant + 64 * ctx->warp_pt.copies;
+}
 
 cudaError_t capture_graph(bsm_ctx *ctx) {
   cudaStream_t cs = ctx->batch_capture;

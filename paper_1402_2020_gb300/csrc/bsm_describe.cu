@@ -23,6 +23,10 @@
 //     pair i sits in lane i % 32, and lanes 0..n/32-1 store them.
 #include <cuda_fp16.h>
 
+#include <algorithm>
+#include <cstdlib>
+#include <vector>
+
 #include "bsm_internal.cuh"
 
 namespace bsm {
@@ -239,10 +243,13 @@ __device__ __forceinline__ void describe_warp_tile(const DescribeArgs &a, const 
   const int halo = a.halo, tp = 32 + 2 * halo, th = kWY + 2 * halo;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   uint32_t *tile = smem;
-  // tile rows by warp, columns by lane (no division in the addressing)
-  for (int ty = warp; ty < th; ty += kWY) {
-    const uint32_t *src = a.plane + (size_t)min(max(y0 + ty - halo, 0), a.h - 1) * a.w;
-    for (int tx = lane; tx < tp; tx += 32) cp_async4(tile + ty * tp + tx, src + min(max(x0 + tx - halo, 0), a.w - 1));
+  // every copy of the tile (at pt.copy_base[c]; copy 0 at 0): rows by warp, columns by lane
+  for (int c = 0; c < pt.copies; ++c) {
+    uint32_t *dst = tile + pt.copy_base[c];
+    for (int ty = warp; ty < th; ty += kWY) {
+      const uint32_t *src = a.plane + (size_t)min(max(y0 + ty - halo, 0), a.h - 1) * a.w;
+      for (int tx = lane; tx < tp; tx += 32) cp_async4(dst + ty * tp + tx, src + min(max(x0 + tx - halo, 0), a.w - 1));
+    }
   }
   // The offsets differ per lane, so a constant-bank read of them is serialised across the warp: read
   // them once per tile, through an opaque move that keeps them in registers instead of re-read.
@@ -355,11 +362,17 @@ __global__ void __launch_bounds__(kWY * 32) describe_warp_kernel(const DescribeA
   describe_warp_tile<NW, 8>(a, pt, blockIdx.x * 32, blockIdx.y * kWY, smem);
 }
 
-size_t describe_warp_smem(int halo) { return 4 * (size_t)(kWY + 2 * halo) * (32 + 2 * halo); }
+// Words between the bases of consecutive tile copies: the tile rounded up to whole 32-word rows of banks,
+// plus one such row for the copy's bank shift.
+int copy_stride(int halo) { return (((kWY + 2 * halo) * (32 + 2 * halo) + 31) & ~31) + 32; }
+
+size_t describe_warp_smem(int halo, int copies) {
+  return copies <= 1 ? 4 * (size_t)(kWY + 2 * halo) * (32 + 2 * halo) : 4 * (size_t)copies * copy_stride(halo);
+}
 
 template <int NW>
 cudaError_t launch_warp_nw(const DescribeArgs &a, const PairTable &pt, cudaStream_t s) {
-  const size_t smem = describe_warp_smem(a.halo);
+  const size_t smem = describe_warp_smem(a.halo, pt.copies);
   cudaError_t e = cudaFuncSetAttribute(describe_warp_kernel<NW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   dim3 grid((a.w + 31) / 32, (a.h + kWY - 1) / kWY);
@@ -466,11 +479,11 @@ cudaError_t launch_nw(const DescribeArgs &a, const PairTable &pt, cudaStream_t s
 static_assert(kWY == kTY, "the batched describe kernels share one tiling");
 
 template <int NW, bool WARP>
-cudaError_t prepare_batch_nw(int halo, int sms, int *grid) {
+cudaError_t prepare_batch_nw(int halo, int copies, int sms, int *grid) {
   size_t smem;
   void (*kern)(BatchHeader *, const BatchPair *, int, int, const PairTable);
   if constexpr (WARP) {
-    smem = describe_warp_smem(halo);
+    smem = describe_warp_smem(halo, copies);
     kern = describe_warp_batch_kernel<NW>;
   } else {
     smem = describe_smem<NW>(halo);
@@ -488,7 +501,7 @@ template <int NW, bool WARP>
 cudaError_t launch_batch_nw(BatchHeader *hdr, const BatchPair *pairs, int k, int halo, const PairTable &pt, int grid,
                             cudaStream_t s) {
   if constexpr (WARP)
-    describe_warp_batch_kernel<NW><<<grid, kTY * 32, describe_warp_smem(halo), s>>>(hdr, pairs, k, halo, pt);
+    describe_warp_batch_kernel<NW><<<grid, kTY * 32, describe_warp_smem(halo, pt.copies), s>>>(hdr, pairs, k, halo, pt);
   else
     describe_batch_kernel<NW><<<grid, kTY * 32, describe_smem<NW>(halo), s>>>(hdr, pairs, k, halo, pt);
   return cudaGetLastError();
@@ -499,6 +512,8 @@ bool batch_warp(const bsm_ctx *ctx) {
   return ctx->nw % 2 == 0 && (ctx->describe_variant == 2 || (ctx->describe_variant == 0 && ctx->nw == 8));
 }
 
+// One tile copy at base 0 (the thread-per-pixel kernels: every lane reads the same offset from its own
+// pixel, so a load touches 32 consecutive words).
 PairTable make_pair_table(const bsm_ctx *ctx) {
   const int tp = 32 + 2 * ctx->halo;
   PairTable pt{};
@@ -507,10 +522,153 @@ PairTable make_pair_table(const bsm_ctx *ctx) {
     pt.off[i][0] = q[1] * tp + q[0];
     pt.off[i][1] = q[3] * tp + q[2];
   }
+  pt.copies = 1;
   return pt;
 }
 
+// ---------------------------------------------------------------- gather plan of the warp-per-pixel kernel
+//
+// Lane l of a warp reads, for descriptor word j, the two samples of pair 32 j + l from the tile (one load
+// instruction per word and sample). The offsets of a word's 32 pairs are arbitrary, so with one tile the 32
+// addresses fall in the 32 banks at random and the load replays (about 3.3 wavefronts per load at n = 256,
+// S = 31). The kernel therefore keeps several copies of the tile whose bases lie in different banks: a
+// sample may be read from any copy, and the host picks, per load, a copy for every distinct offset so that
+// the fewest offsets share a bank (a matching of offsets to banks with a capacity L per bank, found by
+// augmenting paths, L raised until one exists). The copies' bank shifts are chosen among a fixed list of
+// candidates by the total wavefronts of all loads. Which lane reads which pair is unchanged, so word j's
+// bit l is still pair 32 j + l's (Eq. 3), and the samples' values are the same in every copy.
+constexpr int kDescribeCopies = 1;    // default tile copies (measured: with 2-4 copies the kernel is slower)
+constexpr int kMaxCopyWords = 16384;  // shared memory the copies of one tile may take (64 KB)
+constexpr int kShiftCandidates = 64;
+
+int bank_of(int word) { return ((word % 32) + 32) % 32; }
+
+struct LoadMatch {
+  int items = 0;       // distinct in-copy offsets of the load
+  int offs[32];
+  int choice[32];      // copy of each offset
+  int nb[32];          // offsets placed in each bank
+  int slot[32][32];    // ... and which
+  const int *base = nullptr;
+  int C = 1, L = 1;
+
+  bool place(int i, uint32_t &seen) {
+    for (int c = 0; c < C; ++c) {
+      const int b = bank_of(base[c] + offs[i]);
+      if ((seen >> b) & 1u) continue;
+      seen |= 1u << b;
+      if (nb[b] < L) {
+        slot[b][nb[b]++] = i;
+        choice[i] = c;
+        return true;
+      }
+      for (int k = 0; k < nb[b]; ++k) {
+        if (place(slot[b][k], seen)) {  // the occupant moved to another bank
+          slot[b][k] = i;
+          choice[i] = c;
+          return true;
+        }
+      }
+    }
+    return false;
+  }
+
+  // The smallest capacity with a complete placement (the load's wavefronts); choice[] holds that placement.
+  int solve(const int *bases, int copies) {
+    base = bases;
+    C = copies;
+    for (L = 1; L <= 32; ++L) {
+      for (int b = 0; b < 32; ++b) nb[b] = 0;
+      bool ok = true;
+      for (int i = 0; i < items && ok; ++i) {
+        uint32_t seen = 0;
+        ok = place(i, seen);
+      }
+      if (ok) return L;
+    }
+    return 32;  // not reached: one bank holds at most 32 offsets
+  }
+};
+
 }  // namespace
+
+int plan_tile_gathers(const int8_t *pairs, int n_bits, int copies, PairTable *pt, int *pitch, int *wavefronts) {
+  if (pairs == nullptr || pt == nullptr || n_bits < 32 || n_bits % 32 != 0 || n_bits > kMaxShortBits || copies < 1 ||
+      copies > kMaxTileCopies)
+    return 0;
+  int halo = 0;
+  for (int i = 0; i < 4 * n_bits; ++i) halo = std::max(halo, std::abs((int)pairs[i]));
+  if (halo > kMaxHalo) return 0;
+  const int tp = 32 + 2 * halo, stride = copy_stride(halo), nl = 2 * (n_bits / 32);
+  while (copies > 1 && copies * stride > kMaxCopyWords) --copies;
+  // the loads: lane l of load 2 j + s reads sample s of pair 32 j + l; item[l] indexes its distinct offset
+  std::vector<LoadMatch> loads(nl);
+  std::vector<int> item((size_t)nl * 32);
+  for (int ld = 0; ld < nl; ++ld) {
+    LoadMatch &m = loads[ld];
+    for (int l = 0; l < 32; ++l) {
+      const int8_t *q = pairs + 4 * (32 * (ld >> 1) + l) + 2 * (ld & 1);
+      const int off = q[1] * tp + q[0];
+      int k = 0;
+      while (k < m.items && m.offs[k] != off) ++k;
+      if (k == m.items) m.offs[m.items++] = off;
+      item[(size_t)ld * 32 + l] = k;
+    }
+  }
+  // candidate bank shifts of copies 1 .. C-1 (copy 0, which holds the centre, at shift 0): evenly spaced,
+  // then sets drawn by a fixed linear congruential generator
+  int best_shift[kMaxTileCopies] = {0, 0, 0, 0}, best_total = 1 << 30;
+  uint32_t rng = 12345u;
+  for (int cand = 0; cand < (copies > 1 ? kShiftCandidates : 1); ++cand) {
+    int shift[kMaxTileCopies] = {0, 0, 0, 0};
+    for (int c = 1; c < copies; ++c) {
+      if (cand == 0) {
+        shift[c] = 32 * c / copies;
+        continue;
+      }
+      for (;;) {
+        rng = rng * 1664525u + 1013904223u;
+        const int v = 1 + (int)((rng >> 8) % 31u);
+        bool dup = false;
+        for (int d = 1; d < c; ++d) dup = dup || shift[d] == v;
+        if (!dup) {
+          shift[c] = v;
+          break;
+        }
+      }
+    }
+    int base[kMaxTileCopies];
+    for (int c = 0; c < copies; ++c) base[c] = c * stride + shift[c];
+    int total = 0;
+    for (int ld = 0; ld < nl; ++ld) total += loads[ld].solve(base, copies);
+    if (total < best_total) {
+      best_total = total;
+      for (int c = 0; c < copies; ++c) best_shift[c] = shift[c];
+    }
+  }
+  *pt = PairTable{};
+  pt->copies = copies;
+  for (int c = 0; c < copies; ++c) pt->copy_base[c] = copies > 1 ? c * stride + best_shift[c] : 0;
+  for (int ld = 0; ld < nl; ++ld) {
+    LoadMatch &m = loads[ld];
+    const int w = m.solve(pt->copy_base, copies);
+    if (wavefronts != nullptr) wavefronts[ld] = w;
+    for (int l = 0; l < 32; ++l) {
+      const int k = item[(size_t)ld * 32 + l];
+      pt->off[32 * (ld >> 1) + l][ld & 1] = pt->copy_base[m.choice[k]] + m.offs[k];
+    }
+  }
+  if (pitch != nullptr) *pitch = tp;
+  return copies;
+}
+
+PairTable warp_pair_table(const bsm_ctx *ctx) {
+  PairTable pt{};
+  const int copies = ctx->describe_copies > 0 ? ctx->describe_copies : kDescribeCopies;
+  if (ctx->p.n_bits <= kMaxShortBits && plan_tile_gathers(ctx->pairs, ctx->p.n_bits, copies, &pt, nullptr, nullptr) > 0)
+    return pt;
+  return make_pair_table(ctx);
+}
 
 cudaError_t launch_color_plane_batch(const bsm_ctx *ctx, const BatchHeader *hdr, const BatchPair *pairs, int grid,
                                      cudaStream_t s) {
@@ -520,19 +678,20 @@ cudaError_t launch_color_plane_batch(const bsm_ctx *ctx, const BatchHeader *hdr,
 
 cudaError_t prepare_describe_batch(const bsm_ctx *ctx, int *grid) {
   const bool wp = batch_warp(ctx);
+  const int hl = ctx->halo, cp = ctx->warp_pt.copies, sm = ctx->sms;
   switch (ctx->nw) {
-    case 1: return prepare_batch_nw<1, false>(ctx->halo, ctx->sms, grid);
-    case 2: return wp ? prepare_batch_nw<2, true>(ctx->halo, ctx->sms, grid) : prepare_batch_nw<2, false>(ctx->halo, ctx->sms, grid);
-    case 4: return wp ? prepare_batch_nw<4, true>(ctx->halo, ctx->sms, grid) : prepare_batch_nw<4, false>(ctx->halo, ctx->sms, grid);
-    case 8: return wp ? prepare_batch_nw<8, true>(ctx->halo, ctx->sms, grid) : prepare_batch_nw<8, false>(ctx->halo, ctx->sms, grid);
+    case 1: return prepare_batch_nw<1, false>(hl, 1, sm, grid);
+    case 2: return wp ? prepare_batch_nw<2, true>(hl, cp, sm, grid) : prepare_batch_nw<2, false>(hl, 1, sm, grid);
+    case 4: return wp ? prepare_batch_nw<4, true>(hl, cp, sm, grid) : prepare_batch_nw<4, false>(hl, 1, sm, grid);
+    case 8: return wp ? prepare_batch_nw<8, true>(hl, cp, sm, grid) : prepare_batch_nw<8, false>(hl, 1, sm, grid);
     default: return cudaErrorInvalidValue;
   }
 }
 
 cudaError_t launch_describe_batch(const bsm_ctx *ctx, BatchHeader *hdr, const BatchPair *pairs, int grid,
                                   cudaStream_t s) {
-  const PairTable pt = make_pair_table(ctx);
   const bool wp = batch_warp(ctx);
+  const PairTable pt = wp ? ctx->warp_pt : make_pair_table(ctx);
   const int k = ctx->mask_rank, hl = ctx->halo;
   switch (ctx->nw) {
     case 1: return launch_batch_nw<1, false>(hdr, pairs, k, hl, pt, grid, s);
@@ -554,16 +713,16 @@ cudaError_t launch_describe_plane(const bsm_ctx *ctx, const uint32_t *plane, int
                                   uint32_t *Phi, cudaStream_t s) {
   if (ctx->nw > 8) return launch_describe_wide(ctx, plane, w, h, B, Phi, s);
   DescribeArgs a{plane, B, Phi, w, h, ctx->mask_rank, ctx->halo};
-  const PairTable pt = make_pair_table(ctx);
   // warp per pixel: chosen, or automatic from n = 256 on (measured faster there; thread per pixel below)
   if (ctx->describe_variant == 2 || (ctx->describe_variant == 0 && ctx->nw == 8)) {
     switch (ctx->nw) {
-      case 2: return launch_warp_nw<2>(a, pt, s);
-      case 4: return launch_warp_nw<4>(a, pt, s);
-      case 8: return launch_warp_nw<8>(a, pt, s);
+      case 2: return launch_warp_nw<2>(a, ctx->warp_pt, s);
+      case 4: return launch_warp_nw<4>(a, ctx->warp_pt, s);
+      case 8: return launch_warp_nw<8>(a, ctx->warp_pt, s);
       default: return cudaErrorInvalidValue;
     }
   }
+  const PairTable pt = make_pair_table(ctx);
   switch (ctx->nw) {
     case 1: return launch_nw<1>(a, pt, s);
     case 2: return launch_nw<2>(a, pt, s);

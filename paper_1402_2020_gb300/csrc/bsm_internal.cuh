@@ -23,10 +23,16 @@ constexpr long long kTcAutoWork = 1280LL * 720 * 128;
 // Byte layout of a colour-table entry: L | (a + 128) << 8 | (b + 128) << 16 | I << 24.
 constexpr uint32_t kLabMask = 0x00FFFFFFu;
 
-// Pair offsets in the shared-memory tile of the describe kernel: element i is
-// (dy_p * pitch + dx_p, dy_q * pitch + dx_q) for the tile pitch chosen at launch.
+// Pair offsets in the shared-memory tile of the describe kernels: element i is, for each of pair i's two
+// samples, its offset from the centre pixel, dy * pitch + dx for the tile pitch chosen at launch, plus the
+// base of the tile copy the sample is read from. The warp-per-pixel kernel keeps `copies` copies of its
+// tile at bases that fall in different shared-memory banks and reads each sample from the copy that
+// spreads its warp's 32 loads over the banks; the other kernels keep one copy at base 0.
+constexpr int kMaxTileCopies = 4;
 struct PairTable {
   int32_t off[kMaxShortBits][2];
+  int32_t copy_base[kMaxTileCopies];
+  int32_t copies;
 };
 
 // ---------------------------------------------------------------- batched execution
@@ -71,6 +77,7 @@ struct bsm_ctx {
   uint32_t *vote_es = nullptr;      // device, 2 R^2 + 1 entries
   uint32_t *status = nullptr;       // device status word (bsm_status latched by kernels)
   int32_t *wide_offs = nullptr;     // device pair offsets of the long-descriptor describe kernel
+  bsm::PairTable warp_pt{};         // gather plan of the warp-per-pixel describe kernel (tile copies)
   // Launch shapes (bsm_set_tuning); 0 selects the library's heuristic.
   int cost_rows = 0;        // rows per CTA band of the cost kernel
   int cost_plain_popc = 0;  // 1: plain popcount in the cost kernel instead of the carry-save tree
@@ -80,6 +87,7 @@ struct bsm_ctx {
   int batch_rows = 0;       // rows per task of the batched cost kernel
   int cost_variant = 0;     // 0 automatic, 1 one column per lane, 2 two columns per lane, 3 tensor cores
   int describe_variant = 0; // 0 automatic, 1 thread per pixel, 2 warp per pixel
+  int describe_copies = 0;  // tile copies of the warp-per-pixel describe kernel (0: the library's default)
   int withhold_arrivals = 0;  // test hook: cost kernels skip their mbarrier arrivals
   // Batched execution (bsm_batch_run).
   int sms = 0;
@@ -125,6 +133,13 @@ cudaError_t prepare_describe_batch(const bsm_ctx *ctx, int *grid);
 cudaError_t prepare_cost_batch(const bsm_ctx *ctx, int *grid);
 cudaError_t prepare_refine_batch(const bsm_ctx *ctx, int *grid);
 void wide_offsets(const bsm_ctx *ctx, int32_t *out);
+// Gather plan of the warp-per-pixel describe kernel for the context's pair table and tile copies (host
+// only): the copies' bases and every sample's copy.
+PairTable warp_pair_table(const bsm_ctx *ctx);
+// The same plan for any pair table and number of copies; wavefronts[l] (2 n_bits / 32 entries, or nullptr)
+// receives the shared-memory wavefronts of load l (word j's first samples at 2 j, its second at 2 j + 1).
+// Returns the number of copies used (fewer than asked when the tile is large), or 0 on bad arguments.
+int plan_tile_gathers(const int8_t *pairs, int n_bits, int copies, PairTable *pt, int *pitch, int *wavefronts);
 cudaError_t launch_describe_wide(const bsm_ctx *ctx, const uint32_t *plane, int w, int h, uint32_t *B, uint32_t *Phi,
                                  cudaStream_t s);
 cudaError_t launch_cost_long(const bsm_ctx *ctx, const uint32_t *BL, const uint32_t *PhiL, const uint32_t *BR,

@@ -1,15 +1,20 @@
 // Left/right check and voting refinement of the left disparity map (Sec. 3, Eq. 9-10).
 //
-// One CTA covers a 32 x 8 block of output pixels. It stages, for the block plus a halo of R pixels,
-// each pixel's CIELAB word and its disparity if that pixel passes the left/right check (-1
-// otherwise), together with the two integer vote tables. Valid pixels keep their disparity. Invalid
+// Every pixel is summarised in one refinement word: byte 0 = L | v << 7 (v: the pixel passes the
+// left/right check; CIELAB L is at most 100, so bit 7 is free), byte 1 = a + 128, byte 2 = b + 128,
+// byte 3 = the pixel's disparity when v, else the no-vote fallback of Eq. 10's row rule (the smaller of
+// the nearest valid disparities to its left and right on the row, whichever exists, else 0). A pre-pass
+// (refine_words_kernel, one warp per row) forms the words; the batched form builds them while staging,
+// with byte 3 = 0 for invalid pixels, and scans the row for the fallback instead.
+//
+// One CTA covers a 32 x 32 block of output pixels. It stages the words of the block plus a halo of R
+// pixels, together with the two integer vote tables. Valid pixels keep their disparity. Invalid
 // pixels are collected into a list that the CTA's warps share: a warp takes one invalid pixel at a
-// time; lane l owns window column l (and l + 32 when 2R+1 > 32) and walks down its rows, summing each
-// valid neighbour's vote floor(Ec[c] * Es[e2] / 2^15) in a register while consecutive voters share a
-// disparity and adding the run to a per-warp shared histogram over d when the disparity changes
-// (disparities are piecewise smooth, so runs are long and shared atomics few). The warp then takes
-// the smallest d with the largest weight (Eq. 9). When no vote is positive the warp scans the row
-// outward, 32 positions per step, for the nearest valid pixels on each side.
+// time and walks the window's valid voters, summing each one's vote floor(Ec[c] * Es[e2] / 2^15) in a
+// register while consecutive voters share a disparity and adding the run to a per-warp shared
+// histogram over d when the disparity changes (disparities are piecewise smooth, so runs are long and
+// shared atomics few). The warp then takes the smallest d with the largest weight (Eq. 9), or the
+// fallback when no vote is positive.
 //
 // The batched form reads the colour words from the batch's colour planes, and its disparity inputs
 // are the batched cost kernel's keys (A << 10 | d): every read keeps the low 10 bits, and each CTA
@@ -39,9 +44,16 @@ struct RefineArgs {
   int w, h, pitch, dmax, tol, R;
   int hist_stride;         // shared histogram bins per warp (>= dmax)
   bool finalize;           // write the masked disparities back into dL and dR
-  const uint32_t *near;    // per pixel (left + 1) | (right + 1) << 16: the nearest valid disparities on the row
-                           // on either side (0: none), or nullptr to scan the row
+  const uint32_t *words;   // the refinement words of the view (with the row fallback), or nullptr to form
+                           // them while staging and scan the row for the fallback
 };
+
+constexpr uint32_t kValidBit = 0x80u;
+
+// The refinement word of a pixel with colour word `colour`, check result `ok` and byte 3 `d`.
+__device__ __forceinline__ uint32_t refine_word(uint32_t colour, bool ok, uint32_t d) {
+  return (colour & kLabMask) | (ok ? kValidBit : 0u) | (d << 24);
+}
 
 __device__ __forceinline__ uint32_t lab_sad(uint32_t a, uint32_t b) {
   return __dp4a(__vabsdiffu4(a, b), 0x00010101u, 0u);
@@ -65,7 +77,7 @@ __device__ __forceinline__ void load_vote_tables(const uint32_t *Ec, const uint3
   for (int i = threadIdx.x; i < ne; i += blockDim.x) smem[kMaxSad + 1 + i] = __ldg(Es + i);
 }
 
-// One 32 x 8 block with top-left corner (x0, y0); `tabs` holds the vote tables, `work` the tile.
+// One kTX x kTY block with top-left corner (x0, y0); `tabs` holds the vote tables, `work` the tile.
 // Every thread of the CTA reaches its two CTA-wide barriers. RT > 0: the window radius is RT (the
 // window's 2 RT + 1 <= 32 columns are lanes and its rows an unrolled loop, so every shared-memory
 // address is a per-lane base plus a constant); RT == 0: any radius, a.R.
@@ -77,10 +89,9 @@ __device__ __forceinline__ void refine_tile(const RefineArgs &a, int x0, int y0,
   const int tp = kTX + 2 * R, th = kTY + 2 * R;
   const uint32_t *sEc = tabs;
   const uint32_t *sEs = tabs + (kMaxSad + 1);
-  uint32_t *slab = work;                                                // th * tp
+  uint32_t *slab = work;                                                // th * tp refinement words
   uint32_t *shist = slab + th * tp;                                     // kWarps * hist_stride
-  int16_t *sd = reinterpret_cast<int16_t *>(shist + kWarps * a.hist_stride);  // th * tp
-  int *s_count = reinterpret_cast<int *>(sd + ((th * tp + 1) & ~1));
+  int *s_count = reinterpret_cast<int *>(shist + kWarps * a.hist_stride);
   int16_t *s_list = reinterpret_cast<int16_t *>(s_count + 1);           // kTX * kTY
   // RT > 0: per tile row, the validity of its tp <= 64 columns as two bit words; per warp, the list of
   // an invalid pixel's voters (window row << 5 | window column)
@@ -89,10 +100,27 @@ __device__ __forceinline__ void refine_tile(const RefineArgs &a, int x0, int y0,
 
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   if (threadIdx.x == 0) *s_count = 0;
-  // Staging, kSG entries per thread at a time: each level of dependent loads (colour bytes and dL, then
-  // the colour table and dR) is issued for all of them before any result is used.
+  // Staging, kSG entries per thread at a time. From the pre-pass: one word per entry. Otherwise each
+  // level of dependent loads (colour bytes and dL, then the colour table and dR) is issued for all of them
+  // before any result is used. Outside the image: an invalid word.
   constexpr int kSG = 4;
-  for (int i0 = threadIdx.x; i0 < th * tp; i0 += kSG * (int)blockDim.x) {
+  for (int i0 = threadIdx.x; a.words != nullptr && i0 < th * tp; i0 += kSG * (int)blockDim.x) {
+    uint32_t v[kSG];
+#pragma unroll
+    for (int u = 0; u < kSG; ++u) {
+      const int i = i0 + u * (int)blockDim.x;
+      const int ty = i / tp, tx = i - ty * tp;
+      const int gx = x0 + tx - R, gy = y0 + ty - R;
+      v[u] = 0u;
+      if (i < th * tp && gx >= 0 && gx < a.w && gy >= 0 && gy < a.h) v[u] = __ldg(a.words + (size_t)gy * a.w + gx);
+    }
+#pragma unroll
+    for (int u = 0; u < kSG; ++u) {
+      const int i = i0 + u * (int)blockDim.x;
+      if (i < th * tp) slab[i] = v[u];
+    }
+  }
+  for (int i0 = threadIdx.x; a.words == nullptr && i0 < th * tp; i0 += kSG * (int)blockDim.x) {
     int gx[kSG], gy[kSG], d[kSG];
     bool in[kSG];
     uint32_t key[kSG];
@@ -125,18 +153,15 @@ __device__ __forceinline__ void refine_tile(const RefineArgs &a, int x0, int y0,
 #pragma unroll
     for (int u = 0; u < kSG; ++u) {
       const int i = i0 + u * (int)blockDim.x;
-      if (i < th * tp) {
-        slab[i] = key[u] & kLabMask;
-        sd[i] = ok[u] ? (int16_t)d[u] : (int16_t)-1;
-      }
+      if (i < th * tp) slab[i] = refine_word(key[u], ok[u], ok[u] ? (uint32_t)d[u] : 0u);
     }
   }
   __syncthreads();
   if constexpr (RT > 0) {  // the validity bitmaps of the tile rows (read after the next barrier)
     static_assert(kTX + 2 * RT <= 64, "a tile row in two bit words");
     for (int r = warp; r < th; r += kWarps) {
-      const uint32_t b0 = __ballot_sync(0xFFFFFFFFu, lane < tp && sd[r * tp + lane] >= 0);
-      const uint32_t b1 = __ballot_sync(0xFFFFFFFFu, 32 + lane < tp && sd[r * tp + 32 + lane] >= 0);
+      const uint32_t b0 = __ballot_sync(0xFFFFFFFFu, lane < tp && (slab[r * tp + lane] & kValidBit));
+      const uint32_t b1 = __ballot_sync(0xFFFFFFFFu, 32 + lane < tp && (slab[r * tp + 32 + lane] & kValidBit));
       if (lane == 0) {
         vbits[2 * r] = b0;
         vbits[2 * r + 1] = b1;
@@ -149,8 +174,8 @@ __device__ __forceinline__ void refine_tile(const RefineArgs &a, int x0, int y0,
     const int x = x0 + tx, y = y0 + ty;
     if (x < a.w && y < a.h) {
       const size_t i = (size_t)y * a.w + x;
-      const int dv = sd[(ty + R) * tp + tx + R];
-      if (dv >= 0) a.out[i] = dv;
+      const uint32_t wv = slab[(ty + R) * tp + tx + R];
+      if (wv & kValidBit) a.out[i] = (int)(wv >> 24);
       else s_list[atomicAdd(s_count, 1)] = (int16_t)p;
     }
   }
@@ -164,7 +189,8 @@ __device__ __forceinline__ void refine_tile(const RefineArgs &a, int x0, int y0,
     const int x = x0 + tx, y = y0 + ty;
     for (int d = lane; d < a.dmax; d += 32) hist[d] = 0;
     __syncwarp();
-    const uint32_t labx = slab[(ty + R) * tp + tx + R];
+    const uint32_t wx0 = slab[(ty + R) * tp + tx + R];  // the invalid pixel's own word
+    const uint32_t labx = wx0 | kValidBit;  // every voter has the bit: it drops out of the CIELAB SAD
     if constexpr (RT > 0) {
       // Only valid neighbours vote, and around an invalid pixel most are invalid (they cluster): lane wy
       // takes window row wy's validity bits from the row bitmap, a warp prefix sum of their counts lays
@@ -194,9 +220,9 @@ __device__ __forceinline__ void refine_tile(const RefineArgs &a, int x0, int y0,
       uint32_t run = 0;
       for (int q = s0; q < s1; ++q) {
         const int pos = wl[q], wy = pos >> 5, wx = pos & 31;
-        const int toff = (ty + wy) * tp + tx + wx;
-        const int dv = sd[toff];
-        const uint32_t v = (sEc[lab_sad(labx, slab[toff])] * sEs[(wx - RT) * (wx - RT) + (wy - RT) * (wy - RT)]) >> kVoteShift;
+        const uint32_t wv = slab[(ty + wy) * tp + tx + wx];
+        const int dv = (int)(wv >> 24);
+        const uint32_t v = (sEc[lab_sad(labx, wv)] * sEs[(wx - RT) * (wx - RT) + (wy - RT) * (wy - RT)]) >> kVoteShift;
         if (dv != run_d) {
           if (run) atomicAdd(&hist[run_d], run);
           run_d = dv;
@@ -208,15 +234,15 @@ __device__ __forceinline__ void refine_tile(const RefineArgs &a, int x0, int y0,
     }
     for (int wx = lane; RT == 0 && wx < side; wx += 32) {
       const int dx2 = (wx - R) * (wx - R);
-      const int16_t *dcol = sd + ty * tp + tx + wx;  // window row 0 of this column
-      const uint32_t *lcol = slab + ty * tp + tx + wx;
+      const uint32_t *lcol = slab + ty * tp + tx + wx;  // window row 0 of this column
       int run_d = -1;
       uint32_t run = 0;
       for (int wy = 0; wy < side; ++wy) {
-        const int dv = dcol[wy * tp];
-        if (dv >= 0) {
+        const uint32_t wv = lcol[wy * tp];
+        if (wv & kValidBit) {
+          const int dv = (int)(wv >> 24);
           const int dy = wy - R;
-          const uint32_t c = lab_sad(labx, lcol[wy * tp]);
+          const uint32_t c = lab_sad(labx, wv);
           const uint32_t v = (sEc[c] * sEs[dx2 + dy * dy]) >> kVoteShift;
           if (dv != run_d) {
             if (run) atomicAdd(&hist[run_d], run);
@@ -242,15 +268,12 @@ __device__ __forceinline__ void refine_tile(const RefineArgs &a, int x0, int y0,
     int best;
     if (gmax > 0) {
       best = (int)__reduce_min_sync(0xFFFFFFFFu, (unsigned)(bv == gmax ? bd : 0x7FFFFFFF));
+    } else if (a.words != nullptr) {
+      best = (int)(wx0 >> 24);  // no positive vote: the pre-pass's row fallback
     } else {
       // no positive vote: nearest valid disparities on the row
       int left = -1, right = -1;
-      if (a.near != nullptr) {
-        const uint32_t nv = __ldg(a.near + (size_t)y * a.w + x);
-        left = (int)(nv & 0xFFFFu) - 1;
-        right = (int)(nv >> 16) - 1;
-      }
-      for (int xs = x - 1; a.near == nullptr && xs >= 0; xs -= 32) {
+      for (int xs = x - 1; xs >= 0; xs -= 32) {
         const int xi = xs - lane;
         int d = -1;
         if (xi >= 0) d = disp_at(a.dL, (size_t)y * a.w + xi);
@@ -261,7 +284,7 @@ __device__ __forceinline__ void refine_tile(const RefineArgs &a, int x0, int y0,
           break;
         }
       }
-      for (int xs = x + 1; a.near == nullptr && xs < a.w; xs += 32) {
+      for (int xs = x + 1; xs < a.w; xs += 32) {
         const int xi = xs + lane;
         int d = -1;
         if (xi < a.w) d = disp_at(a.dL, (size_t)y * a.w + xi);
@@ -296,33 +319,48 @@ __device__ __forceinline__ void refine_tile(const RefineArgs &a, int x0, int y0,
 
 size_t tile_bytes(int R, int hist_stride) {
   const int tp = kTX + 2 * R, th = kTY + 2 * R;
-  return (size_t)th * tp * 4 + (size_t)kWarps * hist_stride * 4 + (size_t)((th * tp + 1) & ~1) * 2 + 4 +
-         (size_t)kTX * kTY * 2 + (size_t)2 * th * 4 + (size_t)kWarps * 32 * (2 * R + 1) * 2;
+  return (size_t)th * tp * 4 + (size_t)kWarps * hist_stride * 4 + 4 + (size_t)kTX * kTY * 2 + (size_t)2 * th * 4 +
+         (size_t)kWarps * 32 * (2 * R + 1) * 2;
 }
 
-// Nearest valid disparities on each row (for the refinement's no-vote case): one warp per row walks it in
-// 32-pixel segments, left to right and then right to left, carrying the last valid disparity seen; a
-// pixel's nearest valid neighbour inside its segment comes from the ballot of the segment's valid lanes.
-// The loads (and left/right checks) of kNS segments are issued together; the left-to-right pass leaves
-// each pixel's own valid disparity + 1 (0: invalid) in the upper half for the right-to-left pass.
+// Refinement words of a view (the plain form's pre-pass): one warp per row walks it in 32-pixel segments,
+// left to right and then right to left. Left to right: each pixel's colour word (its RGB through the
+// colour table), WTA disparity and left/right check give its word; an invalid pixel's byte 3 holds the
+// nearest valid disparity to its left (0 before the row's first valid pixel, whose position the warp
+// keeps). Right to left: an invalid pixel's byte 3 becomes the fallback of that value and the nearest
+// valid disparity to its right, carried along the row and, inside a segment, taken from the ballot of the
+// segment's valid lanes. Each lane reads back only the words it wrote. The loads (and left/right checks)
+// of kNS segments are issued together.
 constexpr int kNS = 8;
 
-__global__ void __launch_bounds__(256) near_valid_kernel(const RefineArgs a, uint32_t *near) {
+__global__ void __launch_bounds__(256) refine_words_kernel(const RefineArgs a, uint32_t *words) {
   const int lane = threadIdx.x & 31;
   const int y = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (y >= a.h) return;
   const size_t row = (size_t)y * a.w;
-  int carry = -1;  // the last valid disparity left of the segment
+  const uint8_t *rgb = a.rgb + (size_t)y * a.pitch;
+  int carry = -1;   // the last valid disparity left of the segment
+  int first = a.w;  // the row's first valid pixel
   for (int xb = 0; xb < a.w; xb += 32 * kNS) {
     int d[kNS];
+    uint32_t key[kNS];
     bool ok[kNS];
 #pragma unroll
     for (int u = 0; u < kNS; ++u) {
       const int x = xb + 32 * u + lane;
-      d[u] = x < a.w ? disp_at(a.dL, row + x) : a.dmax;
+      d[u] = a.dmax;
+      key[u] = 0u;
+      if (x < a.w) {
+        d[u] = disp_at(a.dL, row + x);
+        key[u] = ((uint32_t)rgb[3 * x] << 16) | ((uint32_t)rgb[3 * x + 1] << 8) | (uint32_t)rgb[3 * x + 2];
+      }
     }
 #pragma unroll
-    for (int u = 0; u < kNS; ++u) ok[u] = d[u] < a.dmax && lr_valid(a, xb + 32 * u + lane, y, d[u]);
+    for (int u = 0; u < kNS; ++u) {
+      const int x = xb + 32 * u + lane;
+      ok[u] = d[u] < a.dmax && lr_valid(a, x, y, d[u]);  // d == dmax outside the row
+      if (x < a.w) key[u] = __ldg(a.table + key[u]);
+    }
 #pragma unroll
     for (int u = 0; u < kNS; ++u) {
       const int x = xb + 32 * u + lane;
@@ -330,27 +368,33 @@ __global__ void __launch_bounds__(256) near_valid_kernel(const RefineArgs a, uin
       const uint32_t below = m & ((1u << lane) - 1u);  // valid lanes strictly left of this one
       const int dl = __shfl_sync(0xFFFFFFFFu, d[u], below ? 31 - __clz(below) : 0);
       const int left = below ? dl : carry;
-      if (x < a.w) near[row + x] = (uint32_t)(left + 1) | ((ok[u] ? (uint32_t)(d[u] + 1) : 0u) << 16);
+      if (m != 0u && first == a.w) first = xb + 32 * u + __ffs(m) - 1;
+      if (x < a.w) words[row + x] = refine_word(key[u], ok[u], (uint32_t)(ok[u] ? d[u] : max(left, 0)));
       if (m) carry = __shfl_sync(0xFFFFFFFFu, d[u], 31 - __clz(m));
     }
   }
   carry = -1;  // the first valid disparity right of the segment
   for (int xb = ((a.w - 1) / (32 * kNS)) * (32 * kNS); xb >= 0; xb -= 32 * kNS) {
-    uint32_t nv[kNS];
+    uint32_t wv[kNS];
 #pragma unroll
     for (int u = 0; u < kNS; ++u) {
       const int x = xb + 32 * u + lane;
-      nv[u] = x < a.w ? near[row + x] : 0u;
+      wv[u] = x < a.w ? words[row + x] : 0u;
     }
 #pragma unroll
     for (int u = kNS - 1; u >= 0; --u) {
       const int x = xb + 32 * u + lane;
-      const int vd = (int)(nv[u] >> 16) - 1;  // this pixel's valid disparity, or -1
-      const uint32_t m = __ballot_sync(0xFFFFFFFFu, vd >= 0);
+      const bool valid = (wv[u] & kValidBit) != 0u;
+      const int vd = (int)(wv[u] >> 24);
+      const uint32_t m = __ballot_sync(0xFFFFFFFFu, valid);
       const uint32_t above = lane == 31 ? 0u : m & (0xFFFFFFFEu << lane);  // valid lanes strictly right
       const int dr = __shfl_sync(0xFFFFFFFFu, vd, above ? __ffs(above) - 1 : 0);
       const int right = above ? dr : carry;
-      if (x < a.w) near[row + x] = (nv[u] & 0xFFFFu) | ((uint32_t)(right + 1) << 16);
+      if (x < a.w && !valid) {
+        const bool has_left = x > first;  // vd is the nearest valid disparity to the left
+        const int f = has_left && right >= 0 ? min(vd, right) : has_left ? vd : right >= 0 ? right : 0;
+        words[row + x] = (wv[u] & kLabMask) | ((uint32_t)f << 24);
+      }
       if (m) carry = __shfl_sync(0xFFFFFFFFu, vd, __ffs(m) - 1);
     }
   }
@@ -398,12 +442,12 @@ __global__ void __launch_bounds__(kThreadsR) refine_batch_kernel(BatchHeader *hd
 }  // namespace
 
 cudaError_t launch_refine(const bsm_ctx *ctx, const uint8_t *rgb, int pitch, const int32_t *dL, const int32_t *dR,
-                          int w, int h, int dmax, int32_t *out, uint32_t *near, cudaStream_t s) {
+                          int w, int h, int dmax, int32_t *out, uint32_t *words, cudaStream_t s) {
   // The plain form never writes dL or dR (finalize is off), so the const inputs stay untouched.
   RefineArgs a{rgb, nullptr, ctx->color_table, const_cast<int32_t *>(dL), const_cast<int32_t *>(dR), out, w, h, pitch,
-               dmax, ctx->p.lr_tol, ctx->p.vote_radius, dmax, false, near};
-  if (near != nullptr) {
-    near_valid_kernel<<<(h + 7) / 8, 256, 0, s>>>(a, near);
+               dmax, ctx->p.lr_tol, ctx->p.vote_radius, dmax, false, words};
+  if (words != nullptr) {
+    refine_words_kernel<<<(h + 7) / 8, 256, 0, s>>>(a, words);
     const cudaError_t e0 = cudaGetLastError();
     if (e0 != cudaSuccess) return e0;
   }

@@ -117,6 +117,24 @@ def test_describe_warp_per_pixel_bit_exact(B, orc, w, h, n, k):
     c.close()
 
 
+# The warp-per-pixel kernel with 2..4 copies of its tile, each sample read from the copy its gather plan
+# assigns (a tuning; the default is one copy); S = 9 makes a small halo, S = 63 takes fewer copies.
+@pytest.mark.parametrize("w,h,n,S,copies", [(450, 375, 256, 31, 4), (37, 23, 256, 31, 2), (61, 9, 128, 31, 3),
+                                            (40, 11, 64, 9, 4), (29, 13, 256, 63, 4)])
+def test_describe_tile_copies_bit_exact(B, orc, w, h, n, S, copies):
+    l, _, _ = synth.stereo_pair(w, h, 16, seed=130 + w)
+    pairs = synth.pair_table(n, S, seed=w + h + 2)
+    c = Ctx(B, pairs, dmax=16, window_S=S)
+    B.bsm_set_tuning(c.ctx, 0, 0, 0, 0, 2, copies)
+    assert B.bsm_get_tuning(c.ctx)["describe_copies"] == copies
+    Bp, Pp, _, _ = c.describe(l, 3)
+    torch.cuda.synchronize()
+    oB, oP = orc.describe(l, pairs, None)
+    assert (u32(Bp) == oB).all()
+    assert (u32(Pp) == oP).all()
+    c.close()
+
+
 @pytest.mark.parametrize("win,n,dmax", [(1, 256, 24), (3, 64, 24), (5, 256, 24), (7, 128, 24), (5, 32, 24),
                                         (3, 256, 150), (7, 256, 137), (1, 128, 140)])
 def test_cost_volume_bit_exact(B, orc, win, n, dmax):
