@@ -167,7 +167,7 @@ def test_tuning_does_not_change_bits(B, orc, rows, plain, variant, dmax):
     c = Ctx(B, pairs, agg_window=5, dmax=dmax)
     B.bsm_set_tuning(c.ctx, rows, plain, 0, variant)
     assert B.bsm_get_tuning(c.ctx) == {"cost_rows": rows, "cost_popc_plain": plain, "batch_rows": 0,
-                                       "cost_variant": variant, "describe_variant": 0}
+                                       "cost_variant": variant, "describe_variant": 0, "describe_copies": 0}
     BL, PL, _, _ = c.describe(l)
     BR, PR, _, _ = c.describe(r)
     dL, dR, cost = c.cost_wta(BL, PL, BR, PR, dmax, want_cost=True)
