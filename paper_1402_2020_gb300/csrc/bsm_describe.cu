@@ -320,16 +320,20 @@ __device__ __forceinline__ void describe_warp_tile(const DescribeArgs &a, const 
     }
     while (lo < hi) {  // T in [lo, hi] with count(w <= hi) >= k; every step halves the interval
       const uint32_t mid = (lo + hi) >> 1;
-      const uint32_t tb = mid * 0x10001u + kHalfBias;
+      // (1024 + mid + 1) - (1024 + w) saturated to [0, 1] is 1 exactly where w <= mid (integers below 2048
+      // are exact in fp16); the lane's sum starts at 1024, so its bits are 0x6400 + the count of each half
+      const uint32_t tb = (mid + 1) * 0x10001u + kHalfBias;
       const __half2 t2 = *reinterpret_cast<const __half2 *>(&tb);
-      // S = sum of the 0xFFFF-per-true-half masks = c_lo (2^16 - 1) + c_hi (2^32 - 2^16) mod 2^32, so
-      // -S (2^16 * 2 + 1) = c_lo + (c_lo + c_hi) 2^16 mod 2^32: the lane's count in the high half, below it a
-      // part under 2^16 that stays under 2^16 summed over the warp (c_lo <= NW / 2 per lane)
-      uint32_t S = 0;
+      __half2 c[NH];
 #pragma unroll
-      for (int m = 0; m < NH; ++m) S += __hle2_mask(*reinterpret_cast<const __half2 *>(&wv[m]), t2);
-      const uint32_t tot = __reduce_add_sync(0xFFFFFFFFu, S * (0u - 0x20001u));  // count << 16 | sum of c_lo
-      if (tot >= ((uint32_t)a.k << 16)) hi = mid;
+      for (int m = 0; m < NH; ++m) c[m] = __hsub2_sat(t2, *reinterpret_cast<const __half2 *>(&wv[m]));
+      const uint32_t bias = kHalfBias;
+      __half2 sum = *reinterpret_cast<const __half2 *>(&bias);
+#pragma unroll
+      for (int m = 0; m < NH; ++m) sum = __hadd2(sum, c[m]);
+      // over the warp: 32 (0x6400 (1 + 2^16)) + C_lo + C_hi 2^16 mod 2^32, both counts below 2^16
+      const uint32_t tot = __reduce_add_sync(0xFFFFFFFFu, *reinterpret_cast<const uint32_t *>(&sum)) - 0x800C8000u;
+      if ((tot & 0xFFFFu) + (tot >> 16) >= (uint32_t)a.k) hi = mid;
       else lo = mid + 1;
     }
     const uint32_t tb = lo * 0x10001u + kHalfBias;  // fp16 1024 + T in both halves
