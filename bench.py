@@ -580,7 +580,7 @@ def pinned_to_one_core(fn):
         os.sched_setaffinity(0, before)
 
 
-def refine_roofline(kname, dL, dR, dmax, R, lr_tol, seconds):
+def refine_roofline(kname, dL, dR, dmax, R, lr_tol, seconds, traffic=None):
     """Eq. 9-10 as instruction work: the vote window of every pixel that fails the left/right check.
     Per window position (clipped to the image) one load and one test of the voter's validity; per valid
     voter eight more (its colour word, the CIELAB SAD as a four-way absolute difference and a byte sum,
@@ -610,7 +610,7 @@ def refine_roofline(kname, dL, dR, dmax, R, lr_tol, seconds):
     peak = SMS * ISSUE_PER_CLK_SM * MAX_SM_MHZ * 1e6 / 1e9
     achieved = ops / seconds / 1e9
     return {"bound": "issue", "kernel": kname, "achieved": achieved, "peak": peak, "unit": "Ginstr/s",
-            "frac": achieved / peak, "traffic": None, "work_per_launch": ops,
+            "frac": achieved / peak, "traffic": traffic, "work_per_launch": ops,
             "peak_basis": f"{SMS} SMs x 4 schedulers x 32 lanes/clk x {MAX_SM_MHZ} MHz",
             "invalid_pixels": n_inv, "window_positions": positions, "valid_voters": voters,
             "note": "lane instructions of Eq. 9-10: 2 per window position, 8 per valid voter, 2 dmax per invalid "
@@ -808,7 +808,7 @@ def run_pair(args, cfg, world, rank, local, n_bits=N_BITS, window_S=WINDOW_S, si
     roof_ref = None
     if not sgm:
         roof_ref = refine_roofline(rname, dL.cpu().numpy(), dR.cpu().numpy(), dmax, VOTE_R, 1,
-                                   float(per[:, 3].mean()) * 1e-3)
+                                   float(per[:, 3].mean()) * 1e-3, profile_traffic("bsm_refine.cu", workload_key))
     line = {
         "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_step, "higher_is_better": True, "scaling": "weak",
