@@ -25,10 +25,9 @@
 namespace bsm {
 namespace {
 
-// A CTA of kWarps warps refines a kTX x kTY block. Its staged tile adds the window's R-pixel halo on
-// every side, so the block is square-ish: at R = 15 a 32 x 32 block stages 3.75 entries per output pixel
-// (a 32 x 8 block staged 9.2, and the staging, with its dependent colour-table and left/right-check
-// loads, was three quarters of the kernel's time).
+// A CTA of kWarps warps refines a kTX x kTY block (kTX x kShortTY on small images, below). Its staged tile
+// adds the window's R-pixel halo on every side, so the block is square-ish: at R = 15 a 32 x 32 block
+// stages 3.75 entries per output pixel (a 32 x 8 block stages 9.2).
 constexpr int kTX = kRefineTX, kTY = kRefineTY;
 constexpr int kWarps = 8;
 constexpr int kThreadsR = 32 * kWarps;
@@ -77,25 +76,25 @@ __device__ __forceinline__ void load_vote_tables(const uint32_t *Ec, const uint3
   for (int i = threadIdx.x; i < ne; i += blockDim.x) smem[kMaxSad + 1 + i] = __ldg(Es + i);
 }
 
-// One kTX x kTY block with top-left corner (x0, y0); `tabs` holds the vote tables, `work` the tile.
+// One kTX x TY block with top-left corner (x0, y0); `tabs` holds the vote tables, `work` the tile.
 // Every thread of the CTA reaches its two CTA-wide barriers. RT > 0: the window radius is RT (the
 // window's 2 RT + 1 <= 32 columns are lanes and its rows an unrolled loop, so every shared-memory
 // address is a per-lane base plus a constant); RT == 0: any radius, a.R.
-template <int RT>
+template <int RT, int TY>
 __device__ __forceinline__ void refine_tile(const RefineArgs &a, int x0, int y0, const uint32_t *tabs,
                                             uint32_t *work) {
   static_assert(RT == 0 || 2 * RT + 1 <= 32, "one lane per window column");
   const int R = RT > 0 ? RT : a.R, side = 2 * R + 1;
-  const int tp = kTX + 2 * R, th = kTY + 2 * R;
+  const int tp = kTX + 2 * R, th = TY + 2 * R;
   const uint32_t *sEc = tabs;
   const uint32_t *sEs = tabs + (kMaxSad + 1);
   uint32_t *slab = work;                                                // th * tp refinement words
   uint32_t *shist = slab + th * tp;                                     // kWarps * hist_stride
   int *s_count = reinterpret_cast<int *>(shist + kWarps * a.hist_stride);
-  int16_t *s_list = reinterpret_cast<int16_t *>(s_count + 1);           // kTX * kTY
+  int16_t *s_list = reinterpret_cast<int16_t *>(s_count + 1);           // kTX * TY
   // RT > 0: per tile row, the validity of its tp <= 64 columns as two bit words; per warp, the list of
   // an invalid pixel's voters (window row << 5 | window column)
-  uint32_t *vbits = reinterpret_cast<uint32_t *>(s_list + kTX * kTY);  // 2 th
+  uint32_t *vbits = reinterpret_cast<uint32_t *>(s_list + kTX * TY);   // 2 th
   uint16_t *vlist = reinterpret_cast<uint16_t *>(vbits + 2 * th);      // kWarps * 32 * (2 RT + 1)
 
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -169,7 +168,7 @@ __device__ __forceinline__ void refine_tile(const RefineArgs &a, int x0, int y0,
     }
   }
 
-  for (int p = threadIdx.x; p < kTX * kTY; p += blockDim.x) {
+  for (int p = threadIdx.x; p < kTX * TY; p += blockDim.x) {
     const int tx = p & (kTX - 1), ty = p / kTX;
     const int x = x0 + tx, y = y0 + ty;
     if (x < a.w && y < a.h) {
@@ -305,7 +304,7 @@ __device__ __forceinline__ void refine_tile(const RefineArgs &a, int x0, int y0,
   }
 
   if (a.finalize) {
-    for (int p = threadIdx.x; p < kTX * kTY; p += blockDim.x) {
+    for (int p = threadIdx.x; p < kTX * TY; p += blockDim.x) {
       const int tx = p & (kTX - 1), ty = p / kTX;
       const int x = x0 + tx, y = y0 + ty;
       if (x < a.w && y < a.h) {
@@ -317,9 +316,11 @@ __device__ __forceinline__ void refine_tile(const RefineArgs &a, int x0, int y0,
   }
 }
 
-size_t tile_bytes(int R, int hist_stride) {
-  const int tp = kTX + 2 * R, th = kTY + 2 * R;
-  return (size_t)th * tp * 4 + (size_t)kWarps * hist_stride * 4 + 4 + (size_t)kTX * kTY * 2 + (size_t)2 * th * 4 +
+// The shared memory refine_tile carves up after the vote tables, in its order: the staged words, the
+// warps' histograms, the invalid-pixel count and list, the row bitmaps and the warps' voter lists.
+size_t tile_bytes(int R, int hist_stride, int ty) {
+  const int tp = kTX + 2 * R, th = ty + 2 * R;
+  return (size_t)th * tp * 4 + (size_t)kWarps * hist_stride * 4 + 4 + (size_t)kTX * ty * 2 + (size_t)2 * th * 4 +
          (size_t)kWarps * 32 * (2 * R + 1) * 2;
 }
 
@@ -402,11 +403,26 @@ __global__ void __launch_bounds__(256) refine_words_kernel(const RefineArgs a, u
 
 constexpr int kRFast = 15;  // the radius with an unrolled window walk (the paper's setting)
 
-template <int RT>
+// Blocks of kTX x TY: 32 rows where the grid fills the GPU (fewer staged halo entries per output pixel),
+// kShortTY rows on images too small for that (more CTAs).
+constexpr int kShortTY = 8;
+
+template <int RT, int TY>
 __global__ void __launch_bounds__(kThreadsR) refine_kernel(const RefineArgs a, const uint32_t *Ec, const uint32_t *Es) {
   extern __shared__ __align__(16) uint32_t smem[];
   load_vote_tables(Ec, Es, a.R, smem);
-  refine_tile<RT>(a, blockIdx.x * kTX, blockIdx.y * kTY, smem, smem + table_words(a.R));
+  refine_tile<RT, TY>(a, blockIdx.x * kTX, blockIdx.y * TY, smem, smem + table_words(a.R));
+}
+
+template <int TY>
+cudaError_t launch_refine_ty(const RefineArgs &a, const bsm_ctx *ctx, cudaStream_t s) {
+  const size_t smem = table_words(a.R) * 4 + tile_bytes(a.R, a.hist_stride, TY);
+  auto kern = a.R == kRFast ? refine_kernel<kRFast, TY> : refine_kernel<0, TY>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  dim3 grid((a.w + kTX - 1) / kTX, (a.h + TY - 1) / TY);
+  kern<<<grid, kThreadsR, smem, s>>>(a, ctx->vote_ec, ctx->vote_es);
+  return cudaGetLastError();
 }
 
 // Batched refinement: persistent CTAs take (pair, block) tickets.
@@ -435,7 +451,7 @@ __global__ void __launch_bounds__(kThreadsR) refine_batch_kernel(BatchHeader *hd
     const int r = tk - p.ref_base, ty = r / p.ref_tx, tx = r - ty * p.ref_tx;
     RefineArgs a{p.rgb[0], p.plane[0], table, p.disp[0], p.disp[1], p.out, p.w, p.h, p.pitch, p.dmax,
                  tol, R, hist_stride, true, nullptr};
-    refine_tile<RT>(a, tx * kTX, ty * kTY, smem, smem + table_words(R));
+    refine_tile<RT, kTY>(a, tx * kTX, ty * kTY, smem, smem + table_words(R));
   }
 }
 
@@ -451,18 +467,13 @@ cudaError_t launch_refine(const bsm_ctx *ctx, const uint8_t *rgb, int pitch, con
     const cudaError_t e0 = cudaGetLastError();
     if (e0 != cudaSuccess) return e0;
   }
-  const size_t smem = table_words(a.R) * 4 + tile_bytes(a.R, dmax);
-  auto kern = a.R == kRFast ? refine_kernel<kRFast> : refine_kernel<0>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  dim3 grid((w + kTX - 1) / kTX, (h + kTY - 1) / kTY);
-  kern<<<grid, kThreadsR, smem, s>>>(a, ctx->vote_ec, ctx->vote_es);
-  return cudaGetLastError();
+  const long long blocks = (long long)((w + kTX - 1) / kTX) * ((h + kTY - 1) / kTY);
+  return blocks >= 4LL * ctx->sms ? launch_refine_ty<kTY>(a, ctx, s) : launch_refine_ty<kShortTY>(a, ctx, s);
 }
 
 cudaError_t prepare_refine_batch(const bsm_ctx *ctx, int *grid) {
   const int R = ctx->p.vote_radius, hs = ctx->p.dmax;
-  const size_t smem = table_words(R) * 4 + tile_bytes(R, hs);
+  const size_t smem = table_words(R) * 4 + tile_bytes(R, hs, kTY);
   auto kern = R == kRFast ? refine_batch_kernel<kRFast> : refine_batch_kernel<0>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
@@ -475,7 +486,7 @@ cudaError_t prepare_refine_batch(const bsm_ctx *ctx, int *grid) {
 cudaError_t launch_refine_batch(const bsm_ctx *ctx, BatchHeader *hdr, const BatchPair *pairs, int grid,
                                 cudaStream_t s) {
   const int R = ctx->p.vote_radius, hs = ctx->p.dmax;
-  const size_t smem = table_words(R) * 4 + tile_bytes(R, hs);
+  const size_t smem = table_words(R) * 4 + tile_bytes(R, hs, kTY);
   auto kern = R == kRFast ? refine_batch_kernel<kRFast> : refine_batch_kernel<0>;
   kern<<<grid, kThreadsR, smem, s>>>(hdr, pairs, ctx->vote_ec, ctx->vote_es, ctx->color_table, ctx->p.lr_tol, R, hs);
   return cudaGetLastError();
