@@ -76,6 +76,26 @@ __device__ __forceinline__ void load_vote_tables(const uint32_t *Ec, const uint3
   for (int i = threadIdx.x; i < ne; i += blockDim.x) smem[kMaxSad + 1 + i] = __ldg(Es + i);
 }
 
+// The shared memory a CTA's tile takes after the vote tables, as byte offsets in carve-up order: the
+// staged words (th x tp), the warps' histograms, the invalid-pixel count and list (kTX x ty), the row
+// bitmaps (2 words a tile row) and the warps' voter lists (32 x (2R + 1) entries each). refine_tile takes
+// its pointers from here and the launch sizes the allocation from `bytes`, so the two cannot disagree.
+struct TileLayout {
+  size_t hist, count, list, vbits, vlist, bytes;
+};
+
+__host__ __device__ __forceinline__ TileLayout tile_layout(int R, int hist_stride, int ty) {
+  const size_t tp = kTX + 2 * R, th = ty + 2 * R;
+  TileLayout l;
+  l.hist = th * tp * 4;
+  l.count = l.hist + (size_t)kWarps * hist_stride * 4;
+  l.list = l.count + 4;
+  l.vbits = l.list + (size_t)kTX * ty * 2;  // a multiple of 4: the list has kTX * ty = 32 ty entries
+  l.vlist = l.vbits + th * 2 * 4;
+  l.bytes = l.vlist + (size_t)kWarps * 32 * (2 * R + 1) * 2;
+  return l;
+}
+
 // One kTX x TY block with top-left corner (x0, y0); `tabs` holds the vote tables, `work` the tile.
 // Every thread of the CTA reaches its two CTA-wide barriers. RT > 0: the window radius is RT (the
 // window's 2 RT + 1 <= 32 columns are lanes and its rows an unrolled loop, so every shared-memory
@@ -88,14 +108,16 @@ __device__ __forceinline__ void refine_tile(const RefineArgs &a, int x0, int y0,
   const int tp = kTX + 2 * R, th = TY + 2 * R;
   const uint32_t *sEc = tabs;
   const uint32_t *sEs = tabs + (kMaxSad + 1);
+  const TileLayout lay = tile_layout(R, a.hist_stride, TY);
+  uint8_t *base = reinterpret_cast<uint8_t *>(work);
   uint32_t *slab = work;                                                // th * tp refinement words
-  uint32_t *shist = slab + th * tp;                                     // kWarps * hist_stride
-  int *s_count = reinterpret_cast<int *>(shist + kWarps * a.hist_stride);
-  int16_t *s_list = reinterpret_cast<int16_t *>(s_count + 1);           // kTX * TY
+  uint32_t *shist = reinterpret_cast<uint32_t *>(base + lay.hist);     // kWarps * hist_stride
+  int *s_count = reinterpret_cast<int *>(base + lay.count);
+  int16_t *s_list = reinterpret_cast<int16_t *>(base + lay.list);      // kTX * TY
   // RT > 0: per tile row, the validity of its tp <= 64 columns as two bit words; per warp, the list of
   // an invalid pixel's voters (window row << 5 | window column)
-  uint32_t *vbits = reinterpret_cast<uint32_t *>(s_list + kTX * TY);   // 2 th
-  uint16_t *vlist = reinterpret_cast<uint16_t *>(vbits + 2 * th);      // kWarps * 32 * (2 RT + 1)
+  uint32_t *vbits = reinterpret_cast<uint32_t *>(base + lay.vbits);    // 2 th
+  uint16_t *vlist = reinterpret_cast<uint16_t *>(base + lay.vlist);    // kWarps * 32 * (2 RT + 1)
 
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   if (threadIdx.x == 0) *s_count = 0;
@@ -316,13 +338,7 @@ __device__ __forceinline__ void refine_tile(const RefineArgs &a, int x0, int y0,
   }
 }
 
-// The shared memory refine_tile carves up after the vote tables, in its order: the staged words, the
-// warps' histograms, the invalid-pixel count and list, the row bitmaps and the warps' voter lists.
-size_t tile_bytes(int R, int hist_stride, int ty) {
-  const int tp = kTX + 2 * R, th = ty + 2 * R;
-  return (size_t)th * tp * 4 + (size_t)kWarps * hist_stride * 4 + 4 + (size_t)kTX * ty * 2 + (size_t)2 * th * 4 +
-         (size_t)kWarps * 32 * (2 * R + 1) * 2;
-}
+size_t tile_bytes(int R, int hist_stride, int ty) { return tile_layout(R, hist_stride, ty).bytes; }
 
 // Refinement words of a view (the plain form's pre-pass): one warp per row walks it in 32-pixel segments,
 // left to right and then right to left. Left to right: each pixel's colour word (its RGB through the
