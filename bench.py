@@ -345,9 +345,9 @@ def run_batch(args, cfg, world, rank, local):
     tuning = bsm.bsm_get_tuning(ctx)
     # the batch: four persistent launches, plus one tensor-core cost launch per pair of at least
     # 1280 x 720 x 128 pixel-disparities; the per-pair calls: colour pre-pass and describe per view, the
-    # cost stage's kernels, the refinement-word pass and refine
+    # cost stage's kernels, the refinement-word pass, the block ordering and refine
     n_tc = sum(1 for t in ts if t["w"] * t["h"] * t["dmax"] >= 1280 * 720 * 128) if tuning["cost_variant"] in (0, 3) else 0
-    plain_launches = sum(4 + bsm.bsm_cost_plan(ctx, t["w"], t["h"], t["dmax"])["launches"] + 2 for t in ts)
+    plain_launches = sum(4 + bsm.bsm_cost_plan(ctx, t["w"], t["h"], t["dmax"])["launches"] + 3 for t in ts)
     line = {
         "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_batch, "higher_is_better": True, "scaling": "weak",
@@ -822,8 +822,9 @@ def run_pair(args, cfg, world, rank, local, n_bits=N_BITS, window_S=WINDOW_S, si
                      "refine": float(per[:, 3].mean())},
         "pairs_per_s": world / (t_step * 1e-3),
         "bad_pixel_rate": bad,  # |d - d_gt| > 1 against the generator's ground truth, rank 0's pair
-        # colour pre-pass + describe per view, the cost stage's kernels, the refinement-word pass + refine
-        "gpu_launches": (4 + klaunch + 2 + (2 * sgm[2] if sgm else 0)) * args.steps,
+        # colour pre-pass + describe per view, the cost stage's kernels, the refinement-word pass, the block
+        # ordering and refine
+        "gpu_launches": (4 + klaunch + 3 + (2 * sgm[2] if sgm else 0)) * args.steps,
         "roofline": roof_desc if describe_dominant else roof_cost,
         ("roofline_cost" if describe_dominant else "roofline_describe"): roof_cost if describe_dominant else roof_desc,
         "clocks": clocks,

@@ -111,6 +111,7 @@ void bsm_destroy(bsm_ctx *ctx) {
   cudaFree(ctx->vote_es);
   cudaFree(ctx->status);
   cudaFree(ctx->wide_offs);
+  cudaFree(ctx->refine_tiles);
   cudaFree(ctx->ws);
   cudaFree(ctx->plane);
   if (ctx->batch_graph) cudaGraphExecDestroy(ctx->batch_graph);
@@ -185,6 +186,7 @@ bsm_status bsm_create(const bsm_params *p, bsm_ctx **out) {
       delete[] offs;
     }
   }
+  if (e == cudaSuccess) e = cudaMalloc(&ctx->refine_tiles, sizeof(int32_t) * 2 * bsm::kMaxRefineTiles);
   if (e == cudaSuccess) e = cudaMemset(ctx->status, 0, sizeof(uint32_t));
   if (e == cudaSuccess) e = bsm::build_color_table(ctx->color_table, lin_dev, 0);
   if (e == cudaSuccess) e = cudaDeviceSynchronize();

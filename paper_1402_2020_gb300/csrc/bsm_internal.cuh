@@ -39,6 +39,7 @@ struct PairTable {
 
 constexpr int kMaxBatch = 1024;   // pairs per bsm_batch_run call
 constexpr int kRefineTX = 32, kRefineTY = 32;  // output block of one refinement CTA (per pair and batched)
+constexpr int kMaxRefineTiles = (16384 / kRefineTX) * (16384 / kRefineTY);  // blocks of the largest image
 constexpr int kBatchDisp = 64;    // disparities per CTA of the batched cost kernel (8 warps)
 
 // One pair of a batch, as the batched kernels see it (built on the host, copied to the device).
@@ -78,6 +79,7 @@ struct bsm_ctx {
   uint32_t *status = nullptr;       // device status word (bsm_status latched by kernels)
   int32_t *wide_offs = nullptr;     // device pair offsets of the long-descriptor describe kernel
   bsm::PairTable warp_pt{};         // gather plan of the warp-per-pixel describe kernel (tile copies)
+  int32_t *refine_tiles = nullptr;  // device, 2 x kMaxRefineTiles: refinement blocks' invalid counts and their order
   // Launch shapes (bsm_set_tuning); 0 selects the library's heuristic.
   int cost_rows = 0;        // rows per CTA band of the cost kernel
   int cost_plain_popc = 0;  // 1: plain popcount in the cost kernel instead of the carry-save tree

@@ -7,8 +7,10 @@
 // (refine_words_kernel, one warp per row) forms the words; the batched form builds them while staging,
 // with byte 3 = 0 for invalid pixels, and scans the row for the fallback instead.
 //
-// One CTA covers a 32 x 32 block of output pixels. It stages the words of the block plus a halo of R
-// pixels, together with the two integer vote tables. Valid pixels keep their disparity. Invalid
+// One CTA (16 warps) covers a 32 x 32 block of output pixels. The pre-pass also counts each block's invalid
+// pixels, and the blocks are taken in decreasing order of that count: invalid pixels cluster (occlusions),
+// so a few blocks carry most of the votes, and started last they would set the kernel's tail. The CTA
+// stages the words of the block plus a halo of R pixels, together with the two integer vote tables. Valid pixels keep their disparity. Invalid
 // pixels are collected into a list that the CTA's warps share: a warp takes one invalid pixel at a
 // time and walks the window's valid voters, summing each one's vote floor(Ec[c] * Es[e2] / 2^15) in a
 // register while consecutive voters share a disparity and adding the run to a per-warp shared
@@ -29,7 +31,7 @@ namespace {
 // adds the window's R-pixel halo on every side, so the block is square-ish: at R = 15 a 32 x 32 block
 // stages 3.75 entries per output pixel (a 32 x 8 block stages 9.2).
 constexpr int kTX = kRefineTX, kTY = kRefineTY;
-constexpr int kWarps = 8;
+constexpr int kWarps = 16;  // a block's invalid pixels spread over more warps (the heaviest blocks set the tail)
 constexpr int kThreadsR = 32 * kWarps;
 constexpr uint32_t kDispMask = 1023u;
 
@@ -45,6 +47,9 @@ struct RefineArgs {
   bool finalize;           // write the masked disparities back into dL and dR
   const uint32_t *words;   // the refinement words of the view (with the row fallback), or nullptr to form
                            // them while staging and scan the row for the fallback
+  int *tile_cnt;           // per block: its invalid pixels (counted by the pre-pass), or nullptr
+  const int *tile_order;   // the blocks in the order CTAs take them (most invalid pixels first), or nullptr
+  int tile_h;              // rows of a block (kTY or kShortTY)
 };
 
 constexpr uint32_t kValidBit = 0x80u;
@@ -386,6 +391,11 @@ __global__ void __launch_bounds__(256) refine_words_kernel(const RefineArgs a, u
       const int dl = __shfl_sync(0xFFFFFFFFu, d[u], below ? 31 - __clz(below) : 0);
       const int left = below ? dl : carry;
       if (m != 0u && first == a.w) first = xb + 32 * u + __ffs(m) - 1;
+      if (a.tile_cnt != nullptr) {  // the segment's invalid pixels, to the count of its block
+        const int nbad = __popc(__ballot_sync(0xFFFFFFFFu, x < a.w) & ~m);
+        if (lane == 0 && nbad > 0)
+          atomicAdd(a.tile_cnt + (y / a.tile_h) * ((a.w + kTX - 1) / kTX) + (xb + 32 * u) / kTX, nbad);
+      }
       if (x < a.w) words[row + x] = refine_word(key[u], ok[u], (uint32_t)(ok[u] ? d[u] : max(left, 0)));
       if (m) carry = __shfl_sync(0xFFFFFFFFu, d[u], 31 - __clz(m));
     }
@@ -423,11 +433,35 @@ constexpr int kRFast = 15;  // the radius with an unrolled window walk (the pape
 // kShortTY rows on images too small for that (more CTAs).
 constexpr int kShortTY = 8;
 
+// The blocks in decreasing order of their invalid pixels (buckets of 8; any order within a bucket): CTAs
+// are dispatched in index order, so the blocks that take longest start first instead of setting the tail.
+// Every block appears exactly once. One CTA.
+constexpr int kOrderBuckets = kTX * kTY / 8 + 1;
+
+__global__ void __launch_bounds__(1024) order_tiles_kernel(const int *cnt, int n, int *order) {
+  __shared__ int hist[kOrderBuckets], base[kOrderBuckets];
+  for (int i = threadIdx.x; i < kOrderBuckets; i += blockDim.x) hist[i] = 0;
+  __syncthreads();
+  for (int i = threadIdx.x; i < n; i += blockDim.x) atomicAdd(&hist[min(cnt[i] >> 3, kOrderBuckets - 1)], 1);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int run = 0;
+    for (int b = kOrderBuckets - 1; b >= 0; --b) {
+      base[b] = run;
+      run += hist[b];
+    }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < n; i += blockDim.x) order[atomicAdd(&base[min(cnt[i] >> 3, kOrderBuckets - 1)], 1)] = i;
+}
+
 template <int RT, int TY>
 __global__ void __launch_bounds__(kThreadsR) refine_kernel(const RefineArgs a, const uint32_t *Ec, const uint32_t *Es) {
   extern __shared__ __align__(16) uint32_t smem[];
+  const int lin = (int)(blockIdx.y * gridDim.x + blockIdx.x);
+  const int t = a.tile_order != nullptr ? a.tile_order[lin] : lin;
   load_vote_tables(Ec, Es, a.R, smem);
-  refine_tile<RT, TY>(a, blockIdx.x * kTX, blockIdx.y * TY, smem, smem + table_words(a.R));
+  refine_tile<RT, TY>(a, (t % (int)gridDim.x) * kTX, (t / (int)gridDim.x) * TY, smem, smem + table_words(a.R));
 }
 
 template <int TY>
@@ -477,14 +511,29 @@ cudaError_t launch_refine(const bsm_ctx *ctx, const uint8_t *rgb, int pitch, con
                           int w, int h, int dmax, int32_t *out, uint32_t *words, cudaStream_t s) {
   // The plain form never writes dL or dR (finalize is off), so the const inputs stay untouched.
   RefineArgs a{rgb, nullptr, ctx->color_table, const_cast<int32_t *>(dL), const_cast<int32_t *>(dR), out, w, h, pitch,
-               dmax, ctx->p.lr_tol, ctx->p.vote_radius, dmax, false, words};
+               dmax, ctx->p.lr_tol, ctx->p.vote_radius, dmax, false, words, nullptr, nullptr, kTY};
+  const int tiles_x = (w + kTX - 1) / kTX;
+  const bool tall = (long long)tiles_x * ((h + kTY - 1) / kTY) >= 4LL * ctx->sms;
+  a.tile_h = tall ? kTY : kShortTY;
+  const int ntiles = tiles_x * ((h + a.tile_h - 1) / a.tile_h);
   if (words != nullptr) {
+    if (ctx->refine_tiles != nullptr && ntiles <= kMaxRefineTiles) {
+      a.tile_cnt = ctx->refine_tiles;
+      cudaError_t e0 = cudaMemsetAsync(a.tile_cnt, 0, sizeof(int) * (size_t)ntiles, s);
+      if (e0 != cudaSuccess) return e0;
+    }
     refine_words_kernel<<<(h + 7) / 8, 256, 0, s>>>(a, words);
-    const cudaError_t e0 = cudaGetLastError();
+    cudaError_t e0 = cudaGetLastError();
     if (e0 != cudaSuccess) return e0;
+    if (a.tile_cnt != nullptr) {
+      int *order = ctx->refine_tiles + kMaxRefineTiles;
+      order_tiles_kernel<<<1, 1024, 0, s>>>(a.tile_cnt, ntiles, order);
+      e0 = cudaGetLastError();
+      if (e0 != cudaSuccess) return e0;
+      a.tile_order = order;
+    }
   }
-  const long long blocks = (long long)((w + kTX - 1) / kTX) * ((h + kTY - 1) / kTY);
-  return blocks >= 4LL * ctx->sms ? launch_refine_ty<kTY>(a, ctx, s) : launch_refine_ty<kShortTY>(a, ctx, s);
+  return tall ? launch_refine_ty<kTY>(a, ctx, s) : launch_refine_ty<kShortTY>(a, ctx, s);
 }
 
 cudaError_t prepare_refine_batch(const bsm_ctx *ctx, int *grid) {
