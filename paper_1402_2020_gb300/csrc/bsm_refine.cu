@@ -209,12 +209,20 @@ __device__ __forceinline__ void refine_tile(const RefineArgs &a, int x0, int y0,
 
   const int count = *s_count;
   uint32_t *hist = shist + warp * a.hist_stride;
+  // the warp's histogram is cleared once here; after each pixel only the bins it touched are cleared again
+  for (int d = lane; d < a.dmax; d += 32) hist[d] = 0;
+  __syncwarp();
   for (int it = warp; it < count; it += kWarps) {
     const int t = s_list[it];
     const int tx = t & (kTX - 1), ty = t / kTX;
     const int x = x0 + tx, y = y0 + ty;
-    for (int d = lane; d < a.dmax; d += 32) hist[d] = 0;
-    __syncwarp();
+    // a run of equal disparity goes to the histogram with one atomic; [dlo, dhi] holds the bins the lane touched
+    uint32_t dlo = 0xFFFFu, dhi = 0u;
+    auto add_run = [&](int d, uint32_t v) {
+      atomicAdd(&hist[d], v);
+      dlo = min(dlo, (uint32_t)d);
+      dhi = max(dhi, (uint32_t)d);
+    };
     const uint32_t wx0 = slab[(ty + R) * tp + tx + R];  // the invalid pixel's own word
     const uint32_t labx = wx0 | kValidBit;  // every voter has the bit: it drops out of the CIELAB SAD
     if constexpr (RT > 0) {
@@ -250,13 +258,13 @@ __device__ __forceinline__ void refine_tile(const RefineArgs &a, int x0, int y0,
         const int dv = (int)(wv >> 24);
         const uint32_t v = (sEc[lab_sad(labx, wv)] * sEs[(wx - RT) * (wx - RT) + (wy - RT) * (wy - RT)]) >> kVoteShift;
         if (dv != run_d) {
-          if (run) atomicAdd(&hist[run_d], run);
+          if (run) add_run(run_d, run);
           run_d = dv;
           run = 0;
         }
         run += v;
       }
-      if (run) atomicAdd(&hist[run_d], run);
+      if (run) add_run(run_d, run);
     }
     for (int wx = lane; RT == 0 && wx < side; wx += 32) {
       const int dx2 = (wx - R) * (wx - R);
@@ -271,19 +279,21 @@ __device__ __forceinline__ void refine_tile(const RefineArgs &a, int x0, int y0,
           const uint32_t c = lab_sad(labx, wv);
           const uint32_t v = (sEc[c] * sEs[dx2 + dy * dy]) >> kVoteShift;
           if (dv != run_d) {
-            if (run) atomicAdd(&hist[run_d], run);
+            if (run) add_run(run_d, run);
             run_d = dv;
             run = 0;
           }
           run += v;
         }
       }
-      if (run) atomicAdd(&hist[run_d], run);
+      if (run) add_run(run_d, run);
     }
     __syncwarp();
+    // the argmax scans only the bins some lane touched (no pixel's votes span many disparities)
+    const int rlo = (int)__reduce_min_sync(0xFFFFFFFFu, dlo), rhi = (int)__reduce_max_sync(0xFFFFFFFFu, dhi);
     uint32_t bv = 0;
     int bd = 0x7FFFFFFF;
-    for (int d = lane; d < a.dmax; d += 32) {
+    for (int d = rlo + lane; d <= rhi; d += 32) {
       const uint32_t hv = hist[d];
       if (hv > bv) {
         bv = hv;
@@ -291,6 +301,7 @@ __device__ __forceinline__ void refine_tile(const RefineArgs &a, int x0, int y0,
       }
     }
     const uint32_t gmax = __reduce_max_sync(0xFFFFFFFFu, bv);
+    for (int d = rlo + lane; d <= rhi; d += 32) hist[d] = 0;  // every lane's reads fed the reduction above
     int best;
     if (gmax > 0) {
       best = (int)__reduce_min_sync(0xFFFFFFFFu, (unsigned)(bv == gmax ? bd : 0x7FFFFFFF));
