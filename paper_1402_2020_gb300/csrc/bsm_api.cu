@@ -311,10 +311,11 @@ bsm_status bsm_match_host(bsm_ctx *ctx, const uint8_t *rgbL_host, const uint8_t 
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->copy_done, cudaEventDisableTiming);
     if (e != cudaSuccess) return from_cuda(e);
   }
-  // the right view uploads on the context's copy stream while the left view is described
-  e = cudaEventRecord(ctx->copy_after, s);
+  // the left view uploads first, alone on the host link; the right view then uploads on the context's copy
+  // stream while the left view is described (both at once would share the link and delay the left view)
+  e = cudaMemcpyAsync(dl, rgbL_host, (size_t)h * pitch_bytes, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaEventRecord(ctx->copy_after, s);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->copy_stream, ctx->copy_after, 0);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(dl, rgbL_host, (size_t)h * pitch_bytes, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(dr, rgbR_host, (size_t)h * pitch_bytes, cudaMemcpyHostToDevice, ctx->copy_stream);
   if (e == cudaSuccess) e = cudaEventRecord(ctx->copy_done, ctx->copy_stream);

@@ -98,7 +98,7 @@ struct bsm_ctx {
   cudaEvent_t batch_copied = nullptr;   // the graph's table copy has finished
   cudaStream_t batch_capture = nullptr; // stream the graph is captured on
   cudaStream_t copy_stream = nullptr;   // bsm_match_host: the right view's upload beside the left's describe
-  cudaEvent_t copy_after = nullptr;     // ... ordered after the caller's earlier work
+  cudaEvent_t copy_after = nullptr;     // ... ordered after the caller's earlier work and the left view's upload
   cudaEvent_t copy_done = nullptr;      // ... and awaited before the right view's describe
   uint16_t *sgm_ws = nullptr;           // bsm_sgm: 16-bit path-cost planes of every direction + the largest cost
   size_t sgm_ws_bytes = 0;
