@@ -1,8 +1,8 @@
 """The integer and fp16 identities the describe kernels rely on, checked exhaustively on the host (no GPU).
 
 These are facts about the encodings, not about the oracle: the fp16 form of the Eq. 5 weights, the
-per-step count of the T bisection (Eq. 6) from 0xFFFF half masks, and the order-statistic bracket that
-starts the bisection."""
+per-step count of the T bisection (Eq. 6) from saturating fp16 subtracts, and the order-statistic bracket
+that starts the bisection."""
 import numpy as np
 import pytest
 
@@ -22,33 +22,29 @@ def test_biased_weight_is_the_fp16_of_1024_plus_w():
     assert (np.diff(pats) == 1.0).all()
 
 
-@pytest.mark.parametrize("nh", [1, 2, 4, 64])
-def test_mask_sum_count(nh):
-    # a lane holds nh fp16x2 registers; per register a compare yields 0xFFFF in each true half. The lane
-    # sums the nh masks as 32-bit integers and multiplies by -(2^17 + 1): the high half must be the
-    # lane's count, the low half the count of true low halves (<= nh), whatever the true halves are.
-    mul = (-0x20001) & M32
+@pytest.mark.parametrize("nh", [1, 2, 4])
+def test_saturating_count(nh):
+    # One step of the T bisection. Per fp16x2 register of weights (1024 + w), a saturating subtract from
+    # 1024 + t + 1 gives 1 in each half where w <= t and 0 elsewhere; the lane adds its nh results to a
+    # bias of 1024, so each half's bits are 0x6400 + that half's count; the warp's 32 lane sums added as
+    # 32-bit integers, minus 32 * 0x6400 * (1 + 2^16) mod 2^32, leave the low halves' count in the low 16
+    # bits and the high halves' count above. Every value is an integer below 2048: exact in fp16.
+    assert (32 * 0x6400 * (1 + (1 << 16))) & M32 == 0x800C8000
     rng = np.random.default_rng(nh)
-    for _ in range(200):
-        lo = rng.integers(0, 2, size=nh)
-        hi = rng.integers(0, 2, size=nh)
-        S = 0
-        for a, b in zip(lo, hi):
-            S = (S + (0xFFFF if a else 0) + (0xFFFF0000 if b else 0)) & M32
-        t = (S * mul) & M32
-        assert t >> 16 == int(lo.sum() + hi.sum())
-        assert t & 0xFFFF == int(lo.sum())
-    # every (c_lo, c_hi) and the warp-wide sum of 32 such lanes: count << 16 plus a part below 2^16
-    for c_lo in range(nh + 1):
-        for c_hi in range(nh + 1):
-            S = (c_lo * 0xFFFF + c_hi * 0xFFFF0000) & M32
-            assert (S * mul) & M32 == c_lo + ((c_lo + c_hi) << 16)
-    lanes = rng.integers(0, nh + 1, size=(32, 2))
-    tot = sum(((int(a) * 0xFFFF + int(b) * 0xFFFF0000) * mul) & M32 for a, b in lanes) & M32
-    count = int(lanes.sum())
-    assert tot >> 16 == count and (tot & 0xFFFF) == int(lanes[:, 0].sum())
-    for k in (1, count, count + 1, 32 * 2 * nh):
-        assert (tot >= (k << 16)) == (count >= k)
+    for _ in range(300):
+        t = int(rng.integers(0, 766))
+        w = rng.integers(0, 766, size=(32, nh, 2))  # lanes x registers x halves
+        c = np.clip(np.float16(1024 + t + 1) - (1024 + w).astype(np.float16), np.float16(0), np.float16(1))
+        assert (c == (w <= t)).all()
+        s = np.full((32, 2), 1024, dtype=np.float16)
+        for m in range(nh):
+            s = (s + c[:, m, :]).astype(np.float16)
+        bits = s.view(np.uint16).astype(np.uint64)
+        assert (bits - 0x6400 == (w <= t).sum(axis=1)).all()
+        words = bits[:, 0] | (bits[:, 1] << 16)
+        tot = (int(words.sum()) - 0x800C8000) & M32
+        assert tot & 0xFFFF == int((w[:, :, 0] <= t).sum())
+        assert tot >> 16 == int((w[:, :, 1] <= t).sum())
 
 
 @pytest.mark.parametrize("nw,k", [(2, 16), (4, 32), (8, 64), (8, 33), (8, 32), (4, 1), (8, 256)])
