@@ -248,6 +248,33 @@ def test_refine_fallback_and_tolerance(B, orc):
         c.close()
 
 
+# An image with at least 4 x 152 blocks of 32 x 32 takes the refinement's 32-row blocks in decreasing order
+# of their invalid pixels (counted by the pre-pass). Hand-made maps: disparities below 24 constant over
+# 96 x 96 blocks with dR = dL (invalid only where the match crosses a block edge), and a few large rectangles where
+# dR disagrees, so a handful of blocks carry most of the invalid pixels. R = 7 runs the general-radius
+# kernel, R = 15 the unrolled one.
+@pytest.mark.parametrize("R", [7, 15])
+def test_refine_ordered_blocks_bit_exact(B, orc, R):
+    w, h, dmax = 1280, 512, 64
+    l, _, _ = synth.stereo_pair(w, h, dmax, seed=450)
+    rng = np.random.default_rng(451 + R)
+    blocks = rng.integers(0, 24, size=((h + 95) // 96, (w + 95) // 96))
+    dL = np.kron(blocks, np.ones((96, 96), np.int64))[:h, :w].astype(np.int32)
+    dR = dL.copy()
+    for _ in range(6):
+        y0, x0 = int(rng.integers(0, h - 100)), int(rng.integers(0, w - 160))
+        dR[y0:y0 + int(rng.integers(40, 100)), x0:x0 + int(rng.integers(60, 160))] = rng.integers(0, dmax)
+    c = Ctx(B, synth.pair_table(64, 31, seed=452), dmax=dmax, vote_radius=R)
+    img = torch.from_numpy(np.ascontiguousarray(l.reshape(h, 3 * w))).cuda()
+    out = c.refine(img, 3 * w, torch.from_numpy(dL).cuda(), torch.from_numpy(dR).cuda(), dmax)
+    torch.cuda.synchronize()
+    valid = orc.lr_check(dL, dR, 1)
+    assert 0.02 < 1.0 - valid.mean() < 0.6  # some invalid pixels, clustered in the rectangles
+    ref = orc.refine(l, dL, valid, dmax, R=R)
+    assert (out.cpu().numpy() == ref).all()
+    c.close()
+
+
 def test_match_host_equals_device_chain(B, orc):
     w, h, dmax = 200, 90, 48
     l, r, _ = synth.stereo_pair(w, h, dmax, seed=500)
