@@ -253,11 +253,11 @@ def test_refine_fallback_and_tolerance(B, orc):
 # 96 x 96 blocks with dR = dL (invalid only where the match crosses a block edge), and a few large rectangles where
 # dR disagrees, so a handful of blocks carry most of the invalid pixels. R = 7 runs the general-radius
 # kernel, R = 15 the unrolled one.
-@pytest.mark.parametrize("R", [7, 15])
-def test_refine_ordered_blocks_bit_exact(B, orc, R):
-    w, h, dmax = 1280, 512, 64
+@pytest.mark.parametrize("R,w,h", [(7, 1280, 512), (15, 1280, 512), (15, 1290, 500)])  # the last: ragged blocks
+def test_refine_ordered_blocks_bit_exact(B, orc, R, w, h):
+    dmax = 64
     l, _, _ = synth.stereo_pair(w, h, dmax, seed=450)
-    rng = np.random.default_rng(451 + R)
+    rng = np.random.default_rng(451 + R + w)
     blocks = rng.integers(0, 24, size=((h + 95) // 96, (w + 95) // 96))
     dL = np.kron(blocks, np.ones((96, 96), np.int64))[:h, :w].astype(np.int32)
     dR = dL.copy()
