@@ -7,16 +7,17 @@
 // (refine_words_kernel, one warp per row) forms the words; the batched form builds them while staging,
 // with byte 3 = 0 for invalid pixels, and scans the row for the fallback instead.
 //
-// One CTA (16 warps) covers a 32 x 32 block of output pixels. The pre-pass also counts each block's invalid
-// pixels, and the blocks are taken in decreasing order of that count: invalid pixels cluster (occlusions),
-// so a few blocks carry most of the votes, and started last they would set the kernel's tail. The CTA
-// stages the words of the block plus a halo of R pixels, together with the two integer vote tables. Valid pixels keep their disparity. Invalid
-// pixels are collected into a list that the CTA's warps share: a warp takes one invalid pixel at a
-// time and walks the window's valid voters, summing each one's vote floor(Ec[c] * Es[e2] / 2^15) in a
-// register while consecutive voters share a disparity and adding the run to a per-warp shared
-// histogram over d when the disparity changes (disparities are piecewise smooth, so runs are long and
-// shared atomics few). The warp then takes the smallest d with the largest weight (Eq. 9), or the
-// fallback when no vote is positive.
+// One CTA (16 warps) covers a 32 x 32 block of output pixels (32 x 8 on small images). The pre-pass also
+// counts each block's invalid pixels, and the blocks are taken in decreasing order of that count: invalid
+// pixels cluster (occlusions), so a few blocks carry most of the votes, and started last they would set
+// the kernel's tail. The CTA stages the words of the block plus a halo of R pixels, together with the two
+// integer vote tables. Valid pixels keep their disparity. Invalid pixels are collected into a list that
+// the CTA's warps share: a warp takes one invalid pixel at a time and walks the window's valid voters,
+// summing each one's vote floor(Ec[c] * Es[e2] / 2^15) in a register while consecutive voters share a
+// disparity and adding the run to a per-warp shared histogram over d when the disparity changes
+// (disparities are piecewise smooth, so runs are long and shared atomics few). The warp then takes the
+// smallest d with the largest weight (Eq. 9), scanning only the bins between the smallest and largest
+// disparity it added to, or the fallback when no vote is positive.
 //
 // The batched form reads the colour words from the batch's colour planes, and its disparity inputs
 // are the batched cost kernel's keys (A << 10 | d): every read keeps the low 10 bits, and each CTA
